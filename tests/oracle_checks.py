@@ -1,0 +1,339 @@
+"""Checks that pin the FP64 oracle to what the paper and the mathematics fix.
+
+Each function returns a number (an error or a p-value) so the same checks can
+be asserted by the pin tests and re-run on deliberately broken copies of the
+oracle (the mutation test).  None of them re-derives the oracle's formulas:
+they use closed forms, invariants, exact symmetries, quadrature of the
+definitions, brute-force ray casting and an independent Philox implementation.
+"""
+import math
+
+import numpy as np
+from scipy import stats
+
+from oracle import brute, grad, microfacet, philox, vndf
+
+# (theta_i [deg], phi_i [deg], alpha_x, alpha_y) cases used by several pins
+CASES = [
+    (30.0, 40.0, 0.3, 0.3),
+    (75.0, 120.0, 0.5, 0.1),
+    (85.0, -60.0, 0.05, 0.2),
+    (0.0, 0.0, 0.7, 0.7),
+    (60.0, 10.0, 1.0, 1.0),
+]
+
+
+def direction(theta_deg, phi_deg):
+    t = math.radians(theta_deg)
+    p = math.radians(phi_deg)
+    return np.array([math.sin(t) * math.cos(p), math.sin(t) * math.sin(p), math.cos(t)])
+
+
+def random_batch(n, seed, alpha_lo=1e-2, cos_lo=1e-3):
+    rng = np.random.default_rng(seed)
+    ct = rng.uniform(cos_lo, 1.0, n)
+    ph = rng.uniform(0.0, 2.0 * np.pi, n)
+    st = np.sqrt(1.0 - ct * ct)
+    wi = np.stack([st * np.cos(ph), st * np.sin(ph), ct])
+    ax = np.exp(rng.uniform(np.log(alpha_lo), 0.0, n))
+    ay = np.exp(rng.uniform(np.log(alpha_lo), 0.0, n))
+    u1 = rng.random(n)
+    u2 = rng.random(n)
+    return u1, u2, wi, ax, ay
+
+
+def _bcast(wi, n):
+    return np.broadcast_to(np.asarray(wi, np.float64).reshape(3, 1), (3, n)).copy()
+
+
+# ---------------------------------------------------------------- P1 invariants
+def invariants_error(n=20000, seed=1):
+    """max(| |wm| - 1 |), and the minima of wm.wi and wm.z (must be > 0)."""
+    u1, u2, wi, ax, ay = random_batch(n, seed)
+    wm = vndf.sample_vndf(u1, u2, wi, ax, ay)
+    return (np.abs(np.sqrt(vndf.dot(wm, wm)) - 1.0).max(),
+            vndf.dot(wm, wi).min(), wm[2].min())
+
+
+# ---------------------------------------------------------------- P2 mirror cap
+def mirror_cap_error(n=20000, seed=2):
+    """Reflecting wi' about the returned half vector must give back the cap point c (Sec. 3.2)."""
+    u1, u2, wi, ax, ay = random_batch(n, seed)
+    wi_std = vndf.warp_to_hemisphere(wi, ax, ay)
+    h, c = vndf.sample_cap(u1, u2, wi_std)
+    hn = h / np.sqrt(vndf.dot(h, h))
+    d = vndf.dot(hn, wi_std)
+    refl = 2.0 * d * hn - wi_std
+    return np.abs(refl - c).max()
+
+
+def cap_uniformity_pvalues(n=200000, seed=3, zi=0.4):
+    """c.z must be uniform on [-zi, 1] and its azimuth uniform on [0, 2 pi) (Sec. 3.2, Eq. phase_function_cap)."""
+    rng = np.random.default_rng(seed)
+    u1 = rng.random(n)
+    u2 = rng.random(n)
+    wi_std = _bcast([math.sqrt(1 - zi * zi), 0.0, zi], n)
+    _, c = vndf.sample_cap(u1, u2, wi_std)
+    p_z = stats.kstest((c[2] + zi) / (1.0 + zi), "uniform").pvalue
+    p_phi = stats.kstest(np.mod(np.arctan2(c[1], c[0]), 2 * np.pi) / (2 * np.pi), "uniform").pvalue
+    return p_z, p_phi
+
+
+# ---------------------------------------------------------------- P3 change of variables
+def change_of_variables_error(n=5000, seed=4):
+    """pdf(wm(u)) * |d wm/du1 x d wm/du2| = 1 for every sample (the sampler realises Eq. 1)."""
+    u1, u2, wi, ax, ay = random_batch(n, seed)
+    # keep away from the measure-zero rim where the Jacobian is singular
+    u2 = np.clip(u2, 1e-6, 1 - 1e-6)
+    wm = vndf.sample_vndf(u1, u2, wi, ax, ay)
+    pdf = vndf.vndf_pdf(wm, wi, ax, ay)
+    d1, d2 = grad.u_jacobian_complex_step(u1, u2, wi, ax, ay)
+    cr = np.cross(d1.T, d2.T).T
+    return np.abs(pdf * np.sqrt(vndf.dot(cr, cr)) - 1.0).max()
+
+
+# ---------------------------------------------------------------- P4 quadrature
+def hemisphere_quadrature(ax, ay, m_tau=2000, m_phi=1920):
+    """Midpoint rule on the upper hemisphere with theta = atan(beta tan tau), beta = sqrt(ax ay).
+
+    Returns (wm (3, M), weights (M,), tau (M,), phi (M,)).  The substitution
+    concentrates nodes where a narrow lobe lives; the weights are the solid
+    angle sin(theta) dtheta dphi of each cell.
+    """
+    beta = math.sqrt(ax * ay)
+    tau = (np.arange(m_tau) + 0.5) * (0.5 * np.pi / m_tau)
+    phi = (np.arange(m_phi) + 0.5) * (2.0 * np.pi / m_phi)
+    tt = np.tan(tau)
+    theta = np.arctan(beta * tt)
+    dtheta = beta * (1.0 + tt * tt) / (1.0 + beta * beta * tt * tt)
+    w_tau = np.sin(theta) * dtheta * (0.5 * np.pi / m_tau)
+    th, ph = np.meshgrid(theta, phi, indexing="ij")
+    wt, _ = np.meshgrid(w_tau, phi, indexing="ij")
+    ta, _ = np.meshgrid(tau, phi, indexing="ij")
+    wm = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)]).reshape(3, -1)
+    return wm, (wt * (2.0 * np.pi / m_phi)).reshape(-1), ta.reshape(-1), ph.reshape(-1)
+
+
+def normalisation_errors(theta_deg, phi_deg, ax, ay):
+    """|int pdf - 1|, |int D cos - 1| and the G1 definition (Eq. g1) by quadrature."""
+    wi = direction(theta_deg, phi_deg)
+    wm, w, _, _ = hemisphere_quadrature(ax, ay)
+    n = wm.shape[1]
+    wib = _bcast(wi, n)
+    axb = np.full(n, ax)
+    ayb = np.full(n, ay)
+    pdf = vndf.vndf_pdf(wm, wib, axb, ayb)
+    d = vndf.ndf(wm, axb, ayb)
+    e_pdf = abs((pdf * w).sum() - 1.0)
+    e_ndf = abs((d * wm[2] * w).sum() - 1.0)
+    proj = (np.maximum(vndf.dot(wm, wib), 0.0) * d * w).sum()
+    g1 = vndf.smith_g1(wi.reshape(3, 1), wi.reshape(3, 1), ax, ay)[0]
+    e_g1 = abs(g1 - wi[2] / proj)
+    return e_pdf, e_ndf, e_g1
+
+
+# ---------------------------------------------------------------- P5 alpha = 1
+def alpha_one_errors(n=20000, seed=5):
+    """At alpha = 1 the stretch is the identity (Eqs. 2-4 directly).
+
+    Returns (max rel. error of pdf vs 2 max(0, wi.wm) / (pi (1 + wz)),
+             max |mz^2 - (1 - u2)| at normal incidence: the half vector of the
+             pole and a uniform sphere point is cosine distributed).
+    """
+    u1, u2, wi, _, _ = random_batch(n, seed)
+    one = np.ones(n)
+    wm = vndf.sample_vndf(u1, u2, wi, one, one)
+    pdf = vndf.vndf_pdf(wm, wi, one, one)
+    ref = 2.0 * np.maximum(vndf.dot(wi, wm), 0.0) / (np.pi * (1.0 + wi[2]))
+    e_pdf = np.abs(pdf / ref - 1.0).max()
+    wz = _bcast([0.0, 0.0, 1.0], n)
+    wm0 = vndf.sample_vndf(u1, u2, wz, one, one)
+    e_pole = np.abs(wm0[2] ** 2 - (1.0 - u2)).max()
+    return e_pdf, e_pole
+
+
+def small_alpha_spread(alpha=1e-6, n=20000, seed=6):
+    """Max angle between wm and the pole in units of alpha (alpha -> 0 limit)."""
+    u1, u2, wi, _, _ = random_batch(n, seed, cos_lo=0.05)
+    a = np.full(n, alpha)
+    wm = vndf.sample_vndf(u1, u2, wi, a, a)
+    ang = np.arctan2(np.hypot(wm[0], wm[1]), wm[2])
+    return ang.max() / alpha
+
+
+# ---------------------------------------------------------------- P10 symmetries
+def symmetry_errors(n=20000, seed=7):
+    """Exact symmetries of the construction (returns the max deviation of each)."""
+    u1, u2, wi, ax, ay = random_batch(n, seed)
+    base = vndf.sample_vndf(u1, u2, wi, ax, ay)
+    # rotate wi by pi about z, shift the azimuth by half a turn
+    r = vndf.sample_vndf(np.mod(u1 + 0.5, 1.0), u2, np.stack([-wi[0], -wi[1], wi[2]]), ax, ay)
+    e_rot = max(np.abs(r[0] + base[0]).max(), np.abs(r[1] + base[1]).max(), np.abs(r[2] - base[2]).max())
+    # mirror y, reverse the azimuth
+    m = vndf.sample_vndf(np.mod(1.0 - u1, 1.0), u2, np.stack([wi[0], -wi[1], wi[2]]), ax, ay)
+    e_mir = max(np.abs(m[0] - base[0]).max(), np.abs(m[1] + base[1]).max(), np.abs(m[2] - base[2]).max())
+    # swap the x and y axes together with the roughnesses: azimuth phi -> pi/2 - phi
+    s = vndf.sample_vndf(np.mod(0.25 - u1, 1.0), u2, np.stack([wi[1], wi[0], wi[2]]), ay, ax)
+    e_swp = max(np.abs(s[0] - base[1]).max(), np.abs(s[1] - base[0]).max(), np.abs(s[2] - base[2]).max())
+    return e_rot, e_mir, e_swp
+
+
+# ---------------------------------------------------------------- histogram tests (P7, P8, P9)
+N_TAU_BINS = 20
+N_PHI_BINS = 24
+
+
+def bin_index(wm, ax, ay):
+    """Histogram bin of each normal in (tau, phi) cells matching ``hemisphere_quadrature``."""
+    beta = math.sqrt(ax * ay)
+    theta = np.arctan2(np.hypot(wm[0], wm[1]), wm[2])
+    tau = np.arctan(np.tan(theta) / beta)
+    phi = np.mod(np.arctan2(wm[1], wm[0]), 2 * np.pi)
+    it = np.clip((tau / (0.5 * np.pi) * N_TAU_BINS).astype(int), 0, N_TAU_BINS - 1)
+    ip = np.clip((phi / (2 * np.pi) * N_PHI_BINS).astype(int), 0, N_PHI_BINS - 1)
+    return it * N_PHI_BINS + ip
+
+
+def counts(wm, ax, ay):
+    return np.bincount(bin_index(wm, ax, ay), minlength=N_TAU_BINS * N_PHI_BINS).astype(np.float64)
+
+
+def two_sample_chi2_pvalue(a, b, min_count=10):
+    """Two-sample chi-square homogeneity test on histogram counts a, b."""
+    keep = (a + b) >= min_count
+    ra, rb = a.sum(), b.sum()
+    k1 = math.sqrt(rb / ra)
+    k2 = math.sqrt(ra / rb)
+    aa = np.append(a[keep], a[~keep].sum())
+    bb = np.append(b[keep], b[~keep].sum())
+    m = (aa + bb) > 0
+    aa, bb = aa[m], bb[m]
+    chi2 = (((k1 * aa - k2 * bb) ** 2) / (aa + bb)).sum()
+    return stats.chi2.sf(chi2, aa.size - 1)
+
+
+def expected_bin_probabilities(wi, ax, ay):
+    """Integral of the pdf over each histogram bin (quadrature of Eq. 1)."""
+    wm, w, tau, phi = hemisphere_quadrature(ax, ay)
+    n = wm.shape[1]
+    pdf = vndf.vndf_pdf(wm, _bcast(wi, n), np.full(n, ax), np.full(n, ay))
+    it = np.clip((tau / (0.5 * np.pi) * N_TAU_BINS).astype(int), 0, N_TAU_BINS - 1)
+    ip = np.clip((phi / (2 * np.pi) * N_PHI_BINS).astype(int), 0, N_PHI_BINS - 1)
+    return np.bincount(it * N_PHI_BINS + ip, weights=pdf * w, minlength=N_TAU_BINS * N_PHI_BINS)
+
+
+def sample_case(theta_deg, phi_deg, ax, ay, n, seed, method="cap"):
+    rng = np.random.default_rng(seed)
+    wi = direction(theta_deg, phi_deg)
+    u1 = rng.random(n)
+    u2 = rng.random(n)
+    return vndf.sample_vndf(u1, u2, _bcast(wi, n), np.full(n, ax), np.full(n, ay), method)
+
+
+def chi2_vs_pdf_pvalue(theta_deg, phi_deg, ax, ay, n=1_000_000, seed=8):
+    """P8: sampled histogram against expected counts from the pdf."""
+    wm = sample_case(theta_deg, phi_deg, ax, ay, n, seed)
+    obs = counts(wm, ax, ay)
+    exp = n * expected_bin_probabilities(direction(theta_deg, phi_deg), ax, ay)
+    keep = exp >= 5
+    o = np.append(obs[keep], obs[~keep].sum())
+    e = np.append(exp[keep], exp[~keep].sum())
+    m = e > 0
+    chi2 = (((o - e) ** 2) / e)[m].sum()
+    return stats.chi2.sf(chi2, m.sum() - 1)
+
+
+def brute_force_pvalue(theta_deg, phi_deg, ax, ay, n=1_000_000, seed=9):
+    """P9: cap sampler against ray casting on the truncated ellipsoid (definition, Sec. 2)."""
+    rng = np.random.default_rng(seed)
+    ref = brute.visible_normals(direction(theta_deg, phi_deg), ax, ay, n, rng)
+    wm = sample_case(theta_deg, phi_deg, ax, ay, n, seed + 1)
+    return two_sample_chi2_pvalue(counts(wm, ax, ay), counts(ref, ax, ay))
+
+
+def prior_agreement_pvalue(theta_deg, phi_deg, ax, ay, n=1_000_000, seed=10):
+    """P7: cap sampler against the prior polar-disk sampler (same distribution claimed)."""
+    a = sample_case(theta_deg, phi_deg, ax, ay, n, seed, "cap")
+    b = sample_case(theta_deg, phi_deg, ax, ay, n, seed + 1, "polar")
+    return two_sample_chi2_pvalue(counts(a, ax, ay), counts(b, ax, ay))
+
+
+# ---------------------------------------------------------------- gradients (P11)
+def gradient_errors(n=400, seed=11):
+    """(complex step vs central differences, relative), and max |g_wi . wi| (degree-0 homogeneity)."""
+    u1, u2, wi, ax, ay = random_batch(n, seed, alpha_lo=0.05, cos_lo=0.05)
+    u2 = np.clip(u2, 1e-3, 1 - 1e-3)
+    jc = grad.jacobian_complex_step(u1, u2, wi, ax, ay)
+    jf = grad.jacobian_central_difference(u1, u2, wi, ax, ay)
+    scale = np.abs(jc).max(axis=0, keepdims=True) + 1e-12
+    e_fd = (np.abs(jc - jf) / scale).max()
+    e_hom = np.abs((jc[:3] * wi[:, None, :]).sum(axis=0)).max() / np.abs(jc).max()
+    return e_fd, e_hom
+
+
+# ---------------------------------------------------------------- albedo (P12)
+def smith_lambda_textbook(w, ax, ay):
+    """GGX Smith Lambda (Heitz 2014, JCGT 3(2)): (-1 + sqrt(1 + (ax^2 x^2 + ay^2 y^2) / z^2)) / 2."""
+    return 0.5 * (-1.0 + np.sqrt(1.0 + (ax * ax * w[0] ** 2 + ay * ay * w[1] ** 2) / w[2] ** 2))
+
+
+def g1_g2_textbook_errors(n=5000, seed=12):
+    """G1 = 1/(1 + Lambda) and height-correlated G2 = 1/(1 + Lambda_i + Lambda_o)."""
+    u1, u2, wi, ax, ay = random_batch(n, seed, cos_lo=0.05)
+    _, _, wo, _, _ = random_batch(n, seed + 1, cos_lo=0.05)
+    wm = vndf.sample_vndf(u1, u2, wi, ax, ay)
+    vis = (vndf.dot(wm, wo) > 0)
+    li = smith_lambda_textbook(wi, ax, ay)
+    lo = smith_lambda_textbook(wo, ax, ay)
+    e1 = np.abs(vndf.smith_g1(wm, wi, ax, ay) - 1.0 / (1.0 + li)).max()
+    g2 = microfacet.smith_g2(wm, wi, wo, ax, ay)
+    e2 = np.abs(g2[vis] - 1.0 / (1.0 + li[vis] + lo[vis])).max()
+    return e1, e2
+
+
+def brdf_albedo_quadrature(wi, ax, ay, f0, m_theta=1500, m_phi=1500):
+    """E = integral over the upper hemisphere of f_r(wi, wo) cos(theta_o) (Eq. rendering, L = 1)."""
+    th = (np.arange(m_theta) + 0.5) * (0.5 * np.pi / m_theta)
+    ph = (np.arange(m_phi) + 0.5) * (2 * np.pi / m_phi)
+    t, p = np.meshgrid(th, ph, indexing="ij")
+    wo = np.stack([np.sin(t) * np.cos(p), np.sin(t) * np.sin(p), np.cos(t)]).reshape(3, -1)
+    dw = (np.sin(t) * (0.5 * np.pi / m_theta) * (2 * np.pi / m_phi)).reshape(-1)
+    n = wo.shape[1]
+    f = microfacet.brdf(_bcast(wi, n), wo, ax, ay, f0)
+    return (f * wo[2] * dw).sum()
+
+
+def albedo_consistency_error(theta_deg, ax, ay, f0=0.04):
+    """Importance-sampled albedo (quadrature over u) vs direct BRDF integration over wo."""
+    wi = direction(theta_deg, 0.0)
+    e_u = microfacet.albedo_quadrature(wi, ax, ay, f0, m=1024)
+    e_w = brdf_albedo_quadrature(wi, ax, ay, f0)
+    return abs(e_u - e_w)
+
+
+def reflection_errors(n=5000, seed=13):
+    """Eq. halfvector inverts Eq. reflect: normalize(wa + wb) = wm and |wb| = 1."""
+    u1, u2, wi, ax, ay = random_batch(n, seed, cos_lo=0.05)
+    wa = wi
+    wm = vndf.sample_vndf(u1, u2, wa, ax, ay)
+    wb = microfacet.reflect(wm, wa)
+    h = wa + wb
+    hn = h / np.sqrt(vndf.dot(h, h))
+    return np.abs(hn - wm).max(), np.abs(np.sqrt(vndf.dot(wb, wb)) - 1.0).max()
+
+
+def reflected_change_of_variables_error(n=2000, seed=14):
+    """PDF(wb) |d wb/du1 x d wb/du2| = 1: the BSDF pdf of App. A (with Eq. jacobian) is
+    the density of the reflected direction, checked pointwise through the sampler."""
+    u1, u2, wa, ax, ay = random_batch(n, seed, alpha_lo=0.05, cos_lo=0.05)
+    u2 = np.clip(u2, 1e-4, 1 - 1e-4)
+    wm = vndf.sample_vndf(u1, u2, wa, ax, ay)
+    pdf = microfacet.bsdf_pdf(wm, wa, ax, ay)
+
+    def wb_of(v1, v2):
+        return microfacet.reflect(vndf.sample_vndf(v1, v2, wa.astype(np.complex128), ax, ay), wa)
+
+    d1 = np.imag(wb_of(u1 + 1j * grad.H_CS, u2.astype(np.complex128))) / grad.H_CS
+    d2 = np.imag(wb_of(u1.astype(np.complex128), u2 + 1j * grad.H_CS)) / grad.H_CS
+    cr = np.cross(d1.T, d2.T).T
+    return np.abs(pdf * np.sqrt(vndf.dot(cr, cr)) - 1.0).max()
