@@ -1,0 +1,377 @@
+#!/usr/bin/env python3
+"""Throughput of spherical-cap GGX VNDF sampling on GB300 (one JSON line on rank 0).
+
+Workload (the anisotropic streaming case): 2^28 samples per GPU per step,
+float32 structure-of-arrays, alpha_x and alpha_y independently log-uniform in
+[1e-3, 1], cos(theta_i) uniform in [1e-4, 1], phi_i uniform, uniforms drawn in
+the kernel from Philox4x32-10 (seed 2).  A step is one vndf_sample call over
+the whole batch (stretch, cap sample, half vector, unstretch, fused pdf,
+store): 20 B read + 16 B written per sample, 9.66 GB per step, far larger than
+L2, so no flush is needed between steps.  The same step is timed with the prior
+polar-disk sampler for comparison.
+
+Arms:
+  default            the CUDA library (this repository)
+  --impl reference   the FP64 CPU oracle timed on bounded samples of the same
+                     workload (no GPU work)
+
+Multi-GPU (torchrun): every rank samples its own 2^28 slice of one global index
+range (weak scaling, no collective on the data path); the barrier and
+max-over-ranks timing are the only communication.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VNDF Gsamples/s (fwd, fwd+bwd) vs prior-sampler kernel; % HBM/SFU roofline"
+UNIT = "Gsamples/s"
+WORKLOAD = "anisotropic_stream_2e28"
+BYTES_PER_SAMPLE = 36  # in: wi xyz + alpha xy (20 B); out: wm xyz + pdf (16 B)
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ("paper_2306_05044_gb300/csrc/sample.cu", "paper_2306_05044_gb300/csrc/vndf_math.cuh",
+                  "paper_2306_05044_gb300/csrc/philox.cuh", "paper_2306_05044_gb300/csrc/common.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "vndf_sample_cap_anisotropic_stream.md")
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--log2n", type=int, default=28, help="samples per GPU per step = 2^log2n")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-prior", action="store_true")
+    p.add_argument("--no-clocks", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic_per_sample():
+    """DRAM bytes per sample from the committed ncu summary, if it matches the current kernel."""
+    try:
+        text = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        line = line.strip().strip("-* ")
+        if ":" in line:
+            k, _, v = line.partition(":")
+            vals[k.strip().strip("`")] = v.strip().strip("`")
+    if vals.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_sample"])
+    except (KeyError, ValueError):
+        return None
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(parts)
+            except ValueError:
+                pass
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, val in zip(names, r[5:9]) if val.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def time_oracle_sample(n, seed=2):
+    """Oracle (FP64 numpy) over the first n samples of the workload; returns seconds."""
+    import numpy as np
+    import torch
+
+    import workloads
+    from oracle import philox, vndf
+    d = workloads.anisotropic_stream(n=n, device="cpu")
+    wi = np.stack([d[k].numpy() for k in ("wi_x", "wi_y", "wi_z")])
+    ax, ay = d["alpha_x"].numpy(), d["alpha_y"].numpy()
+    torch.set_num_threads(1)
+    t0 = time.perf_counter()
+    u1, u2 = philox.sample_uniforms(seed, 0, 0, n)
+    vndf.sample_vndf_with_pdf(u1, u2, wi, ax, ay, "cap")
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(budget_s=15.0):
+    probe = 1 << 16
+    t = time_oracle_sample(probe)
+    n = int(min(1 << 24, max(probe, probe * budget_s / max(t, 1e-6))))
+    n = 1 << int(math.log2(n))
+    t = time_oracle_sample(n)
+    return {"value": n / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n} samples of the 2^28 anisotropic workload (Philox seed 2): "
+                      f"FP64 numpy oracle, Philox + cap sampler + pdf, single thread, {t:.1f} s"}
+
+
+def emit(obj):
+    print(json.dumps(obj), flush=True)
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    steps, warm = max(args.steps, 1), max(args.warmup, 0)
+    probe = 1 << 14
+    t = time_oracle_sample(probe)
+    per_step = int(min(1 << 22, max(1 << 12, probe * (120.0 / (steps + warm)) / max(t, 1e-6))))
+    per_step = 1 << int(math.log2(per_step))
+    for _ in range(warm):
+        time_oracle_sample(per_step)
+    times = [time_oracle_sample(per_step) for _ in range(steps)]
+    total = sum(times)
+    value = per_step * steps / total / 1e9
+    emit({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+          "steps": steps, "warmup": warm, "ms_per_step": 1e3 * total / steps, "higher_is_better": True,
+          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+          "config": {"workload": WORKLOAD, "samples_per_step": per_step, "seed": 2,
+                     "note": "bounded sample of the 2^28-sample workload per step"},
+          "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                           "sample": f"{per_step} samples per step, FP64 numpy oracle, single thread"},
+          "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_2306_05044_gb300 as vndf
+    import workloads
+    from paper_2306_05044_gb300 import _build
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    vndf.load()
+    n = 1 << args.log2n
+    base = rank * n
+    d = workloads.anisotropic_stream(n=n, device=dev)
+    outs = [torch.empty(n, device=dev) for _ in range(4)]
+    stream = torch.cuda.current_stream(dev)
+
+    def step(method="cap"):
+        vndf.vndf_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], seed=2,
+                         counter_base=base, method=method, wm_x=outs[0], wm_y=outs[1], wm_z=outs[2],
+                         pdf=outs[3])
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(fn, steps, warmup, clocks=False):
+        for _ in range(warmup):
+            fn()
+        barrier()
+        sampler = ClockSampler(local) if clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        evs[0].record(stream)
+        for k in range(steps):
+            fn()
+            evs[k + 1].record(stream)
+        barrier()
+        clock = sampler.stop() if sampler else None
+        per = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+        total = evs[0].elapsed_time(evs[-1])
+        if world > 1:
+            t = torch.tensor([total], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total = float(t.item())
+        return total, per, clock
+
+    steps, warm = max(args.steps, 1), max(args.warmup, 3)
+    total, per, clock = timed(step, steps, warm, clocks=not args.no_clocks)
+    value = world * n * steps / (total * 1e-3) / 1e9
+    avg_ms = total / steps
+
+    peak, peak_kind = hbm_peak()
+    achieved = BYTES_PER_SAMPLE * n / (avg_ms * 1e-3) / 1e9
+    tps = measured_traffic_per_sample()
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warm,
+        "ms_per_step": avg_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "samples_per_gpu": n, "method": "spherical_cap", "rng": "philox4x32-10 in-kernel",
+                   "alpha": "log-uniform [1e-3, 1] x, y independent", "cos_theta_i": "uniform [1e-4, 1]",
+                   "l2": "inputs larger than L2 (9.66 GB touched per step); no flush",
+                   "parallelism": f"index-range shards x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": f"{peak_kind} copy bandwidth",
+                     "traffic": (tps * n) if tps is not None else None,
+                     "algorithmic_bytes": BYTES_PER_SAMPLE * n, "kernel": "sample_vec4_kernel<cap, philox, aniso, pdf>"},
+        "gpu_launches": steps,
+        "clocks": clock,
+        "per_step_ms": {"min": min(per), "median": statistics.median(per), "max": max(per)},
+    }
+
+    if not args.no_prior:
+        ptotal, pper, _ = timed(lambda: step("polar"), steps, warm)
+        pv = world * n * steps / (ptotal * 1e-3) / 1e9
+        result["prior_sampler"] = {
+            "value": pv, "unit": UNIT, "ms_per_step": ptotal / steps,
+            "roofline_frac": BYTES_PER_SAMPLE * n / (ptotal / steps * 1e-3) / 1e9 / peak,
+            "cap_over_prior": value / pv}
+        result["gpu_launches_prior"] = steps
+
+    if not args.no_e2e:
+        result["e2e"] = e2e(vndf, d, n, base, dev, stream, steps, warm, barrier, world)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        emit(result)
+
+
+def e2e(vndf, d, n, base, dev, stream, steps, warm, barrier, world):
+    """Same step through the public API with host buffers: H2D inputs, sample, D2H outputs.
+
+    Chunks of 2^24 samples are pipelined over three streams so copies in both
+    directions overlap the kernels; the timed region covers all of it.
+    """
+    import torch
+    keys = ("wi_x", "wi_y", "wi_z", "alpha_x", "alpha_y")
+    host_in = {k: d[k].cpu().pin_memory() for k in keys}
+    host_out = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in range(4)]
+    chunk = min(n, 1 << 24)
+    nstreams = 3
+    streams = [torch.cuda.Stream(dev) for _ in range(nstreams)]
+    dev_in = [{k: torch.empty(chunk, device=dev) for k in keys} for _ in range(nstreams)]
+    dev_out = [[torch.empty(chunk, device=dev) for _ in range(4)] for _ in range(nstreams)]
+    start_ev = torch.cuda.Event()
+
+    def one_step():
+        start_ev.record(stream)
+        done = []
+        for c, off in enumerate(range(0, n, chunk)):
+            m = min(chunk, n - off)
+            s = streams[c % nstreams]
+            s.wait_event(start_ev)
+            with torch.cuda.stream(s):
+                di, do = dev_in[c % nstreams], dev_out[c % nstreams]
+                for k in keys:
+                    di[k][:m].copy_(host_in[k][off:off + m], non_blocking=True)
+                vndf.vndf_sample(di["wi_x"], di["wi_y"], di["wi_z"], di["alpha_x"], di["alpha_y"], seed=2,
+                                 counter_base=base + off, wm_x=do[0], wm_y=do[1], wm_z=do[2], pdf=do[3], n=m,
+                                 stream=s)
+                for j in range(4):
+                    host_out[j][off:off + m].copy_(do[j][:m], non_blocking=True)
+        for s in streams:
+            ev = torch.cuda.Event()
+            ev.record(s)
+            stream.wait_event(ev)
+
+    for _ in range(warm):
+        one_step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        one_step()
+    e1.record(stream)
+    barrier()
+    total = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+    return {"value": world * n * steps / (total * 1e-3) / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": 20 * n, "d2h_bytes_per_step": 16 * n,
+            "ms_per_step": total / steps, "pipeline": f"{nstreams} streams, {chunk}-sample chunks, pinned host memory"}
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

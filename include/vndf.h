@@ -1,0 +1,128 @@
+/*
+ * vndf.h -- C ABI of libvndf: spherical-cap sampling of GGX visible normals on
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: Dupuy & Benyoub, "Sampling Visible GGX Normals with Spherical Caps",
+ * HPG 2023 (arXiv 2306.05044).  Every entry point below batches the paper's
+ * per-sample problem "map two uniforms (u1, u2) in [0, 1), an incident
+ * direction wi and roughnesses (alpha_x, alpha_y) to a microfacet normal wm"
+ * (Sec. 2, "Importance Sampling") over n samples.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ * - Arrays are structure-of-arrays float32 (or int32 where stated) in DEVICE
+ *   memory, owned by the caller, and must stay valid until the work enqueued
+ *   on `cuda_stream` has finished.  Element i of every array belongs to sample
+ *   (or query) i.  Pointers must be 4-byte aligned; when every pointer of a
+ *   call is 16-byte aligned the 128-bit vector path is taken, otherwise a
+ *   scalar path.  Results never depend on the path, the launch shape or how a
+ *   batch is split into calls.
+ * - `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *   are asynchronous and allocate no memory.
+ * - Host-side argument errors return a negative VNDF_ERR_* code before any
+ *   work is enqueued.  A failed launch returns VNDF_ERR_CUDA.  Errors that
+ *   happen while the kernel runs surface at the caller's next synchronisation.
+ * - Domain: wi.z > 0, alpha_x > 0, alpha_y > 0, all finite.  wi need not be
+ *   unit length (the method is invariant to its scale).  A sample outside the
+ *   domain raises no error: it returns wm = (0, 0, 1) and pdf = 0.
+ * - Random numbers: when u1 and u2 are both NULL, the uniforms are drawn in
+ *   the kernel from Philox4x32-10 (Salmon et al., SC'11) with key = seed and
+ *   counter = (b mod 2^32, b >> 32, stream_id, 0), b = g >> 1, where
+ *   g = counter_base + i is the global index of sample i (mod 2^64).  An even g
+ *   takes words (0, 1) of its block, an odd g words (2, 3); the first word
+ *   gives u1 and the second u2 as (word >> 8) * 2^-24.  u1 drives the azimuth
+ *   and u2 the cap height, as in both samplers the paper prints.
+ */
+#ifndef VNDF_H
+#define VNDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define VNDF_OK 0
+#define VNDF_ERR_NULL (-1)      /* a required pointer is NULL                        */
+#define VNDF_ERR_SIZE (-2)      /* a size is negative or above its stated limit      */
+#define VNDF_ERR_ALIGN (-3)     /* a pointer is not aligned to its element size      */
+#define VNDF_ERR_METHOD (-4)    /* unknown sampling method                           */
+#define VNDF_ERR_WORKSPACE (-5) /* workspace missing or smaller than required        */
+#define VNDF_ERR_CUDA (-6)      /* a CUDA runtime call or kernel launch failed       */
+#define VNDF_ERR_ARG (-7)       /* optional arguments given in an invalid combination */
+
+/* ---- sampling methods ------------------------------------------------ */
+/* The paper's sampler: half vector between wi and a point drawn uniformly on
+ * the spherical cap z in (-wi.z, 1] (Sec. 3.3, proved in Sec. 3.2). */
+#define VNDF_METHOD_SPHERICAL_CAP 0
+/* The prior sampler of Heitz 2018 that the paper improves on: uniform point on
+ * the projected cross section of the hemisphere (Sec. 2, step (2)). */
+#define VNDF_METHOD_POLAR_DISK 1
+
+/* Version of this ABI; bumped on any incompatible change. */
+int vndf_abi_version(void);
+
+/* Static, NUL-terminated description of a status code (never NULL). */
+const char *vndf_status_string(int status);
+
+/*
+ * vndf_rng_uniform -- the uniforms (u1, u2) that sample i would draw in
+ * Philox mode (see "Random numbers" above; the paper only requires u in
+ * [0, 1), Sec. 2).  Values lie in [0, 1 - 2^-24] and are exact float32.
+ *   n        number of samples (0 <= n < 2^62); n = 0 is a no-op.
+ *   u1, u2   outputs, n floats each (device).
+ * Returns VNDF_OK, VNDF_ERR_NULL, VNDF_ERR_SIZE, VNDF_ERR_ALIGN or VNDF_ERR_CUDA.
+ */
+int vndf_rng_uniform(int64_t n, uint64_t seed, uint64_t counter_base, uint32_t stream_id,
+                     float *u1, float *u2, void *cuda_stream);
+
+/*
+ * vndf_sample -- draw wm for each sample and, optionally, its density.
+ * Sec. 2 steps (1)-(3): stretch wi by M^-1 = diag(alpha_x, alpha_y, 1) and
+ * normalise; sample the hemisphere (method); unstretch by M^-T and normalise.
+ * With VNDF_METHOD_SPHERICAL_CAP step (2) is the paper's Sec. 3.3 sampler.
+ * The density is the GGX VNDF of Eq. 1,
+ *   pdf = G1(wi) max(0, wi.wm) D(wm) / wi.z      (D, G1 as in App. A),
+ * evaluated from the sampler's intermediate vectors rather than from the
+ * rounded wm, so it stays accurate at small roughness.
+ *   n                  number of samples (0 <= n < 2^62).
+ *   wi_x, wi_y, wi_z   incident direction, pointing away from the surface.
+ *   alpha_x, alpha_y   roughness; alpha_y = NULL means isotropic (alpha_y = alpha_x).
+ *   u1, u2             explicit uniforms in [0, 1), or both NULL for in-kernel Philox.
+ *   seed, counter_base, stream_id   Philox parameters (ignored with explicit u).
+ *   method             VNDF_METHOD_SPHERICAL_CAP or VNDF_METHOD_POLAR_DISK.
+ *   wm_x, wm_y, wm_z   outputs: unit microfacet normal.
+ *   pdf                output density (solid angle of wm), or NULL to skip it.
+ * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, ALIGN, METHOD, ARG, CUDA).
+ */
+int vndf_sample(int64_t n,
+                const float *wi_x, const float *wi_y, const float *wi_z,
+                const float *alpha_x, const float *alpha_y,
+                const float *u1, const float *u2,
+                uint64_t seed, uint64_t counter_base, uint32_t stream_id,
+                int method,
+                float *wm_x, float *wm_y, float *wm_z, float *pdf,
+                void *cuda_stream);
+
+/*
+ * vndf_pdf -- GGX VNDF density of given normals (Eq. 1, written through the
+ * App. A forms of D and G1):
+ *   pdf = 2 max(0, wi.wm) / (pi alpha_x alpha_y (|M^-1 wi| + wi.z) Q^2),
+ *   Q   = wm.x^2/alpha_x^2 + wm.y^2/alpha_y^2 + wm.z^2,
+ * which is G1(wi) max(0, wi.wm) D(wm) / wi.z for unit wm.  wm is used as given
+ * (unit length expected); wm.z <= 0 gives 0.  alpha_y = NULL means isotropic.
+ * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, ALIGN, CUDA).
+ */
+int vndf_pdf(int64_t n,
+             const float *wi_x, const float *wi_y, const float *wi_z,
+             const float *alpha_x, const float *alpha_y,
+             const float *wm_x, const float *wm_y, const float *wm_z,
+             float *pdf, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VNDF_H */

@@ -93,6 +93,14 @@ def sample_words(seed, counter_base, stream_id, n):
     return w1, w2
 
 
+def uniforms_at(seed, counter_base, stream_id, index):
+    """(u1, u2) in FP64 of the samples with the given local indices (any order)."""
+    g = np.uint64(int(counter_base) & 0xFFFFFFFFFFFFFFFF) + np.asarray(index, dtype=np.uint64)
+    out = philox4x32_10(block_counters(g >> np.uint64(1), stream_id), seed_key(seed))
+    odd = (g & np.uint64(1)).astype(bool)
+    return word_to_unit(np.where(odd, out[2], out[0])), word_to_unit(np.where(odd, out[3], out[1]))
+
+
 def sample_uniforms(seed, counter_base, stream_id, n):
     """(u1, u2) in FP64 for samples i = 0..n-1 (both exactly representable in FP32)."""
     w1, w2 = sample_words(seed, counter_base, stream_id, n)

@@ -1,0 +1,164 @@
+"""Python binding of libvndf: spherical-cap GGX visible-normal sampling on GB300.
+
+Dupuy & Benyoub, "Sampling Visible GGX Normals with Spherical Caps" (HPG 2023).
+The functions here carry the names of the C entry points declared in
+``include/vndf.h`` and only marshal arguments: they check tensor placement and
+dtype, allocate outputs with torch when none are given, pass raw device
+pointers and the current CUDA stream, and turn a negative status into
+``VndfError``.  Every step of the computation runs in libvndf's CUDA kernels;
+there is no fallback.  Importing works without a GPU, but every call needs
+the compiled library (``__graft_entry__.build()``) and a CUDA device.
+"""
+import ctypes
+import os
+
+import torch
+
+_PKG_DIR = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG_DIR, "libvndf.so")
+
+METHODS = {"cap": 0, "spherical_cap": 0, "polar": 1, "polar_disk": 1}
+
+VNDF_OK = 0
+_P = ctypes.c_void_p
+_F = ctypes.c_float
+_I32 = ctypes.c_int32
+_U32 = ctypes.c_uint32
+_I64 = ctypes.c_int64
+_U64 = ctypes.c_uint64
+_SZ = ctypes.c_size_t
+
+# name -> (restype, argtypes); mirrors include/vndf.h
+SIGNATURES = {
+    "vndf_abi_version": (ctypes.c_int, []),
+    "vndf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "vndf_rng_uniform": (ctypes.c_int, [_I64, _U64, _U64, _U32, _P, _P, _P]),
+    "vndf_sample": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _U64, _U64, _U32, ctypes.c_int,
+                                   _P, _P, _P, _P, _P]),
+    "vndf_pdf": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+}
+
+
+class VndfError(RuntimeError):
+    """A libvndf entry point returned a negative status."""
+
+    def __init__(self, func, status):
+        self.status = status
+        super().__init__(f"{func}: {status_string(status)} (status {status})")
+
+
+_lib = None
+
+
+def load():
+    """Load libvndf.so (built in-tree) and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libvndf.so is not built at {LIB_PATH}; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_string(status):
+    return load().vndf_status_string(int(status)).decode()
+
+
+def vndf_abi_version():
+    return load().vndf_abi_version()
+
+
+def _check(func, status):
+    if status != VNDF_OK:
+        raise VndfError(func, status)
+
+
+def _ptr(t, name, dtype=torch.float32):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must live on a CUDA device")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream, device):
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _out(t, n, like):
+    return torch.empty(n, dtype=torch.float32, device=like.device) if t is None else t
+
+
+def _method(method):
+    if isinstance(method, int):
+        return method
+    try:
+        return METHODS[method]
+    except KeyError:
+        raise ValueError(f"unknown method {method!r}") from None
+
+
+def vndf_rng_uniform(n, seed, counter_base=0, stream_id=0, u1=None, u2=None, device=None, stream=None):
+    """The (u1, u2) that vndf_sample draws in Philox mode for samples 0..n-1."""
+    device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    if u1 is None:
+        u1 = torch.empty(n, dtype=torch.float32, device=device)
+    if u2 is None:
+        u2 = torch.empty(n, dtype=torch.float32, device=device)
+    st = load().vndf_rng_uniform(int(n), int(seed) & (2**64 - 1), int(counter_base) & (2**64 - 1),
+                                 int(stream_id) & 0xFFFFFFFF, _ptr(u1, "u1"), _ptr(u2, "u2"),
+                                 _stream(stream, u1.device))
+    _check("vndf_rng_uniform", st)
+    return u1, u2
+
+
+def vndf_sample(wi_x, wi_y, wi_z, alpha_x, alpha_y=None, u1=None, u2=None, seed=0, counter_base=0,
+                stream_id=0, method="cap", wm_x=None, wm_y=None, wm_z=None, pdf=None, with_pdf=True,
+                n=None, stream=None):
+    """Sample wm (and its pdf) for every element; see vndf_sample in include/vndf.h.
+
+    alpha_y=None means isotropic; u1=u2=None means in-kernel Philox with
+    (seed, counter_base, stream_id).  Returns (wm_x, wm_y, wm_z, pdf or None).
+    """
+    n = wi_x.numel() if n is None else int(n)
+    wm_x = _out(wm_x, n, wi_x)
+    wm_y = _out(wm_y, n, wi_x)
+    wm_z = _out(wm_z, n, wi_x)
+    if with_pdf:
+        pdf = _out(pdf, n, wi_x)
+    else:
+        pdf = None
+    st = load().vndf_sample(
+        n, _ptr(wi_x, "wi_x"), _ptr(wi_y, "wi_y"), _ptr(wi_z, "wi_z"), _ptr(alpha_x, "alpha_x"),
+        _ptr(alpha_y, "alpha_y"), _ptr(u1, "u1"), _ptr(u2, "u2"), int(seed) & (2**64 - 1),
+        int(counter_base) & (2**64 - 1), int(stream_id) & 0xFFFFFFFF, _method(method),
+        _ptr(wm_x, "wm_x"), _ptr(wm_y, "wm_y"), _ptr(wm_z, "wm_z"), _ptr(pdf, "pdf"),
+        _stream(stream, wi_x.device))
+    _check("vndf_sample", st)
+    return wm_x, wm_y, wm_z, pdf
+
+
+def vndf_pdf(wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf=None, n=None, stream=None):
+    """GGX VNDF density of the given normals; see vndf_pdf in include/vndf.h."""
+    n = wi_x.numel() if n is None else int(n)
+    pdf = _out(pdf, n, wi_x)
+    st = load().vndf_pdf(n, _ptr(wi_x, "wi_x"), _ptr(wi_y, "wi_y"), _ptr(wi_z, "wi_z"),
+                         _ptr(alpha_x, "alpha_x"), _ptr(alpha_y, "alpha_y"), _ptr(wm_x, "wm_x"),
+                         _ptr(wm_y, "wm_y"), _ptr(wm_z, "wm_z"), _ptr(pdf, "pdf"),
+                         _stream(stream, wi_x.device))
+    _check("vndf_pdf", st)
+    return pdf

@@ -1,0 +1,18 @@
+// Status strings and the ABI version of libvndf.
+#include "vndf.h"
+
+extern "C" int vndf_abi_version(void) { return 1; }
+
+extern "C" const char* vndf_status_string(int status) {
+  switch (status) {
+    case VNDF_OK: return "ok";
+    case VNDF_ERR_NULL: return "a required pointer is NULL";
+    case VNDF_ERR_SIZE: return "a size is negative or above its limit";
+    case VNDF_ERR_ALIGN: return "a pointer is not aligned to its element size";
+    case VNDF_ERR_METHOD: return "unknown sampling method";
+    case VNDF_ERR_WORKSPACE: return "workspace missing or too small";
+    case VNDF_ERR_CUDA: return "a CUDA runtime call or kernel launch failed";
+    case VNDF_ERR_ARG: return "optional arguments given in an invalid combination";
+    default: return "unknown status";
+  }
+}

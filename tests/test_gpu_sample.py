@@ -1,0 +1,223 @@
+"""GPU parity of the sampling path against the FP64 oracle (through the C ABI).
+
+Sizes span many CTAs and a ragged tail; the full 2^28-sample anisotropic
+workload is checked on sampled outputs in the launch configuration the bench
+times.  Tolerances are explained in tests/parity.py.
+"""
+import numpy as np
+import pytest
+import torch
+
+import parity
+import workloads
+from oracle import philox, vndf as ovndf
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def v():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2306_05044_gb300 as lib
+    return lib
+
+
+def _np(*ts):
+    return [t.detach().cpu().numpy() for t in ts]
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=DEV)
+
+
+@pytest.mark.parametrize("n,seed,base,sid", [
+    (1 << 20, 1, 0, 0),
+    ((1 << 20) + 3, 2, 7, 1),
+    (4097, 0xFFFFFFFFFFFFFFFF, (1 << 64) - 6, 0xFFFFFFFF),
+    (33, 5, (1 << 32) - 3, 12),
+])
+def test_philox_bit_exact(v, n, seed, base, sid):
+    u1, u2 = v.vndf_rng_uniform(n, seed, base, sid, device=DEV)
+    r1, r2 = philox.sample_uniforms(seed, base, sid, n)
+    g1, g2 = _np(u1, u2)
+    np.testing.assert_array_equal(g1.astype(np.float64), r1)
+    np.testing.assert_array_equal(g2.astype(np.float64), r2)
+
+
+def test_philox_unaligned_output(v):
+    buf1 = torch.empty(1030, device=DEV)
+    buf2 = torch.empty(1030, device=DEV)
+    v.vndf_rng_uniform(1027, 9, 4, 2, u1=buf1[1:1028], u2=buf2[3:1030])
+    r1, r2 = philox.sample_uniforms(9, 4, 2, 1027)
+    np.testing.assert_array_equal(buf1[1:1028].cpu().numpy().astype(np.float64), r1)
+    np.testing.assert_array_equal(buf2[3:1030].cpu().numpy().astype(np.float64), r2)
+
+
+def test_cap_isotropic_2e20_explicit_u(v):
+    """2^20 samples, isotropic alpha ~ U[0.01, 1], wi uniform on the hemisphere, u from Philox(1)."""
+    n = 1 << 20
+    d = workloads.isotropic_2e20(n=n, device=DEV)
+    u1, u2 = philox.sample_uniforms(1, 0, 0, n)
+    wx, wy, wz, pdf = v.vndf_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], None, _dev(u1), _dev(u2))
+    wi = np.stack(_np(d["wi_x"], d["wi_y"], d["wi_z"]))
+    a = d["alpha_x"].cpu().numpy()
+    st = parity.compare_cap(np.stack(_np(wx, wy, wz)), pdf.cpu().numpy(), u1, u2, wi, a, a)
+    print("isotropic_2e20", st)
+    assert st["tail_angle_frac"] < 1e-4
+
+
+@pytest.mark.parametrize("n,base", [((1 << 20) + 5, 0), ((1 << 20) + 2, 3)])
+def test_cap_anisotropic_philox(v, n, base):
+    """Anisotropic workload distribution (log-uniform alphas in [1e-3, 1]), in-kernel Philox(2)."""
+    d = workloads.anisotropic_stream(n=n, device=DEV)
+    wx, wy, wz, pdf = v.vndf_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"],
+                                    seed=2, counter_base=base)
+    u1, u2 = philox.sample_uniforms(2, base, 0, n)
+    wi = np.stack(_np(d["wi_x"], d["wi_y"], d["wi_z"]))
+    st = parity.compare_cap(np.stack(_np(wx, wy, wz)), pdf.cpu().numpy(), u1, u2, wi,
+                            d["alpha_x"].cpu().numpy(), d["alpha_y"].cpu().numpy())
+    print("anisotropic", n, base, st)
+    assert st["tail_angle_frac"] < 1e-4 and st["tail_pdf_frac"] < 1e-4
+
+
+def test_philox_mode_equals_explicit_uniforms(v):
+    n = 100003
+    d = workloads.anisotropic_stream(n=n, seed=31, device=DEV)
+    a = v.vndf_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], seed=77, counter_base=11,
+                      stream_id=4)
+    u1, u2 = v.vndf_rng_uniform(n, 77, 11, 4, device=DEV)
+    b = v.vndf_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], u1, u2)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+def test_results_independent_of_path_and_split(v):
+    """Vector path, scalar path (unaligned views) and split calls give identical bits."""
+    n = 50001
+    d = workloads.anisotropic_stream(n=n + 1, seed=32, device=DEV)
+    full = v.vndf_sample(d["wi_x"][:n], d["wi_y"][:n], d["wi_z"][:n], d["alpha_x"][:n], d["alpha_y"][:n],
+                         seed=5, counter_base=100)
+    # shift every input by one element: misaligned, so the scalar path runs
+    shifted = {k: torch.cat([d[k][:1], d[k][:n]]) for k in ("wi_x", "wi_y", "wi_z", "alpha_x", "alpha_y")}
+    s = v.vndf_sample(shifted["wi_x"][1:], shifted["wi_y"][1:], shifted["wi_z"][1:], shifted["alpha_x"][1:],
+                      shifted["alpha_y"][1:], seed=5, counter_base=100, n=n)
+    for x, y in zip(full, s):
+        assert torch.equal(x, y)
+    # two calls over [0, k) and [k, n) with the counter base advanced by k
+    for k in (4, 9, 25000, 33333):
+        p1 = v.vndf_sample(*(d[q][:k] for q in ("wi_x", "wi_y", "wi_z", "alpha_x", "alpha_y")),
+                           seed=5, counter_base=100)
+        p2 = v.vndf_sample(*(d[q][k:n].contiguous() for q in ("wi_x", "wi_y", "wi_z", "alpha_x", "alpha_y")),
+                           seed=5, counter_base=100 + k)
+        for x, a, b in zip(full, p1, p2):
+            assert torch.equal(x, torch.cat([a, b]))
+
+
+def test_without_pdf_same_normals(v):
+    n = 4099
+    d = workloads.anisotropic_stream(n=n, seed=33, device=DEV)
+    a = v.vndf_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], seed=1)
+    b = v.vndf_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], seed=1, with_pdf=False)
+    assert b[3] is None
+    for x, y in zip(a[:3], b[:3]):
+        assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 5, 7, 8, 9])
+def test_tiny_sizes(v, n):
+    d = workloads.anisotropic_stream(n=max(n, 1), seed=34, device=DEV)
+    sl = {k: t[:n] for k, t in d.items()}
+    wx, wy, wz, pdf = v.vndf_sample(sl["wi_x"], sl["wi_y"], sl["wi_z"], sl["alpha_x"], sl["alpha_y"], seed=3)
+    if n == 0:
+        return
+    u1, u2 = philox.sample_uniforms(3, 0, 0, n)
+    wi = np.stack(_np(sl["wi_x"], sl["wi_y"], sl["wi_z"]))
+    parity.compare_cap(np.stack(_np(wx, wy, wz)), pdf.cpu().numpy(), u1, u2, wi,
+                       sl["alpha_x"].cpu().numpy(), sl["alpha_y"].cpu().numpy())
+
+
+def test_domain_edges_and_extremes(v):
+    """Fallback on invalid inputs; the extremes of the parity domain (alpha = 1e-3, wi.z = 1e-4,
+    u2 = 0 and u2 = 1 - 2^-24, u1 = 0)."""
+    nan = float("nan")
+    inf = float("inf")
+    wx = [0.3, 0.3, 0.3, 0.3, nan, 0.3, inf, 1.0, 0.99999, 0.0, 0.6, 0.6, 0.6, 0.6]
+    wy = [0.1, 0.1, 0.1, 0.1, 0.1, 0.1, 0.1, 0.0, 0.0, 0.0, 0.8, 0.8, -0.8, 0.8]
+    wz = [0.0, -0.5, 0.9, 0.9, 0.9, 0.9, 0.9, 1e-4, 1e-4, 1.0, 0.05, 0.05, 0.05, 0.05]
+    ax = [0.5, 0.5, 0.0, -1.0, 0.5, nan, 0.5, 1e-3, 1.0, 1e-3, 1e-3, 1.0, 1e-3, 0.3]
+    ay = [0.5, 0.5, 0.5, 0.5, 0.5, 0.5, 0.5, 1e-3, 1e-3, 1e-3, 1.0, 1e-3, 1e-3, 0.7]
+    u1 = [0.25, 0.25, 0.25, 0.25, 0.25, 0.25, 0.25, 0.0, 0.5, 0.75, 0.1, 0.9, 0.3, 0.0]
+    u2 = [0.5, 0.5, 0.5, 0.5, 0.5, 0.5, 0.5, 0.0, 1 - 2 ** -24, 1 - 2 ** -24, 0.999, 0.5, 1 - 2 ** -24, 0.0]
+    t = [_dev(x) for x in (wx, wy, wz, ax, ay, u1, u2)]
+    wmx, wmy, wmz, pdf = v.vndf_sample(*t[:5], t[5], t[6])
+    wi = np.array([wx, wy, wz], dtype=np.float32)
+    st = parity.compare_cap(np.stack(_np(wmx, wmy, wmz)), pdf.cpu().numpy(),
+                            np.array(u1, np.float32), np.array(u2, np.float32), wi,
+                            np.array(ax, np.float32), np.array(ay, np.float32))
+    assert st["out_of_domain"] == 7
+
+
+def test_prior_sampler_parity(v):
+    """The prior (polar-disk) sampler against its own FP64 oracle, same I/O as the cap sampler."""
+    n = (1 << 20) + 1
+    d = workloads.anisotropic_stream(n=n, device=DEV)
+    wx, wy, wz, pdf = v.vndf_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], seed=2,
+                                    method="polar")
+    u1, u2 = philox.sample_uniforms(2, 0, 0, n)
+    wi = np.stack(_np(d["wi_x"], d["wi_y"], d["wi_z"])).astype(np.float64)
+    ax, ay = (t.cpu().numpy().astype(np.float64) for t in (d["alpha_x"], d["alpha_y"]))
+    ref = ovndf.sample_vndf(u1, u2, wi, ax, ay, "polar")
+    pref = ovndf.vndf_pdf(ref, wi, ax, ay)
+    ang = parity.angle_between(np.stack(_np(wx, wy, wz)).astype(np.float64), ref)
+    rel = np.abs(pdf.cpu().numpy() / pref - 1.0)
+    print(f"prior: max angle {ang.max():.3e} p99.99 {np.quantile(ang, 0.9999):.3e} "
+          f"tail>4e-6 {(ang > 4e-6).mean():.2e}; pdf max rel {rel.max():.3e} tail>1e-5 {(rel > 1e-5).mean():.2e}")
+    assert np.quantile(ang, 0.999) < 4e-6
+    assert np.quantile(rel, 0.999) < 1e-5
+
+
+def test_pdf_entry_at_given_normals(v):
+    """vndf_pdf against the oracle's density at the same float32 normals."""
+    n = (1 << 18) + 3
+    d = workloads.anisotropic_stream(n=n, seed=35, device=DEV)
+    wx, wy, wz, _ = v.vndf_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], seed=8,
+                                  with_pdf=False)
+    p = v.vndf_pdf(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], wx, wy, wz)
+    wi = np.stack(_np(d["wi_x"], d["wi_y"], d["wi_z"])).astype(np.float64)
+    wm = np.stack(_np(wx, wy, wz)).astype(np.float64)
+    ax, ay = (t.cpu().numpy().astype(np.float64) for t in (d["alpha_x"], d["alpha_y"]))
+    ref = ovndf.vndf_pdf(wm, wi, ax, ay)
+    rel = np.abs(p.cpu().numpy() / ref - 1.0)
+    # the dot product wi.wm cancels for normals near the visibility boundary
+    kd = (np.abs(wi * wm).sum(0) / np.abs(ovndf.dot(wi, wm))) / np.sqrt(ovndf.dot(wi, wi))
+    bound = np.maximum(1e-5, parity.K_ULP * (kd + 8.0) * parity.EPS32)
+    assert np.all(rel <= bound), rel.max()
+    # isotropic form
+    pi = v.vndf_pdf(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], None, wx, wy, wz)
+    refi = ovndf.vndf_pdf(wm, wi, ax, ax)
+    assert np.all(np.abs(pi.cpu().numpy() / refi - 1.0) <= bound)
+
+
+@pytest.mark.slow
+def test_full_size_anisotropic_stream_sampled(v):
+    """2^28 samples in one call (the bench's launch), checked on 2^16 sampled outputs + both ends."""
+    n = 1 << 28
+    d = workloads.anisotropic_stream(n=n, device=DEV)
+    out = v.vndf_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], seed=2)
+    rng = np.random.default_rng(0)
+    idx = np.unique(np.concatenate([np.arange(1024), n - 1 - np.arange(1024), rng.integers(0, n, 1 << 16)]))
+    ti = torch.as_tensor(idx, device=DEV)
+    wi = np.stack([d[k].index_select(0, ti).cpu().numpy() for k in ("wi_x", "wi_y", "wi_z")])
+    ax, ay = (d[k].index_select(0, ti).cpu().numpy() for k in ("alpha_x", "alpha_y"))
+    wm = np.stack([o.index_select(0, ti).cpu().numpy() for o in out[:3]])
+    pdf = out[3].index_select(0, ti).cpu().numpy()
+    u1, u2 = philox.uniforms_at(2, 0, 0, idx)
+    st = parity.compare_cap(wm, pdf, u1, u2, wi, ax, ay)
+    print("full size sampled", st)
+    del d, out
+    torch.cuda.empty_cache()

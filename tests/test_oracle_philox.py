@@ -103,3 +103,11 @@ def test_uniforms_statistically_uniform():
     assert stats.kstest(u1, "uniform").pvalue > 1e-3
     assert stats.kstest(u2, "uniform").pvalue > 1e-3
     assert abs(np.corrcoef(u1, u2)[0, 1]) < 0.02
+
+
+def test_uniforms_at_matches_contiguous_stream():
+    a1, a2 = philox.sample_uniforms(5, 3, 9, 1000)
+    idx = np.array([0, 1, 2, 17, 500, 999, 998])
+    b1, b2 = philox.uniforms_at(5, 3, 9, idx)
+    np.testing.assert_array_equal(a1[idx], b1)
+    np.testing.assert_array_equal(a2[idx], b2)
