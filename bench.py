@@ -45,7 +45,7 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "vndf_sample_cap_anisotropic_strea
 def parse_args():
     p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--log2n", type=int, default=28, help="samples per GPU per step = 2^log2n")
@@ -94,53 +94,104 @@ def hbm_peak():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clock and clock-event reasons sampled every 5 ms during the timed region.
 
-    def __init__(self, gpu_index):
-        self.gpu = gpu_index
-        self.proc = None
-        self.path = None
+    Reads NVML through ctypes (libnvidia-ml ships with the driver); falls back to
+    `nvidia-smi -lms 200` when NVML cannot be loaded.  Read-only: it changes no
+    GPU setting.
+    """
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, torch_device):
+        import threading
+        self.dev = torch_device
+        self.samples = []
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._thread = None
+        self._smi = None
+        self._nvml = self._open_nvml()
+
+    def _open_nvml(self):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            handle = ctypes.c_void_p()
+            bus = None
+            try:
+                import torch
+                props = torch.cuda.get_device_properties(self.dev)
+                bus = "%08x:%02x:%02x.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+            except Exception:
+                bus = None
+            ok = bus is not None and lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(handle)) == 0
+            if not ok and lib.nvmlDeviceGetHandleByIndex_v2(self.dev.index or 0, ctypes.byref(handle)) != 0:
+                return None
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(handle, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = float(mx.value)
+            return lib, handle
+        except OSError:
+            return None
+
+    def _poll(self):
+        import ctypes
+        lib, handle = self._nvml
+        clk = ctypes.c_uint()
+        rs = ctypes.c_ulonglong()
+        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self._stop.is_set():
+            if lib.nvmlDeviceGetClockInfo(handle, 1, ctypes.byref(clk)) == 0:
+                r = rs.value if get_reasons(handle, ctypes.byref(rs)) == 0 else 0
+                self.samples.append((float(clk.value), int(r)))
+            self._stop.wait(0.005)
 
     def start(self):
+        import threading
+        if self._nvml is not None:
+            self._thread = threading.Thread(target=self._poll, daemon=True)
+            self._thread.start()
+            return
         import tempfile
-        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        fd, self._path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            self._smi = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev.index or 0}", "--query-gpu=clocks.sm,clocks.max.sm,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self._path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
-            self.proc = None
+            self._smi = None
 
     def stop(self):
-        if self.proc is None:
+        if self._thread is not None:
+            self._stop.set()
+            self._thread.join()
+            if not self.samples:
+                return None
+            reasons = sorted({name for _, r in self.samples for bit, name in self.REASONS.items() if r & bit})
+            return {"sm_mhz": statistics.median(c for c, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                    "reasons": reasons, "samples": len(self.samples), "source": "nvml 5 ms"}
+        if self._smi is None:
             return None
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                rows.append(parts)
-            except ValueError:
-                pass
-        os.unlink(self.path)
+        self._smi.terminate()
+        self._smi.wait(timeout=5)
+        rows = [[x.strip() for x in line.split(",")] for line in open(self._path)]
+        os.unlink(self._path)
+        rows = [r for r in rows if len(r) >= 6 and r[0].replace(".", "").isdigit()]
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        reasons = sorted({n for r in rows for n, val in zip(names, r[5:9]) if val.lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": reasons, "samples": len(rows)}
+        return {"sm_mhz": statistics.median(float(r[0]) for r in rows),
+                "sm_max_mhz": max(float(r[1]) for r in rows),
+                "reasons": sorted({n for r in rows for n, v in zip(names, r[2:6]) if v.lower() == "active"}),
+                "samples": len(rows), "source": "nvidia-smi 200 ms"}
 
 
 def time_oracle_sample(n, seed=2):
@@ -235,10 +286,9 @@ def run_ours(args, rank, world):
         for _ in range(warmup):
             fn()
         barrier()
-        sampler = ClockSampler(local) if clocks else None
+        sampler = ClockSampler(dev) if clocks else None
         if sampler:
             sampler.start()
-            time.sleep(0.3)
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
         evs[0].record(stream)
         for k in range(steps):

@@ -19,6 +19,7 @@
  *   batch is split into calls.
  * - `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
  *   are asynchronous and allocate no memory.
+ * - n = 0 is a no-op that returns VNDF_OK without examining any pointer.
  * - Host-side argument errors return a negative VNDF_ERR_* code before any
  *   work is enqueued.  A failed launch returns VNDF_ERR_CUDA.  Errors that
  *   happen while the kernel runs surface at the caller's next synchronisation.

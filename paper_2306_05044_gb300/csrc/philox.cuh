@@ -62,21 +62,21 @@ __device__ __forceinline__ void uniforms1(const Rng& r, uint64_t i, float& u1, f
 }
 
 // Uniforms of samples i0 .. i0+3 (i0 a multiple of 4): two Philox calls when the
-// first global index is even, three when it is odd.
+// first global index is even, three when it is odd.  Each block index is taken
+// from its own global index (mod 2^64), so a batch may straddle the wrap.
 __device__ __forceinline__ void uniforms4(const Rng& r, uint64_t i0, float (&u1)[4], float (&u2)[4]) {
   const uint64_t g0 = r.base + i0;
-  const uint64_t b0 = g0 >> 1;
   if ((g0 & 1u) == 0) {
-    const uint4 a = philox_block(r, b0);
-    const uint4 b = philox_block(r, b0 + 1);
+    const uint4 a = philox_block(r, g0 >> 1);
+    const uint4 b = philox_block(r, (g0 + 2) >> 1);
     u1[0] = word_to_unit(a.x); u2[0] = word_to_unit(a.y);
     u1[1] = word_to_unit(a.z); u2[1] = word_to_unit(a.w);
     u1[2] = word_to_unit(b.x); u2[2] = word_to_unit(b.y);
     u1[3] = word_to_unit(b.z); u2[3] = word_to_unit(b.w);
   } else {
-    const uint4 a = philox_block(r, b0);
-    const uint4 b = philox_block(r, b0 + 1);
-    const uint4 c = philox_block(r, b0 + 2);
+    const uint4 a = philox_block(r, g0 >> 1);
+    const uint4 b = philox_block(r, (g0 + 1) >> 1);
+    const uint4 c = philox_block(r, (g0 + 3) >> 1);
     u1[0] = word_to_unit(a.z); u2[0] = word_to_unit(a.w);
     u1[1] = word_to_unit(b.x); u2[1] = word_to_unit(b.y);
     u1[2] = word_to_unit(b.z); u2[2] = word_to_unit(b.w);

@@ -191,9 +191,9 @@ using namespace vndf;
 extern "C" int vndf_rng_uniform(int64_t n, uint64_t seed, uint64_t counter_base, uint32_t stream_id, float* u1,
                                 float* u2, void* cuda_stream) {
   if (n < 0 || n >= kMaxN) return VNDF_ERR_SIZE;
+  if (n == 0) return VNDF_OK;
   if (!u1 || !u2) return VNDF_ERR_NULL;
   if (!all_aligned4(u1, u2)) return VNDF_ERR_ALIGN;
-  if (n == 0) return VNDF_OK;
   const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const Rng r = make_rng(seed, counter_base, stream_id);
   int64_t done = 0;
@@ -212,10 +212,10 @@ extern "C" int vndf_sample(int64_t n, const float* wi_x, const float* wi_y, cons
                            float* wm_y, float* wm_z, float* pdf, void* cuda_stream) {
   if (n < 0 || n >= kMaxN) return VNDF_ERR_SIZE;
   if (method != VNDF_METHOD_SPHERICAL_CAP && method != VNDF_METHOD_POLAR_DISK) return VNDF_ERR_METHOD;
+  if (n == 0) return VNDF_OK;
   if (!wi_x || !wi_y || !wi_z || !alpha_x || !wm_x || !wm_y || !wm_z) return VNDF_ERR_NULL;
   if ((u1 == nullptr) != (u2 == nullptr)) return VNDF_ERR_ARG;
   if (!all_aligned4(wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, wm_x, wm_y, wm_z, pdf)) return VNDF_ERR_ALIGN;
-  if (n == 0) return VNDF_OK;
   SampleArgs a{wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, wm_x, wm_y, wm_z, pdf,
                make_rng(seed, counter_base, stream_id)};
   const bool vec = all_aligned16(wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, wm_x, wm_y, wm_z, pdf);
@@ -228,9 +228,9 @@ extern "C" int vndf_pdf(int64_t n, const float* wi_x, const float* wi_y, const f
                         const float* alpha_y, const float* wm_x, const float* wm_y, const float* wm_z, float* pdf,
                         void* cuda_stream) {
   if (n < 0 || n >= kMaxN) return VNDF_ERR_SIZE;
+  if (n == 0) return VNDF_OK;
   if (!wi_x || !wi_y || !wi_z || !alpha_x || !wm_x || !wm_y || !wm_z || !pdf) return VNDF_ERR_NULL;
   if (!all_aligned4(wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf)) return VNDF_ERR_ALIGN;
-  if (n == 0) return VNDF_OK;
   const bool vec = all_aligned16(wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf);
   const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   return alpha_y ? launch_pdf<false>(n, wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf, vec, s)
