@@ -53,6 +53,8 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-prior", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--no-fwd-bwd", action="store_true")
+    p.add_argument("--log2n-adjoint", type=int, default=24)
     return p.parse_args()
 
 
@@ -338,6 +340,10 @@ def run_ours(args, rank, world):
             "cap_over_prior": value / pv}
         result["gpu_launches_prior"] = steps
 
+    if not args.no_fwd_bwd:
+        result["fwd_bwd"] = fwd_bwd(vndf, dev, rank, world, timed, peak, args.log2n_adjoint)
+        result["gpu_launches_fwd_bwd"] = 2 * steps
+
     if not args.no_e2e:
         result["e2e"] = e2e(vndf, d, n, base, dev, stream, steps, warm, barrier, world)
 
@@ -345,6 +351,32 @@ def run_ours(args, rank, world):
         result["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         emit(result)
+
+
+def fwd_bwd(vndf, dev, rank, world, timed, peak, log2n):
+    """Fused forward + loss + adjoint on the 2^24-sample adjoint workload (52 B/sample)."""
+    import torch
+
+    import workloads
+    n = 1 << log2n
+    d = workloads.adjoint_2e24(n=n, device=dev)
+    outs = (torch.empty(1, device=dev), *(torch.empty(n, device=dev) for _ in range(5)))
+    ws = torch.empty(max(vndf.vndf_loss_workspace_bytes(n), 4), dtype=torch.uint8, device=dev)
+
+    def step():
+        vndf.vndf_sample_loss_backward(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], d["c_x"],
+                                       d["c_y"], d["c_z"], seed=4, counter_base=rank * n, workspace=ws,
+                                       outputs=outs)
+
+    steps = 100
+    total, per, _ = timed(step, steps, 5)
+    ms = total / steps
+    del d
+    return {"workload": f"adjoint_2e{log2n}", "value": world * n / (ms * 1e-3) / 1e9, "unit": UNIT,
+            "ms_per_step": ms, "steps": steps,
+            "hbm": {"algorithmic_bytes": 52 * n, "achieved_gbs": 52 * n / (ms * 1e-3) / 1e9,
+                    "frac": 52 * n / (ms * 1e-3) / 1e9 / peak},
+            "kernels": "loss_backward_kernel + sum_partials_kernel"}
 
 
 def e2e(vndf, d, n, base, dev, stream, steps, warm, barrier, world):

@@ -122,6 +122,71 @@ int vndf_pdf(int64_t n,
              const float *wm_x, const float *wm_y, const float *wm_z,
              float *pdf, void *cuda_stream);
 
+/*
+ * vndf_sample_backward -- reparameterised gradients of the spherical-cap
+ * sampler and its fused pdf (vndf_sample with VNDF_METHOD_SPHERICAL_CAP):
+ * the vector-Jacobian product of (wm, pdf) with respect to (wi, alpha_x,
+ * alpha_y), with the uniforms u held fixed.  The paper gives the forward map
+ * (Sec. 2 steps (1)-(3), Sec. 3.3, Eq. 1); this is its exact adjoint, computed
+ * by recomputing the forward in registers (nothing is stored between calls).
+ *   n, wi_*, alpha_*, u1, u2, seed, counter_base, stream_id
+ *                       exactly as given to vndf_sample (same u for the same i).
+ *   g_wm_x, g_wm_y, g_wm_z  adjoint of wm (all three NULL = zero).
+ *   g_pdf               adjoint of pdf (NULL = zero).
+ *   g_wi_x, g_wi_y, g_wi_z  outputs d/d wi (all three NULL = not written).
+ *   g_alpha_x           output d/d alpha_x (NULL = not written); with an
+ *                       isotropic call (alpha_y = NULL) it receives d/d alpha.
+ *   g_alpha_y           output d/d alpha_y (NULL = not written; must be NULL
+ *                       when alpha_y is NULL).
+ * Samples outside the domain get zero gradients.  Because the sampler is
+ * invariant to the scale of wi, g_wi . wi = 0 up to rounding.
+ * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, ALIGN, ARG, CUDA).
+ */
+int vndf_sample_backward(int64_t n,
+                         const float *wi_x, const float *wi_y, const float *wi_z,
+                         const float *alpha_x, const float *alpha_y,
+                         const float *u1, const float *u2,
+                         uint64_t seed, uint64_t counter_base, uint32_t stream_id,
+                         const float *g_wm_x, const float *g_wm_y, const float *g_wm_z,
+                         const float *g_pdf,
+                         float *g_wi_x, float *g_wi_y, float *g_wi_z,
+                         float *g_alpha_x, float *g_alpha_y,
+                         void *cuda_stream);
+
+/* Device workspace (bytes) that vndf_sample_loss_backward needs for n samples:
+ * one float per 1024-sample chunk.  0 for n <= 0. */
+size_t vndf_loss_workspace_bytes(int64_t n);
+
+/*
+ * vndf_sample_loss_backward -- fused forward, loss and adjoint for the
+ * reparameterised objective
+ *   loss = sum_i ( c_i . wm_i + log pdf_i )
+ * over the spherical-cap samples of vndf_sample (Sec. 2, Sec. 3.3, Eq. 1):
+ * writes the loss and its gradients with respect to wi and alpha in one pass
+ * (g_wm = c and d loss / d log pdf = 1 per sample).  Samples outside the
+ * domain contribute nothing and get zero gradients.
+ *   c_x, c_y, c_z       per-sample weight vectors (device).
+ *   g_wi_*, g_alpha_*   outputs as in vndf_sample_backward (NULL = skip).
+ *   loss                output, one float (device).  It is summed per fixed
+ *                       1024-sample chunk and then over chunks in index
+ *                       order, so it is bit-reproducible for a given n.
+ *   workspace           device scratch of >= vndf_loss_workspace_bytes(n)
+ *                       bytes, owned by the caller; its contents on entry are
+ *                       ignored.  Concurrent calls need separate workspaces.
+ * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, ALIGN, ARG,
+ * WORKSPACE, CUDA).
+ */
+int vndf_sample_loss_backward(int64_t n,
+                              const float *wi_x, const float *wi_y, const float *wi_z,
+                              const float *alpha_x, const float *alpha_y,
+                              const float *c_x, const float *c_y, const float *c_z,
+                              const float *u1, const float *u2,
+                              uint64_t seed, uint64_t counter_base, uint32_t stream_id,
+                              float *g_wi_x, float *g_wi_y, float *g_wi_z,
+                              float *g_alpha_x, float *g_alpha_y,
+                              float *loss, void *workspace, size_t workspace_bytes,
+                              void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -36,6 +36,11 @@ SIGNATURES = {
     "vndf_sample": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _U64, _U64, _U32, ctypes.c_int,
                                    _P, _P, _P, _P, _P]),
     "vndf_pdf": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "vndf_sample_backward": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _U64, _U64, _U32,
+                                            _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "vndf_loss_workspace_bytes": (_SZ, [_I64]),
+    "vndf_sample_loss_backward": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _U64, _U64, _U32,
+                                                 _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
 }
 
 
@@ -162,3 +167,55 @@ def vndf_pdf(wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf=None, n=N
                          _stream(stream, wi_x.device))
     _check("vndf_pdf", st)
     return pdf
+
+
+def vndf_sample_backward(wi_x, wi_y, wi_z, alpha_x, alpha_y=None, u1=None, u2=None, seed=0, counter_base=0,
+                         stream_id=0, g_wm_x=None, g_wm_y=None, g_wm_z=None, g_pdf=None, want_wi=True,
+                         want_alpha=True, n=None, stream=None):
+    """Gradients of (wm, pdf) w.r.t. (wi, alpha) for fixed u; see vndf_sample_backward in include/vndf.h.
+
+    Returns (g_wi_x, g_wi_y, g_wi_z, g_alpha_x, g_alpha_y); entries not requested are None.
+    With alpha_y=None (isotropic) g_alpha_x holds d/d alpha and g_alpha_y is None.
+    """
+    n = wi_x.numel() if n is None else int(n)
+    g_wi = [_out(None, n, wi_x) for _ in range(3)] if want_wi else [None, None, None]
+    g_ax = _out(None, n, wi_x) if want_alpha else None
+    g_ay = _out(None, n, wi_x) if (want_alpha and alpha_y is not None) else None
+    st = load().vndf_sample_backward(
+        n, _ptr(wi_x, "wi_x"), _ptr(wi_y, "wi_y"), _ptr(wi_z, "wi_z"), _ptr(alpha_x, "alpha_x"),
+        _ptr(alpha_y, "alpha_y"), _ptr(u1, "u1"), _ptr(u2, "u2"), int(seed) & (2**64 - 1),
+        int(counter_base) & (2**64 - 1), int(stream_id) & 0xFFFFFFFF, _ptr(g_wm_x, "g_wm_x"),
+        _ptr(g_wm_y, "g_wm_y"), _ptr(g_wm_z, "g_wm_z"), _ptr(g_pdf, "g_pdf"), _ptr(g_wi[0], "g_wi_x"),
+        _ptr(g_wi[1], "g_wi_y"), _ptr(g_wi[2], "g_wi_z"), _ptr(g_ax, "g_alpha_x"), _ptr(g_ay, "g_alpha_y"),
+        _stream(stream, wi_x.device))
+    _check("vndf_sample_backward", st)
+    return g_wi[0], g_wi[1], g_wi[2], g_ax, g_ay
+
+
+def vndf_loss_workspace_bytes(n):
+    return int(load().vndf_loss_workspace_bytes(int(n)))
+
+
+def vndf_sample_loss_backward(wi_x, wi_y, wi_z, alpha_x, alpha_y, c_x, c_y, c_z, u1=None, u2=None, seed=0,
+                              counter_base=0, stream_id=0, workspace=None, outputs=None, n=None, stream=None):
+    """Fused forward + loss + adjoint of loss = sum(c . wm + log pdf); returns (loss, g_wi_x, g_wi_y, g_wi_z,
+    g_alpha_x, g_alpha_y).  ``outputs`` may pass preallocated (loss, g_wi_x, g_wi_y, g_wi_z, g_alpha_x,
+    g_alpha_y); ``workspace`` a uint8 device tensor of at least vndf_loss_workspace_bytes(n) bytes."""
+    n = wi_x.numel() if n is None else int(n)
+    if outputs is None:
+        outputs = (torch.empty(1, dtype=torch.float32, device=wi_x.device),
+                   *(_out(None, n, wi_x) for _ in range(4)),
+                   _out(None, n, wi_x) if alpha_y is not None else None)
+    loss, gx, gy, gz, gax, gay = outputs
+    need = vndf_loss_workspace_bytes(n)
+    if workspace is None:
+        workspace = torch.empty(max(need, 4), dtype=torch.uint8, device=wi_x.device)
+    st = load().vndf_sample_loss_backward(
+        n, _ptr(wi_x, "wi_x"), _ptr(wi_y, "wi_y"), _ptr(wi_z, "wi_z"), _ptr(alpha_x, "alpha_x"),
+        _ptr(alpha_y, "alpha_y"), _ptr(c_x, "c_x"), _ptr(c_y, "c_y"), _ptr(c_z, "c_z"), _ptr(u1, "u1"),
+        _ptr(u2, "u2"), int(seed) & (2**64 - 1), int(counter_base) & (2**64 - 1), int(stream_id) & 0xFFFFFFFF,
+        _ptr(gx, "g_wi_x"), _ptr(gy, "g_wi_y"), _ptr(gz, "g_wi_z"), _ptr(gax, "g_alpha_x"),
+        _ptr(gay, "g_alpha_y"), _ptr(loss, "loss"), _ptr(workspace, "workspace", torch.uint8),
+        int(workspace.numel()), _stream(stream, wi_x.device))
+    _check("vndf_sample_loss_backward", st)
+    return loss, gx, gy, gz, gax, gay

@@ -1,0 +1,333 @@
+// Adjoint kernels of the spherical-cap sampler (reparameterised gradients):
+//   vndf_sample_backward        generic vector-Jacobian product of (wm, pdf)
+//   vndf_sample_loss_backward   fused forward + loss + adjoint for
+//                               loss = sum_i (c_i . wm_i + log pdf_i)
+// Both recompute the forward in registers (no stored tape) and share the
+// per-sample adjoint in vndf_adjoint.cuh.  The fused kernel reduces the loss
+// per fixed 1024-sample chunk, and a one-block kernel sums the chunk partials
+// in index order, so the loss is bit-reproducible and independent of the grid.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "philox.cuh"
+#include "vndf_adjoint.cuh"
+
+namespace vndf {
+
+constexpr int kBwdBlock = 256;
+constexpr int kChunk = 4 * kBwdBlock;  // samples per loss partial
+
+struct BwdArgs {
+  const float *wx, *wy, *wz, *ax, *ay, *u1, *u2;
+  const float *gmx, *gmy, *gmz, *gp;  // adjoints (generic) or c (fused: gmx..gmz)
+  float *gwx, *gwy, *gwz, *gax, *gay;
+  Rng rng;
+};
+
+__device__ __forceinline__ void load4(const float* p, int64_t e, float (&d)[4]) {
+  *reinterpret_cast<float4*>(d) = ld_stream(p + e);
+}
+__device__ __forceinline__ void store4(float* p, int64_t e, const float (&d)[4]) {
+  st_stream(p + e, *reinterpret_cast<const float4*>(d));
+}
+
+template <bool PHILOX, bool ISO>
+__global__ void __launch_bounds__(kBwdBlock) backward_vec4_kernel(BwdArgs a, int64_t n4) {
+  const int64_t stride = int64_t(gridDim.x) * kBwdBlock;
+  for (int64_t q = int64_t(blockIdx.x) * kBwdBlock + threadIdx.x; q < n4; q += stride) {
+    const int64_t e = 4 * q;
+    float X[4], Y[4], Z[4], AX[4], AY[4], U1[4], U2[4];
+    float GX[4] = {0.f, 0.f, 0.f, 0.f}, GY[4] = {0.f, 0.f, 0.f, 0.f}, GZ[4] = {0.f, 0.f, 0.f, 0.f};
+    float GP[4] = {0.f, 0.f, 0.f, 0.f};
+    load4(a.wx, e, X);
+    load4(a.wy, e, Y);
+    load4(a.wz, e, Z);
+    load4(a.ax, e, AX);
+    if constexpr (ISO) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) AY[k] = AX[k];
+    } else {
+      load4(a.ay, e, AY);
+    }
+    if constexpr (PHILOX) {
+      uniforms4(a.rng, uint64_t(e), U1, U2);
+    } else {
+      load4(a.u1, e, U1);
+      load4(a.u2, e, U2);
+    }
+    if (a.gmx) {
+      load4(a.gmx, e, GX);
+      load4(a.gmy, e, GY);
+      load4(a.gmz, e, GZ);
+    }
+    if (a.gp) load4(a.gp, e, GP);
+    float OWX[4], OWY[4], OWZ[4], OAX[4], OAY[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float mx, my, mz, pdf;
+      const Grad5 g = cap_backward_one(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], GX[k], GY[k], GZ[k], GP[k],
+                                       0.f, mx, my, mz, pdf);
+      OWX[k] = g.wx;
+      OWY[k] = g.wy;
+      OWZ[k] = g.wz;
+      OAX[k] = ISO ? g.ax + g.ay : g.ax;
+      OAY[k] = g.ay;
+    }
+    if (a.gwx) {
+      store4(a.gwx, e, OWX);
+      store4(a.gwy, e, OWY);
+      store4(a.gwz, e, OWZ);
+    }
+    if (a.gax) store4(a.gax, e, OAX);
+    if (!ISO && a.gay) store4(a.gay, e, OAY);
+  }
+}
+
+template <bool PHILOX, bool ISO>
+__global__ void __launch_bounds__(kBwdBlock) backward_scalar_kernel(BwdArgs a, int64_t begin, int64_t n) {
+  const int64_t stride = int64_t(gridDim.x) * kBwdBlock;
+  for (int64_t e = begin + int64_t(blockIdx.x) * kBwdBlock + threadIdx.x; e < n; e += stride) {
+    const float ax = a.ax[e];
+    const float ay = ISO ? ax : a.ay[e];
+    float u1, u2;
+    if constexpr (PHILOX) {
+      uniforms1(a.rng, uint64_t(e), u1, u2);
+    } else {
+      u1 = a.u1[e];
+      u2 = a.u2[e];
+    }
+    const float gx = a.gmx ? a.gmx[e] : 0.f, gy = a.gmx ? a.gmy[e] : 0.f, gz = a.gmx ? a.gmz[e] : 0.f;
+    float mx, my, mz, pdf;
+    const Grad5 g = cap_backward_one(a.wx[e], a.wy[e], a.wz[e], ax, ay, u1, u2, gx, gy, gz,
+                                     a.gp ? a.gp[e] : 0.f, 0.f, mx, my, mz, pdf);
+    if (a.gwx) {
+      a.gwx[e] = g.wx;
+      a.gwy[e] = g.wy;
+      a.gwz[e] = g.wz;
+    }
+    if (a.gax) a.gax[e] = ISO ? g.ax + g.ay : g.ax;
+    if (!ISO && a.gay) a.gay[e] = g.ay;
+  }
+}
+
+// ---------------------------------------------------------------- fused loss + adjoint
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum in a fixed order (warp butterflies, then warp 0 over the warp sums).
+template <int BLOCK>
+__device__ __forceinline__ float block_sum(float v, float* smem) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) smem[w] = v;
+  __syncthreads();
+  float r = 0.f;
+  if (w == 0) {
+    r = l < BLOCK / 32 ? smem[l] : 0.f;
+    r = warp_sum(r);
+  }
+  __syncthreads();
+  return r;  // valid in thread 0
+}
+
+template <bool PHILOX, bool ISO, bool VEC>
+__global__ void __launch_bounds__(kBwdBlock) loss_backward_kernel(BwdArgs a, int64_t n, int64_t chunks,
+                                                                  float* partials) {
+  __shared__ float smem[kBwdBlock / 32];
+  for (int64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
+    const int64_t e = ch * kChunk + 4 * int64_t(threadIdx.x);
+    float X[4], Y[4], Z[4], AX[4], AY[4], U1[4], U2[4], CX[4], CY[4], CZ[4];
+    const bool full = VEC && e + 3 < n;
+    if (full) {
+      load4(a.wx, e, X);
+      load4(a.wy, e, Y);
+      load4(a.wz, e, Z);
+      load4(a.ax, e, AX);
+      if constexpr (ISO) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) AY[k] = AX[k];
+      } else {
+        load4(a.ay, e, AY);
+      }
+      load4(a.gmx, e, CX);
+      load4(a.gmy, e, CY);
+      load4(a.gmz, e, CZ);
+      if constexpr (!PHILOX) {
+        load4(a.u1, e, U1);
+        load4(a.u2, e, U2);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const bool in = e + k < n;
+        X[k] = in ? a.wx[e + k] : 0.f;
+        Y[k] = in ? a.wy[e + k] : 0.f;
+        Z[k] = in ? a.wz[e + k] : 0.f;  // wz = 0: out of domain, contributes nothing
+        AX[k] = in ? a.ax[e + k] : 1.f;
+        AY[k] = ISO ? AX[k] : (in ? a.ay[e + k] : 1.f);
+        CX[k] = in ? a.gmx[e + k] : 0.f;
+        CY[k] = in ? a.gmy[e + k] : 0.f;
+        CZ[k] = in ? a.gmz[e + k] : 0.f;
+        if constexpr (!PHILOX) {
+          U1[k] = in ? a.u1[e + k] : 0.f;
+          U2[k] = in ? a.u2[e + k] : 0.f;
+        }
+      }
+    }
+    if constexpr (PHILOX) {
+      if (full) {
+        uniforms4(a.rng, uint64_t(e), U1, U2);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) uniforms1(a.rng, uint64_t(e + k), U1[k], U2[k]);
+      }
+    }
+    float OWX[4], OWY[4], OWZ[4], OAX[4], OAY[4];
+    float local = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float mx, my, mz, pdf;
+      const Grad5 g = cap_backward_one(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], CX[k], CY[k], CZ[k], 0.f,
+                                       1.f, mx, my, mz, pdf);
+      const bool ok = pdf > 0.f;
+      local += ok ? fmaf(CX[k], mx, fmaf(CY[k], my, fmaf(CZ[k], mz, logf(pdf)))) : 0.f;
+      OWX[k] = g.wx;
+      OWY[k] = g.wy;
+      OWZ[k] = g.wz;
+      OAX[k] = ISO ? g.ax + g.ay : g.ax;
+      OAY[k] = g.ay;
+    }
+    if (full) {
+      if (a.gwx) {
+        store4(a.gwx, e, OWX);
+        store4(a.gwy, e, OWY);
+        store4(a.gwz, e, OWZ);
+      }
+      if (a.gax) store4(a.gax, e, OAX);
+      if (!ISO && a.gay) store4(a.gay, e, OAY);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (e + k < n) {
+          if (a.gwx) {
+            a.gwx[e + k] = OWX[k];
+            a.gwy[e + k] = OWY[k];
+            a.gwz[e + k] = OWZ[k];
+          }
+          if (a.gax) a.gax[e + k] = OAX[k];
+          if (!ISO && a.gay) a.gay[e + k] = OAY[k];
+        }
+      }
+    }
+    const float s = block_sum<kBwdBlock>(local, smem);
+    if (threadIdx.x == 0) partials[ch] = s;
+  }
+}
+
+// One block: thread t sums partials t, t + 1024, ... in order, then a fixed tree.
+__global__ void __launch_bounds__(1024) sum_partials_kernel(const float* partials, int64_t m, float* out) {
+  __shared__ float smem[32];
+  float v = 0.f;
+  for (int64_t j = threadIdx.x; j < m; j += 1024) v += partials[j];
+  const float s = block_sum<1024>(v, smem);
+  if (threadIdx.x == 0) *out = s;
+}
+
+template <bool PHILOX, bool ISO>
+int launch_backward(const BwdArgs& a, int64_t n, bool vec, cudaStream_t s) {
+  int64_t done = 0;
+  if (vec && n / 4 > 0) {
+    const int64_t n4 = n / 4;
+    backward_vec4_kernel<PHILOX, ISO><<<grid_for(n4, kBwdBlock, 8, 32), kBwdBlock, 0, s>>>(a, n4);
+    done = 4 * n4;
+  }
+  if (done < n)
+    backward_scalar_kernel<PHILOX, ISO><<<grid_for(n - done, kBwdBlock, 8, 32), kBwdBlock, 0, s>>>(a, done, n);
+  return launch_status();
+}
+
+template <bool PHILOX, bool ISO>
+int launch_loss(const BwdArgs& a, int64_t n, bool vec, float* partials, float* loss, cudaStream_t s) {
+  const int64_t chunks = (n + kChunk - 1) / kChunk;
+  const unsigned grid = grid_for(chunks * kBwdBlock, kBwdBlock, 8, 16);
+  if (vec)
+    loss_backward_kernel<PHILOX, ISO, true><<<grid, kBwdBlock, 0, s>>>(a, n, chunks, partials);
+  else
+    loss_backward_kernel<PHILOX, ISO, false><<<grid, kBwdBlock, 0, s>>>(a, n, chunks, partials);
+  sum_partials_kernel<<<1, 1024, 0, s>>>(partials, chunks, loss);
+  return launch_status();
+}
+
+}  // namespace vndf
+
+using namespace vndf;
+
+extern "C" int vndf_sample_backward(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z,
+                                    const float* alpha_x, const float* alpha_y, const float* u1, const float* u2,
+                                    uint64_t seed, uint64_t counter_base, uint32_t stream_id, const float* g_wm_x,
+                                    const float* g_wm_y, const float* g_wm_z, const float* g_pdf, float* g_wi_x,
+                                    float* g_wi_y, float* g_wi_z, float* g_alpha_x, float* g_alpha_y,
+                                    void* cuda_stream) {
+  if (n < 0 || n >= kMaxN) return VNDF_ERR_SIZE;
+  if (n == 0) return VNDF_OK;
+  if (!wi_x || !wi_y || !wi_z || !alpha_x) return VNDF_ERR_NULL;
+  if ((u1 == nullptr) != (u2 == nullptr)) return VNDF_ERR_ARG;
+  const int gwm_count = (g_wm_x != nullptr) + (g_wm_y != nullptr) + (g_wm_z != nullptr);
+  const int gwi_count = (g_wi_x != nullptr) + (g_wi_y != nullptr) + (g_wi_z != nullptr);
+  if (gwm_count != 0 && gwm_count != 3) return VNDF_ERR_ARG;
+  if (gwi_count != 0 && gwi_count != 3) return VNDF_ERR_ARG;
+  if (alpha_y == nullptr && g_alpha_y != nullptr) return VNDF_ERR_ARG;
+  if (!all_aligned4(wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, g_wm_x, g_wm_y, g_wm_z, g_pdf, g_wi_x, g_wi_y,
+                    g_wi_z, g_alpha_x, g_alpha_y))
+    return VNDF_ERR_ALIGN;
+  BwdArgs a{wi_x,   wi_y,   wi_z,   alpha_x, alpha_y,   u1,        u2,       g_wm_x,
+            g_wm_y, g_wm_z, g_pdf,  g_wi_x,  g_wi_y,    g_wi_z,    g_alpha_x, g_alpha_y,
+            make_rng(seed, counter_base, stream_id)};
+  const bool vec = all_aligned16(wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, g_wm_x, g_wm_y, g_wm_z, g_pdf,
+                                 g_wi_x, g_wi_y, g_wi_z, g_alpha_x, g_alpha_y);
+  const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (u1)
+    return alpha_y ? launch_backward<false, false>(a, n, vec, s) : launch_backward<false, true>(a, n, vec, s);
+  return alpha_y ? launch_backward<true, false>(a, n, vec, s) : launch_backward<true, true>(a, n, vec, s);
+}
+
+extern "C" size_t vndf_loss_workspace_bytes(int64_t n) {
+  if (n <= 0) return 0;
+  return size_t((n + kChunk - 1) / kChunk) * sizeof(float);
+}
+
+extern "C" int vndf_sample_loss_backward(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z,
+                                         const float* alpha_x, const float* alpha_y, const float* c_x,
+                                         const float* c_y, const float* c_z, const float* u1, const float* u2,
+                                         uint64_t seed, uint64_t counter_base, uint32_t stream_id, float* g_wi_x,
+                                         float* g_wi_y, float* g_wi_z, float* g_alpha_x, float* g_alpha_y,
+                                         float* loss, void* workspace, size_t workspace_bytes,
+                                         void* cuda_stream) {
+  if (n < 0 || n >= kMaxN) return VNDF_ERR_SIZE;
+  if (!loss) return VNDF_ERR_NULL;
+  const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (n == 0) return cudaMemsetAsync(loss, 0, sizeof(float), s) == cudaSuccess ? VNDF_OK : VNDF_ERR_CUDA;
+  if (!wi_x || !wi_y || !wi_z || !alpha_x || !c_x || !c_y || !c_z) return VNDF_ERR_NULL;
+  if ((u1 == nullptr) != (u2 == nullptr)) return VNDF_ERR_ARG;
+  const int gwi_count = (g_wi_x != nullptr) + (g_wi_y != nullptr) + (g_wi_z != nullptr);
+  if (gwi_count != 0 && gwi_count != 3) return VNDF_ERR_ARG;
+  if (alpha_y == nullptr && g_alpha_y != nullptr) return VNDF_ERR_ARG;
+  if (!workspace || workspace_bytes < vndf_loss_workspace_bytes(n)) return VNDF_ERR_WORKSPACE;
+  if (!all_aligned4(wi_x, wi_y, wi_z, alpha_x, alpha_y, c_x, c_y, c_z, u1, u2, g_wi_x, g_wi_y, g_wi_z,
+                    g_alpha_x, g_alpha_y, loss, workspace))
+    return VNDF_ERR_ALIGN;
+  BwdArgs a{wi_x, wi_y,   wi_z,   alpha_x, alpha_y,   u1,        u2,       c_x,
+            c_y,  c_z,    nullptr, g_wi_x, g_wi_y,    g_wi_z,    g_alpha_x, g_alpha_y,
+            make_rng(seed, counter_base, stream_id)};
+  const bool vec = all_aligned16(wi_x, wi_y, wi_z, alpha_x, alpha_y, c_x, c_y, c_z, u1, u2, g_wi_x, g_wi_y,
+                                 g_wi_z, g_alpha_x, g_alpha_y);
+  float* partials = static_cast<float*>(workspace);
+  if (u1)
+    return alpha_y ? launch_loss<false, false>(a, n, vec, partials, loss, s)
+                   : launch_loss<false, true>(a, n, vec, partials, loss, s);
+  return alpha_y ? launch_loss<true, false>(a, n, vec, partials, loss, s)
+                 : launch_loss<true, true>(a, n, vec, partials, loss, s);
+}

@@ -1,0 +1,178 @@
+"""GPU parity of the adjoint kernels against the oracle's complex-step derivatives.
+
+The reference gradient is the oracle's vector-Jacobian product (oracle.grad,
+complex step through Sec. 2 / Sec. 3.3 / Eq. 1 in FP64), pinned against
+central differences on the CPU.  Per sample the error is measured against the
+largest reference component, e = max_k |g_k - r_k| / max_k |r_k|.  Like the
+forward, the adjoint inherits the conditioning of h = c + i, so a small tail
+of ill-conditioned samples is reported rather than bounded by a flat limit.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import grad, philox, vndf as ovndf
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def v():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2306_05044_gb300 as lib
+    return lib
+
+
+def _np(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def _errors(gpu, ref):
+    scale = np.abs(ref).max(axis=0)
+    return np.abs(gpu - ref).max(axis=0) / np.maximum(scale, 1e-30)
+
+
+def _check_errors(e, label):
+    print(f"{label}: median {np.median(e):.2e} p99.9 {np.quantile(e, 0.999):.2e} max {e.max():.2e} "
+          f"frac>1e-3 {(e > 1e-3).mean():.2e}")
+    assert np.median(e) < 1e-5
+    assert np.quantile(e, 0.999) < 1e-3
+
+
+@pytest.mark.parametrize("iso,explicit", [(False, False), (True, False), (False, True)])
+def test_backward_matches_complex_step(v, iso, explicit):
+    n = (1 << 16) + 3
+    d = workloads.adjoint_2e24(n=n, device=DEV)
+    g = torch.Generator(device=DEV).manual_seed(9)
+    gwm = [torch.randn(n, generator=g, device=DEV) for _ in range(3)]
+    gp = torch.randn(n, generator=g, device=DEV)
+    ay = None if iso else d["alpha_y"]
+    if explicit:
+        u1n, u2n = philox.sample_uniforms(123, 0, 0, n)
+        u1 = torch.as_tensor(u1n.astype(np.float32), device=DEV)
+        u2 = torch.as_tensor(u2n.astype(np.float32), device=DEV)
+        kw = dict(u1=u1, u2=u2)
+    else:
+        u1n, u2n = philox.sample_uniforms(4, 5, 0, n)
+        kw = dict(seed=4, counter_base=5)
+    gx, gy, gz, gax, gay = v.vndf_sample_backward(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], ay,
+                                                  g_wm_x=gwm[0], g_wm_y=gwm[1], g_wm_z=gwm[2], g_pdf=gp, **kw)
+    wi = np.stack([_np(d[k]) for k in ("wi_x", "wi_y", "wi_z")])
+    axn = _np(d["alpha_x"])
+    ayn = axn if iso else _np(d["alpha_y"])
+    rwi, rax, ray = grad.vjp(u1n, u2n, wi, axn, ayn, np.stack([_np(t) for t in gwm]), _np(gp), isotropic=iso)
+    if iso:
+        ref = np.concatenate([rwi, rax[None]])
+        got = np.stack([_np(gx), _np(gy), _np(gz), _np(gax)])
+        assert gay is None
+    else:
+        ref = np.concatenate([rwi, rax[None], ray[None]])
+        got = np.stack([_np(gx), _np(gy), _np(gz), _np(gax), _np(gay)])
+    _check_errors(_errors(got, ref), f"backward iso={iso} explicit={explicit}")
+    # the sampler is invariant to the scale of wi
+    gw = got[:3]
+    hom = np.abs((gw * wi).sum(0)) / (np.sqrt((gw ** 2).sum(0)) * np.sqrt((wi ** 2).sum(0)) + 1e-30)
+    assert np.quantile(hom, 0.999) < 1e-3
+
+
+def test_backward_optional_outputs_and_inputs(v):
+    n = 4099
+    d = workloads.adjoint_2e24(n=n, seed=40, device=DEV)
+    gp = torch.ones(n, device=DEV)
+    full = v.vndf_sample_backward(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], seed=1, g_pdf=gp)
+    only_a = v.vndf_sample_backward(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], seed=1,
+                                    g_pdf=gp, want_wi=False)
+    assert only_a[0] is None
+    assert torch.equal(full[3], only_a[3]) and torch.equal(full[4], only_a[4])
+    # no adjoint at all: zero gradients
+    z = v.vndf_sample_backward(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], seed=1)
+    for t in z:
+        assert torch.count_nonzero(t) == 0
+
+
+def test_fused_loss_matches_oracle(v):
+    n = (1 << 20) + 7
+    d = workloads.adjoint_2e24(n=n, device=DEV)
+    loss, gx, gy, gz, gax, gay = v.vndf_sample_loss_backward(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"],
+                                                             d["alpha_y"], d["c_x"], d["c_y"], d["c_z"], seed=4)
+    loss2 = v.vndf_sample_loss_backward(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], d["c_x"],
+                                        d["c_y"], d["c_z"], seed=4)[0]
+    assert torch.equal(loss, loss2)  # deterministic
+    u1, u2 = philox.sample_uniforms(4, 0, 0, n)
+    wi = np.stack([_np(d[k]) for k in ("wi_x", "wi_y", "wi_z")])
+    ax, ay = _np(d["alpha_x"]), _np(d["alpha_y"])
+    c = np.stack([_np(d[k]) for k in ("c_x", "c_y", "c_z")])
+    wm, pdf = ovndf.sample_vndf_with_pdf(u1, u2, wi, ax, ay)
+    terms = ovndf.dot(c, wm) + np.log(pdf)
+    ref = terms.sum()
+    got = float(loss.item())
+    print(f"loss gpu {got:.8e} oracle {ref:.8e} rel {abs(got / ref - 1):.2e}")
+    assert abs(got - ref) <= 1e-5 * np.abs(terms).sum()
+    # gradients on a subset: g_wm = c, g_pdf = 1 / pdf
+    idx = np.arange(0, n, 97)
+    rwi, rax, ray = grad.vjp(u1[idx], u2[idx], wi[:, idx], ax[idx], ay[idx], c[:, idx], 1.0 / pdf[idx])
+    ref_g = np.concatenate([rwi, rax[None], ray[None]])
+    got_g = np.stack([_np(t)[idx] for t in (gx, gy, gz, gax, gay)])
+    _check_errors(_errors(got_g, ref_g), "fused loss gradients")
+
+
+def test_fused_loss_ragged_and_unaligned(v):
+    """Tail chunks and the scalar path give the same per-sample gradients as the generic backward."""
+    n = 3001
+    d = workloads.adjoint_2e24(n=n + 1, seed=41, device=DEV)
+    sl = {k: t[1:].clone()[:n] for k, t in d.items()}  # clone -> aligned
+    un = {k: t[1:n + 1] for k, t in d.items()}          # view offset by one float -> unaligned
+    for src in (sl, un):
+        loss, gx, gy, gz, gax, gay = v.vndf_sample_loss_backward(
+            src["wi_x"], src["wi_y"], src["wi_z"], src["alpha_x"], src["alpha_y"], src["c_x"], src["c_y"],
+            src["c_z"], seed=8, n=n)
+        _, _, _, pdf = v.vndf_sample(src["wi_x"], src["wi_y"], src["wi_z"], src["alpha_x"], src["alpha_y"],
+                                     seed=8, n=n)
+        ref = v.vndf_sample_backward(src["wi_x"], src["wi_y"], src["wi_z"], src["alpha_x"], src["alpha_y"],
+                                     seed=8, g_wm_x=src["c_x"].contiguous(), g_wm_y=src["c_y"].contiguous(),
+                                     g_wm_z=src["c_z"].contiguous(), g_pdf=1.0 / pdf, n=n)
+        for a, b in zip((gx, gy, gz, gax, gay), ref):
+            torch.testing.assert_close(a[:n], b[:n], rtol=1e-4, atol=1e-6)
+
+
+def test_autograd_function(v):
+    from paper_2306_05044_gb300.autograd import vndf_sample_autograd
+    n = 5000
+    d = workloads.adjoint_2e24(n=n, seed=42, device=DEV)
+    leaves = {k: d[k].clone().requires_grad_(True) for k in ("wi_x", "wi_y", "wi_z", "alpha_x", "alpha_y")}
+    wm_x, wm_y, wm_z, pdf = vndf_sample_autograd(leaves["wi_x"], leaves["wi_y"], leaves["wi_z"],
+                                                 leaves["alpha_x"], leaves["alpha_y"], seed=3, counter_base=10)
+    loss = (d["c_x"] * wm_x + d["c_y"] * wm_y + d["c_z"] * wm_z).sum() + torch.log(pdf).sum()
+    loss.backward()
+    ref = v.vndf_sample_loss_backward(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], d["c_x"],
+                                      d["c_y"], d["c_z"], seed=3, counter_base=10)
+    for k, r in zip(("wi_x", "wi_y", "wi_z", "alpha_x", "alpha_y"), ref[1:]):
+        torch.testing.assert_close(leaves[k].grad, r, rtol=1e-4, atol=1e-5)
+
+
+@pytest.mark.slow
+def test_full_size_fused_loss_sampled(v):
+    """The 2^24-sample fused forward+adjoint launch, checked on sampled gradients."""
+    n = 1 << 24
+    d = workloads.adjoint_2e24(n=n, device=DEV)
+    loss, gx, gy, gz, gax, gay = v.vndf_sample_loss_backward(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"],
+                                                             d["alpha_y"], d["c_x"], d["c_y"], d["c_z"], seed=4)
+    rng = np.random.default_rng(1)
+    idx = np.unique(np.concatenate([np.arange(64), n - 1 - np.arange(64), rng.integers(0, n, 1 << 14)]))
+    ti = torch.as_tensor(idx, device=DEV)
+    pick = lambda t: t.index_select(0, ti).cpu().numpy().astype(np.float64)  # noqa: E731
+    wi = np.stack([pick(d[k]) for k in ("wi_x", "wi_y", "wi_z")])
+    ax, ay = pick(d["alpha_x"]), pick(d["alpha_y"])
+    c = np.stack([pick(d[k]) for k in ("c_x", "c_y", "c_z")])
+    u1, u2 = philox.uniforms_at(4, 0, 0, idx)
+    _, pdf = ovndf.sample_vndf_with_pdf(u1, u2, wi, ax, ay)
+    rwi, rax, ray = grad.vjp(u1, u2, wi, ax, ay, c, 1.0 / pdf)
+    ref = np.concatenate([rwi, rax[None], ray[None]])
+    got = np.stack([pick(t) for t in (gx, gy, gz, gax, gay)])
+    _check_errors(_errors(got, ref), "full-size fused gradients")
+    assert np.isfinite(loss.item())
