@@ -4,8 +4,9 @@
 //                               loss = sum_i (c_i . wm_i + log pdf_i)
 // Both recompute the forward in registers (no stored tape) and share the
 // per-sample adjoint in vndf_adjoint.cuh.  The fused kernel reduces the loss
-// per fixed 1024-sample chunk, and a one-block kernel sums the chunk partials
-// in index order, so the loss is bit-reproducible and independent of the grid.
+// per fixed 128-sample group (one warp, four samples per lane, shuffle tree;
+// no block barrier), and a one-block kernel sums the group partials in index
+// order, so the loss is bit-reproducible and independent of the grid.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -15,7 +16,8 @@
 namespace vndf {
 
 constexpr int kBwdBlock = 256;
-constexpr int kChunk = 4 * kBwdBlock;  // samples per loss partial
+constexpr int kChunk = 4 * kBwdBlock;  // samples per block iteration
+constexpr int kGroup = 128;            // samples per loss partial (one warp)
 
 struct BwdArgs {
   const float *wx, *wy, *wz, *ax, *ay, *u1, *u2;
@@ -32,7 +34,7 @@ __device__ __forceinline__ void store4(float* p, int64_t e, const float (&d)[4])
 }
 
 template <bool PHILOX, bool ISO>
-__global__ void __launch_bounds__(kBwdBlock) backward_vec4_kernel(BwdArgs a, int64_t n4) {
+__global__ void __launch_bounds__(kBwdBlock, 3) backward_vec4_kernel(BwdArgs a, int64_t n4) {
   const int64_t stride = int64_t(gridDim.x) * kBwdBlock;
   for (int64_t q = int64_t(blockIdx.x) * kBwdBlock + threadIdx.x; q < n4; q += stride) {
     const int64_t e = 4 * q;
@@ -134,9 +136,8 @@ __device__ __forceinline__ float block_sum(float v, float* smem) {
 }
 
 template <bool PHILOX, bool ISO, bool VEC>
-__global__ void __launch_bounds__(kBwdBlock) loss_backward_kernel(BwdArgs a, int64_t n, int64_t chunks,
+__global__ void __launch_bounds__(kBwdBlock, 3) loss_backward_kernel(BwdArgs a, int64_t n, int64_t chunks,
                                                                   float* partials) {
-  __shared__ float smem[kBwdBlock / 32];
   for (int64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
     const int64_t e = ch * kChunk + 4 * int64_t(threadIdx.x);
     float X[4], Y[4], Z[4], AX[4], AY[4], U1[4], U2[4], CX[4], CY[4], CZ[4];
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(kBwdBlock) loss_backward_kernel(BwdArgs a, int
       const Grad5 g = cap_backward_one(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], CX[k], CY[k], CZ[k], 0.f,
                                        1.f, mx, my, mz, pdf);
       const bool ok = pdf > 0.f;
-      local += ok ? fmaf(CX[k], mx, fmaf(CY[k], my, fmaf(CZ[k], mz, logf(pdf)))) : 0.f;
+      local += ok ? fmaf(CX[k], mx, fmaf(CY[k], my, fmaf(CZ[k], mz, __logf(pdf)))) : 0.f;
       OWX[k] = g.wx;
       OWY[k] = g.wy;
       OWZ[k] = g.wz;
@@ -222,8 +223,10 @@ __global__ void __launch_bounds__(kBwdBlock) loss_backward_kernel(BwdArgs a, int
         }
       }
     }
-    const float s = block_sum<kBwdBlock>(local, smem);
-    if (threadIdx.x == 0) partials[ch] = s;
+    // one partial per warp (128 samples); groups past n are never read
+    const float w = warp_sum(local);
+    const int64_t grp = ch * (kChunk / kGroup) + (threadIdx.x >> 5);
+    if ((threadIdx.x & 31) == 0 && grp * kGroup < n) partials[grp] = w;
   }
 }
 
@@ -252,12 +255,13 @@ int launch_backward(const BwdArgs& a, int64_t n, bool vec, cudaStream_t s) {
 template <bool PHILOX, bool ISO>
 int launch_loss(const BwdArgs& a, int64_t n, bool vec, float* partials, float* loss, cudaStream_t s) {
   const int64_t chunks = (n + kChunk - 1) / kChunk;
+  const int64_t groups = (n + kGroup - 1) / kGroup;
   const unsigned grid = grid_for(chunks * kBwdBlock, kBwdBlock, 8, 16);
   if (vec)
     loss_backward_kernel<PHILOX, ISO, true><<<grid, kBwdBlock, 0, s>>>(a, n, chunks, partials);
   else
     loss_backward_kernel<PHILOX, ISO, false><<<grid, kBwdBlock, 0, s>>>(a, n, chunks, partials);
-  sum_partials_kernel<<<1, 1024, 0, s>>>(partials, chunks, loss);
+  sum_partials_kernel<<<1, 1024, 0, s>>>(partials, groups, loss);
   return launch_status();
 }
 
@@ -296,7 +300,7 @@ extern "C" int vndf_sample_backward(int64_t n, const float* wi_x, const float* w
 
 extern "C" size_t vndf_loss_workspace_bytes(int64_t n) {
   if (n <= 0) return 0;
-  return size_t((n + kChunk - 1) / kChunk) * sizeof(float);
+  return size_t((n + kGroup - 1) / kGroup) * sizeof(float);
 }
 
 extern "C" int vndf_sample_loss_backward(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z,

@@ -1,8 +1,10 @@
 // Reverse-mode derivative of the spherical-cap sampler and its fused pdf with
 // the uniforms held fixed (reparameterised gradients).  The paper defines the
 // forward map only (Sec. 2 steps (1)-(3), Sec. 3.3, Eq. 1); this file is its
-// hand-written adjoint.  The forward is recomputed in registers, exactly as
-// sample_one<cap> evaluates it, and the chain rule is applied backwards:
+// hand-written adjoint.  The forward is recomputed in registers (with the
+// same formulas as sample_one<cap>, but cheaper reciprocal and square-root
+// forms since this kernel is bound by instruction issue, not memory), and the
+// chain rule is applied backwards:
 //
 //   s   = (ax wx, ay wy, wz),  r = |s|^-1,  i = s r,  a = 1 + i.z
 //   S   = 2 a (1 - u2) + u2 (i.x^2 + i.y^2),  st = sqrt(u2 S)        (sin theta)
@@ -10,9 +12,10 @@
 //   v   = (ax h.x, ay h.y, h.z),  wm = v / |v|
 //   pdf = |v|^3 / (pi ax ay a |h|^2)
 //
-// Singular points: st = sqrt(u2) sqrt(S) is differentiated through S with
-// d st / dS = sqrt(u2) / (2 sqrt(S)), finite because S >= 2 (1 - u2) >= 2^-23
-// for the 24-bit uniforms (u2 <= 1 - 2^-24) and exactly 0 at u2 = 0.  |v| and
+// Singular points: st = sqrt(u2 S) is differentiated through S with
+// d st / dS = u2 / (2 st) = sqrt(u2) / (2 sqrt(S)), finite because
+// S >= 2 (1 - u2) >= 2^-23 for the 24-bit uniforms (u2 <= 1 - 2^-24) and taken
+// as exactly 0 at u2 = 0.  |v| and
 // |h| are bounded below by h.z = (1 - u2) a > 0.  No clamp sits on the
 // differentiated path.  Out-of-domain samples return zero gradients (their
 // output is the constant fallback).
@@ -40,11 +43,13 @@ __device__ __forceinline__ Grad5 cap_backward_one(float wx, float wy, float wz, 
   const float om = 1.f - u2;
   const float rho2 = fmaf(ix, ix, iy * iy);
   const float S = fmaf(2.f * a, om, u2 * rho2);
-  const float rS = rsqrtf(S);
-  const float su2 = sqrtf(u2);
-  const float st = sqrtf(u2 * S);
+  // st = sqrt(u2 S) and d st / dS = u2 / (2 st) from one rsqrt; both are 0 at u2 = 0
+  const float q = u2 * S;
+  const float rq = rsqrtf(q);
+  const float st = u2 > 0.f ? q * rq : 0.f;
+  const float u2rq = u2 > 0.f ? u2 * rq : 0.f;
   float sp, cp;
-  sincospif(2.f * u1, &sp, &cp);
+  sincospi_taylor(2.f * u1, sp, cp);
   const float hx = fmaf(st, cp, ix), hy = fmaf(st, sp, iy), hz = om * a;
   const float vx = ax * hx, vy = ay * hy, vz = hz;
   const float vv = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
@@ -53,16 +58,20 @@ __device__ __forceinline__ Grad5 cap_backward_one(float wx, float wy, float wz, 
   my = vy * rv;
   mz = vz * rv;
   const float hh = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
-  const float rhh = __frcp_rn(hh);
-  const float ra = __frcp_rn(a);
-  pdf = __fdividef(vv * vv * rv, kPi * ax * ay * a * hh);
+  // one reciprocal of the pdf denominator gives 1/hh, 1/a, 1/ax and 1/ay
+  const float rden = __fdividef(1.f, kPi * ax * ay * a * hh);
+  pdf = vv * vv * rv * rden;
+  const float p_ = kPi * rden;
+  const float q1 = ax * ay * p_;
+  const float q2 = a * hh * p_;
+  const float rhh = q1 * a, ra = q1 * hh, rax = ay * q2, ray = ax * q2;
 
   // ---- reverse
   const float glp = fmaf(gpdf, pdf, glog);  // adjoint of log pdf
   // log pdf = 1.5 log vv - log pi - log ax - log ay - log a - log hh
-  const float g_vv = 1.5f * glp * __frcp_rn(vv);
-  float g_ax = -glp * __frcp_rn(ax);
-  float g_ay = -glp * __frcp_rn(ay);
+  const float g_vv = 1.5f * glp * rv * rv;
+  float g_ax = -glp * rax;
+  float g_ay = -glp * ray;
   float g_a = -glp * ra;
   const float g_hh = -glp * rhh;
   // wm = v / |v|
@@ -80,8 +89,8 @@ __device__ __forceinline__ Grad5 cap_backward_one(float wx, float wy, float wz, 
   const float g_st = fmaf(cp, g_hx, sp * g_hy);
   float g_ix = g_hx, g_iy = g_hy;
   g_a = fmaf(om, g_hz, g_a);
-  // st = sqrt(u2) sqrt(S)
-  const float g_S = 0.5f * su2 * rS * g_st;
+  // st = sqrt(u2 S)
+  const float g_S = 0.5f * u2rq * g_st;
   // S = 2 a om + u2 rho2
   g_a = fmaf(2.f * om, g_S, g_a);
   const float g_rho2 = u2 * g_S;
