@@ -54,6 +54,7 @@ def parse_args():
     p.add_argument("--no-prior", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--no-fwd-bwd", action="store_true")
+    p.add_argument("--no-albedo", action="store_true")
     p.add_argument("--log2n-adjoint", type=int, default=24)
     return p.parse_args()
 
@@ -344,6 +345,10 @@ def run_ours(args, rank, world):
         result["fwd_bwd"] = fwd_bwd(vndf, dev, rank, world, timed, peak, args.log2n_adjoint)
         result["gpu_launches_fwd_bwd"] = 2 * steps
 
+    if not args.no_albedo:
+        result["albedo"] = albedo(vndf, dev, rank, world, timed)
+        result["gpu_launches_albedo"] = 2 * result["albedo"]["steps"]
+
     if not args.no_e2e:
         result["e2e"] = e2e(vndf, d, n, base, dev, stream, steps, warm, barrier, world)
 
@@ -377,6 +382,35 @@ def fwd_bwd(vndf, dev, rank, world, timed, peak, log2n):
             "hbm": {"algorithmic_bytes": 52 * n, "achieved_gbs": 52 * n / (ms * 1e-3) / 1e9,
                     "frac": 52 * n / (ms * 1e-3) / 1e9 / peak},
             "kernels": "loss_backward_kernel + sum_partials_kernel"}
+
+
+def albedo(vndf, dev, rank, world, timed):
+    """Batched directional albedo: 4096 ragged queries, one captured CUDA graph (prologue + persistent kernel)."""
+    import torch
+
+    import workloads
+    g = workloads.albedo_grid(device=dev)
+    nq = g["wi_x"].numel()
+    total = int(g["n_samples"].sum().item())
+    E = torch.empty(nq, device=dev)
+    ws = torch.empty(vndf.vndf_albedo_workspace_bytes(nq, 65536), dtype=torch.uint8, device=dev)
+    args = (g["wi_x"], g["wi_y"], g["wi_z"], g["alpha_x"], None, g["n_samples"])
+    best, tuned_ms = vndf.vndf_albedo_autotune(*args, stream_id=rank * nq, E=E, workspace=ws)
+    side = torch.cuda.Stream(dev)
+    with torch.cuda.stream(side):
+        vndf.vndf_albedo_batched(*args, stream_id=rank * nq, E=E, workspace=ws)
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        vndf.vndf_albedo_batched(*args, stream_id=rank * nq, E=E, workspace=ws)
+    steps = 100
+    tot, per, _ = timed(graph.replay, steps, 5)
+    ms = tot / steps
+    return {"workload": "albedo_grid_4096", "queries": nq, "samples": total,
+            "value": world * total / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "config": {"warps_per_cta": best[0], "groups_per_item": best[1], "ctas_per_sm": best[2]},
+            "captured": "cuda graph (prologue + persistent kernel)",
+            "E_range": [float(E.min().item()), float(E.max().item())]}
 
 
 def e2e(vndf, d, n, base, dev, stream, steps, warm, barrier, world):

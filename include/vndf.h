@@ -187,6 +187,74 @@ int vndf_sample_loss_backward(int64_t n,
                               float *loss, void *workspace, size_t workspace_bytes,
                               void *cuda_stream);
 
+/* Device workspace (bytes) for vndf_albedo_batched / vndf_albedo_autotune with
+ * n_queries queries of at most max_samples_per_query samples each:
+ * control words (item scan, counters) plus one float per 256-sample group
+ * slot.  0 when n_queries <= 0. */
+size_t vndf_albedo_workspace_bytes(int32_t n_queries, int32_t max_samples_per_query);
+
+/*
+ * vndf_albedo_batched -- directional albedo of the GGX microfacet BRDF for a
+ * ragged batch of queries, estimated in one persistent launch with the
+ * spherical-cap VNDF sampler:
+ *   E_q = (1/N_q) sum_j f_r(wo_j, wi_q) |cos theta_o| / PDF(wo_j),
+ * the Monte Carlo estimator of App. A (Eq. rendering_mc with L = 1): wm_j is
+ * sampled as in vndf_sample (Sec. 2, Sec. 3.3), wo_j is wi reflected about it
+ * (Eq. reflect) and PDF = G1 D / (4 cos theta_i) (App. A).  f_r is the
+ * Cook-Torrance BRDF of App. A with the height-correlated G2 and Schlick's
+ * Fresnel F0 + (1 - F0)(1 - wi.wm)^5; terms with wo below the surface are 0.
+ *   n_queries          number of queries (>= 0); 0 is a no-op.
+ *   wi_*, alpha_*      per-query direction (upper hemisphere, any length) and
+ *                      roughness; alpha_y = NULL means isotropic.
+ *   n_samples          per-query sample counts N_q (int32, device).  A count
+ *                      outside [0, max_samples_per_query] yields E_q = NaN; a
+ *                      count of 0 yields E_q = 0.
+ *   max_samples_per_query  the bound the workspace was sized for (<= 2^30).
+ *   f0                 Schlick reflectance at normal incidence.
+ *   seed, counter_base, stream_id  Philox: query q draws from stream
+ *                      stream_id + q, sample j from global index counter_base + j.
+ *   E                  output, n_queries floats (device).
+ *   workspace          device scratch of >= vndf_albedo_workspace_bytes(...)
+ *                      bytes, 256-byte aligned, owned by the caller; contents on
+ *                      entry are ignored.  Concurrent calls need separate
+ *                      workspaces.
+ *   config             NULL (use the configuration vndf_albedo_autotune picked
+ *                      on this device, else a default) or three int32 on the
+ *                      host: warps per CTA (1-16), 256-sample groups per work
+ *                      item (1-256), CTAs per SM (1-32).
+ * The summation order is fixed by the data (256-sample groups, then groups in
+ * order), so E is bit-identical for every config, every split of the queries
+ * into calls, and every replay of a captured CUDA graph.
+ * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, ALIGN, ARG,
+ * WORKSPACE, CUDA).
+ */
+int vndf_albedo_batched(int32_t n_queries,
+                        const float *wi_x, const float *wi_y, const float *wi_z,
+                        const float *alpha_x, const float *alpha_y,
+                        const int32_t *n_samples, int32_t max_samples_per_query,
+                        float f0, uint64_t seed, uint64_t counter_base, uint32_t stream_id,
+                        float *E, void *workspace, size_t workspace_bytes,
+                        const int32_t *config, void *cuda_stream);
+
+/*
+ * vndf_albedo_autotune -- time vndf_albedo_batched on the given batch for a
+ * fixed set of launch configurations (warps per CTA x groups per item x CTAs
+ * per SM), remember the fastest for the current device (later calls with
+ * config = NULL use it) and return it.  Synchronises `cuda_stream`; not for
+ * use during stream capture.  Arguments as for vndf_albedo_batched (E is
+ * overwritten with the batch result), plus:
+ *   best_config        output, three int32 on the host (may be NULL).
+ *   best_ms            output, best time in milliseconds (host, may be NULL).
+ * Returns VNDF_OK or a negative VNDF_ERR_* code.
+ */
+int vndf_albedo_autotune(int32_t n_queries,
+                         const float *wi_x, const float *wi_y, const float *wi_z,
+                         const float *alpha_x, const float *alpha_y,
+                         const int32_t *n_samples, int32_t max_samples_per_query,
+                         float f0, uint64_t seed, uint64_t counter_base, uint32_t stream_id,
+                         float *E, void *workspace, size_t workspace_bytes,
+                         int32_t *best_config, float *best_ms, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -41,6 +41,11 @@ SIGNATURES = {
     "vndf_loss_workspace_bytes": (_SZ, [_I64]),
     "vndf_sample_loss_backward": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _U64, _U64, _U32,
                                                  _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "vndf_albedo_workspace_bytes": (_SZ, [_I32, _I32]),
+    "vndf_albedo_batched": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, _P, _I32, _F, _U64, _U64, _U32, _P, _P, _SZ,
+                                           _P, _P]),
+    "vndf_albedo_autotune": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, _P, _I32, _F, _U64, _U64, _U32, _P, _P, _SZ,
+                                            _P, _P, _P]),
 }
 
 
@@ -219,3 +224,49 @@ def vndf_sample_loss_backward(wi_x, wi_y, wi_z, alpha_x, alpha_y, c_x, c_y, c_z,
         int(workspace.numel()), _stream(stream, wi_x.device))
     _check("vndf_sample_loss_backward", st)
     return loss, gx, gy, gz, gax, gay
+
+
+def vndf_albedo_workspace_bytes(n_queries, max_samples_per_query):
+    return int(load().vndf_albedo_workspace_bytes(int(n_queries), int(max_samples_per_query)))
+
+
+def _albedo_common(wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples, max_samples_per_query, E, workspace):
+    nq = wi_x.numel()
+    if E is None:
+        E = torch.empty(nq, dtype=torch.float32, device=wi_x.device)
+    need = vndf_albedo_workspace_bytes(nq, max_samples_per_query)
+    if workspace is None:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=wi_x.device)
+    args = (nq, _ptr(wi_x, "wi_x"), _ptr(wi_y, "wi_y"), _ptr(wi_z, "wi_z"), _ptr(alpha_x, "alpha_x"),
+            _ptr(alpha_y, "alpha_y"), _ptr(n_samples, "n_samples", torch.int32), int(max_samples_per_query))
+    return E, workspace, args
+
+
+def vndf_albedo_batched(wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples, max_samples_per_query=65536, f0=0.04,
+                        seed=3, counter_base=0, stream_id=0, E=None, workspace=None, config=None, stream=None):
+    """Per-query directional albedo; see vndf_albedo_batched in include/vndf.h.  config: None or
+    (warps per CTA, groups per item, CTAs per SM)."""
+    E, workspace, args = _albedo_common(wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples, max_samples_per_query, E,
+                                        workspace)
+    cfg = None if config is None else (ctypes.c_int32 * 3)(*[int(c) for c in config])
+    st = load().vndf_albedo_batched(*args, float(f0), int(seed) & (2**64 - 1), int(counter_base) & (2**64 - 1),
+                                    int(stream_id) & 0xFFFFFFFF, _ptr(E, "E"), _ptr(workspace, "workspace",
+                                                                                   torch.uint8),
+                                    int(workspace.numel()), cfg, _stream(stream, wi_x.device))
+    _check("vndf_albedo_batched", st)
+    return E
+
+
+def vndf_albedo_autotune(wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples, max_samples_per_query=65536, f0=0.04,
+                         seed=3, counter_base=0, stream_id=0, E=None, workspace=None, stream=None):
+    """Pick and remember the fastest albedo launch configuration; returns ((warps, groups, ctas), ms)."""
+    E, workspace, args = _albedo_common(wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples, max_samples_per_query, E,
+                                        workspace)
+    best = (ctypes.c_int32 * 3)()
+    ms = ctypes.c_float()
+    st = load().vndf_albedo_autotune(*args, float(f0), int(seed) & (2**64 - 1), int(counter_base) & (2**64 - 1),
+                                     int(stream_id) & 0xFFFFFFFF, _ptr(E, "E"),
+                                     _ptr(workspace, "workspace", torch.uint8), int(workspace.numel()), best,
+                                     ctypes.byref(ms), _stream(stream, wi_x.device))
+    _check("vndf_albedo_autotune", st)
+    return tuple(best), ms.value

@@ -1,0 +1,417 @@
+// Batched directional albedo of the GGX microfacet BRDF, estimated with the
+// spherical-cap VNDF sampler: for every query q (incident direction wi_q,
+// roughness alpha_q, sample count N_q)
+//   E_q = (1 / N_q) sum_j f_r(wo_j, wi) |cos theta_o| / PDF(wo_j)        (App. A, Eq. rendering_mc, L = 1)
+// where wm_j is drawn from the VNDF (Sec. 2, Sec. 3.3), wo_j = 2 (wm.wi) wm - wi
+// (Eq. reflect) and PDF = G1 D / (4 cos theta_i) (App. A).  The D and G1 terms
+// cancel, leaving the weight F(wi.wm) G2 / G1(wi) (zero when wo is below the
+// surface), with Schlick's Fresnel and the height-correlated G2 of App. A:
+//   G2 / G1(wi) = (L_i + z_i) z_o / ((L_i + z_i) z_o + z_i P_o / (L_o + z_o)),
+//   L_k = |M^-1 w_k|,  P_o = ax^2 wo.x^2 + ay^2 wo.y^2  (so L_o - z_o = P_o / (L_o + z_o) without cancellation).
+//
+// Work decomposition (ragged counts in one launch):
+// * Samples of a query are cut into groups of 256 consecutive samples; lane l of
+//   the warp that owns a group sums samples 8l .. 8l+7 in order, then the warp
+//   adds the 32 lane sums with a fixed butterfly.  That order is a property of
+//   the data, not of the launch, so E is bit-identical for every launch shape.
+// * An item is `groups_per_item` consecutive groups of one query.  A one-block
+//   prologue computes per-query item counts and their exclusive scan; the
+//   persistent kernel's CTAs claim items from an atomic counter, write one
+//   partial per group, and the CTA that completes a query's last item sums the
+//   query's group partials (fixed lane-strided order + butterfly) into E_q.
+// * Nothing waits on anything: completion is detected with an atomic counter
+//   per query (fence, then atomicAdd), so no CTA ever spins.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+
+#include "common.cuh"
+#include "philox.cuh"
+#include "vndf_math.cuh"
+
+namespace vndf {
+
+constexpr int kGroupSamples = 256;  // samples per reduction group (one warp)
+constexpr int kLaneSamples = 8;     // consecutive samples per lane
+
+struct AlbedoArgs {
+  const float *wx, *wy, *wz, *ax, *ay;
+  const int32_t* ns;
+  int32_t nq;
+  int32_t gmax;  // group slots per query (ceil(max_samples / 256))
+  int32_t max_n;
+  int32_t groups_per_item;
+  float f0;
+  Rng rng;  // rng.stream is the stream id of query 0
+  float* E;
+  int32_t* ctl;     // [0] next item, [1] total items, [2 .. 2+nq] item offsets, then done[nq]
+  float* partials;  // nq * gmax group sums
+};
+
+__host__ __device__ inline size_t albedo_ctl_ints(int32_t nq) { return 3 + 2 * size_t(nq); }
+__host__ __device__ inline size_t albedo_partials_offset(int32_t nq) {
+  return (albedo_ctl_ints(nq) * 4 + 255) / 256 * 256;
+}
+
+// ---------------------------------------------------------------- prologue
+__global__ void __launch_bounds__(1024) albedo_prologue_kernel(AlbedoArgs a) {
+  __shared__ int32_t warp_tot[32];
+  const int t = threadIdx.x;
+  const int32_t per = (a.nq + 1023) / 1024;
+  const int32_t q0 = min(a.nq, t * per), q1 = min(a.nq, q0 + per);
+  int32_t* offsets = a.ctl + 2;
+  int32_t* done = a.ctl + 3 + a.nq;
+  int32_t local = 0;
+  for (int32_t q = q0; q < q1; ++q) {
+    const int32_t n = a.ns[q];
+    const bool valid = n >= 0 && n <= a.max_n;
+    const int32_t groups = valid ? (n + kGroupSamples - 1) / kGroupSamples : 0;
+    local += (groups + a.groups_per_item - 1) / a.groups_per_item;
+    done[q] = 0;
+    if (!valid) a.E[q] = __int_as_float(0x7fc00000);  // NaN: count outside [0, max]
+    else if (n == 0) a.E[q] = 0.f;
+  }
+  // exclusive scan of the per-thread totals (fixed order)
+  int32_t incl = local;
+  const int lane = t & 31, w = t >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_tot[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int32_t x = warp_tot[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    warp_tot[lane] = x;  // inclusive over warps
+  }
+  __syncthreads();
+  int32_t run = (w > 0 ? warp_tot[w - 1] : 0) + incl - local;
+  for (int32_t q = q0; q < q1; ++q) {
+    offsets[q] = run;
+    const int32_t n = a.ns[q];
+    const bool valid = n >= 0 && n <= a.max_n;
+    const int32_t groups = valid ? (n + kGroupSamples - 1) / kGroupSamples : 0;
+    run += (groups + a.groups_per_item - 1) / a.groups_per_item;
+  }
+  if (t == 1023) {
+    offsets[a.nq] = run;
+    a.ctl[1] = run;
+    a.ctl[0] = 0;
+  }
+}
+
+// ---------------------------------------------------------------- sample weight
+struct QueryConst {
+  float ux, uy, uz;  // unit wi
+  float ax, ay;
+  Stretched i;       // M^-1 wi / |M^-1 wi|
+  float A;           // L_i + z_i for the unit wi
+};
+
+__device__ __forceinline__ QueryConst query_const(const AlbedoArgs& a, int32_t q) {
+  QueryConst c;
+  const float wx = a.wx[q], wy = a.wy[q], wz = a.wz[q];
+  c.ax = a.ax[q];
+  c.ay = a.ay ? a.ay[q] : c.ax;
+  const float rn = rsqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz)));
+  c.ux = wx * rn;
+  c.uy = wy * rn;
+  c.uz = wz * rn;
+  const float sx = c.ax * c.ux, sy = c.ay * c.uy;
+  const float l2 = fmaf(sx, sx, fmaf(sy, sy, c.uz * c.uz));
+  const float rl = rsqrtf(l2);
+  c.i = Stretched{sx * rl, sy * rl, c.uz * rl};
+  c.A = l2 * rl + c.uz;
+  return c;
+}
+
+// Estimator term of one sample: F G2 / G1(wi), or 0 when wo is below the surface.
+__device__ __forceinline__ float albedo_weight(const QueryConst& c, float f0, float u1, float u2) {
+  float hx, hy, hz, a;
+  cap_half_vector(c.i, u1, u2, hx, hy, hz, a);
+  const float vx = c.ax * hx, vy = c.ay * hy, vz = hz;
+  const float rv = rsqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
+  const float mx = vx * rv, my = vy * rv, mz = vz * rv;
+  const float d = fmaf(mx, c.ux, fmaf(my, c.uy, mz * c.uz));  // wi.wm > 0
+  const float ox = fmaf(2.f * d, mx, -c.ux);
+  const float oy = fmaf(2.f * d, my, -c.uy);
+  const float oz = fmaf(2.f * d, mz, -c.uz);
+  const float sx = c.ax * ox, sy = c.ay * oy;
+  const float po = fmaf(sx, sx, sy * sy);
+  const float lo = sqrtf(fmaf(oz, oz, po));
+  const float num = c.A * oz;
+  const float g = __fdividef(num, fmaf(c.uz * po, __fdividef(1.f, lo + oz), num));
+  const float t = 1.f - d;
+  const float t2 = t * t;
+  const float fr = fmaf(1.f - f0, t2 * t2 * t, f0);
+  return oz > 0.f ? fr * g : 0.f;
+}
+
+// Uniforms of samples j0, j0+1 (j0 even) of one Philox stream.
+__device__ __forceinline__ void uniforms2(const Rng& r, uint64_t j0, float& a1, float& a2, float& b1, float& b2) {
+  const uint64_t g0 = r.base + j0;
+  if ((g0 & 1u) == 0) {
+    const uint4 w = philox_block(r, g0 >> 1);
+    a1 = word_to_unit(w.x);
+    a2 = word_to_unit(w.y);
+    b1 = word_to_unit(w.z);
+    b2 = word_to_unit(w.w);
+  } else {
+    const uint4 w = philox_block(r, g0 >> 1);
+    const uint4 x = philox_block(r, (g0 + 1) >> 1);
+    a1 = word_to_unit(w.z);
+    a2 = word_to_unit(w.w);
+    b1 = word_to_unit(x.x);
+    b2 = word_to_unit(x.y);
+  }
+}
+
+__device__ __forceinline__ float warp_tree(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- persistent kernel
+__global__ void __launch_bounds__(512) albedo_kernel(AlbedoArgs a) {
+  __shared__ int32_t s_item, s_q, s_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int32_t* offsets = a.ctl + 2;
+  int32_t* done = a.ctl + 3 + a.nq;
+  const int32_t total = a.ctl[1];
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int32_t item = atomicAdd(a.ctl, 1);
+      int32_t q = -1;
+      if (item < total) {  // last q with offsets[q] <= item
+        int32_t lo = 0, hi = a.nq - 1;
+        while (lo < hi) {
+          const int32_t mid = (lo + hi + 1) >> 1;
+          if (offsets[mid] <= item) lo = mid;
+          else hi = mid - 1;
+        }
+        q = lo;
+      }
+      s_item = item;
+      s_q = q;
+    }
+    __syncthreads();
+    const int32_t item = s_item, q = s_q;
+    if (item >= total) break;
+    const int32_t n = a.ns[q];
+    const int32_t groups = (n + kGroupSamples - 1) / kGroupSamples;
+    const int32_t k = item - offsets[q];
+    const int32_t g_end = min(groups, (k + 1) * a.groups_per_item);
+    const QueryConst c = query_const(a, q);
+    Rng r = a.rng;
+    r.stream = a.rng.stream + uint32_t(q);
+    for (int32_t g = k * a.groups_per_item + warp; g < g_end; g += nwarps) {
+      const int32_t j0 = g * kGroupSamples + lane * kLaneSamples;
+      float acc = 0.f;
+#pragma unroll
+      for (int s = 0; s < kLaneSamples; s += 2) {
+        float a1, a2, b1, b2;
+        uniforms2(r, uint64_t(j0 + s), a1, a2, b1, b2);
+        const float w0 = albedo_weight(c, a.f0, a1, a2);
+        const float w1 = albedo_weight(c, a.f0, b1, b2);
+        acc += j0 + s < n ? w0 : 0.f;
+        acc += j0 + s + 1 < n ? w1 : 0.f;
+      }
+      acc = warp_tree(acc);
+      if (lane == 0) {
+        a.partials[size_t(q) * a.gmax + g] = acc;
+        __threadfence();
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int32_t items_q = offsets[q + 1] - offsets[q];
+      s_last = atomicAdd(done + q, 1) == items_q - 1;
+    }
+    __syncthreads();
+    if (s_last && warp == 0) {
+      __threadfence();
+      float sum = 0.f;
+      for (int32_t g = lane; g < groups; g += 32) sum += __ldcg(a.partials + size_t(q) * a.gmax + g);
+      sum = warp_tree(sum);
+      if (lane == 0) a.E[q] = sum / float(n);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- launch configuration
+struct AlbedoConfig {
+  int32_t block_warps, groups_per_item, ctas_per_sm;
+};
+
+bool config_ok(const AlbedoConfig& c) {
+  return c.block_warps >= 1 && c.block_warps <= 16 && c.groups_per_item >= 1 && c.groups_per_item <= 256 &&
+         c.ctas_per_sm >= 1 && c.ctas_per_sm <= 32;
+}
+
+// Per-device tuned configuration (set by vndf_albedo_autotune), else the default.
+std::mutex g_tune_mutex;
+AlbedoConfig g_tuned[64];
+bool g_has_tuned[64] = {false};
+
+AlbedoConfig current_config() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  if (dev >= 0 && dev < 64 && g_has_tuned[dev]) return g_tuned[dev];
+  return AlbedoConfig{8, 2, 4};
+}
+
+int launch_albedo(AlbedoArgs a, const AlbedoConfig& c, cudaStream_t s) {
+  a.groups_per_item = c.groups_per_item;
+  albedo_prologue_kernel<<<1, 1024, 0, s>>>(a);
+  const unsigned grid = static_cast<unsigned>(sm_count() * c.ctas_per_sm);
+  albedo_kernel<<<grid, 32 * c.block_warps, 0, s>>>(a);
+  return launch_status();
+}
+
+}  // namespace vndf
+
+using namespace vndf;
+
+extern "C" size_t vndf_albedo_workspace_bytes(int32_t n_queries, int32_t max_samples_per_query) {
+  if (n_queries <= 0 || max_samples_per_query < 0) return 0;
+  const size_t gmax = (size_t(max_samples_per_query) + kGroupSamples - 1) / kGroupSamples;
+  return albedo_partials_offset(n_queries) + size_t(n_queries) * gmax * sizeof(float);
+}
+
+namespace vndf {
+int albedo_validate(int32_t n_queries, const float* wi_x, const float* wi_y, const float* wi_z, const float* alpha_x,
+                    const float* alpha_y, const int32_t* n_samples, int32_t max_samples, float* E,
+                    void* workspace, size_t workspace_bytes) {
+  if (n_queries < 0 || max_samples < 0 || max_samples > (1 << 30)) return VNDF_ERR_SIZE;
+  if (n_queries == 0) return VNDF_OK;
+  if (!wi_x || !wi_y || !wi_z || !alpha_x || !n_samples || !E) return VNDF_ERR_NULL;
+  if (!all_aligned4(wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples, E)) return VNDF_ERR_ALIGN;
+  if (!workspace || workspace_bytes < vndf_albedo_workspace_bytes(n_queries, max_samples))
+    return VNDF_ERR_WORKSPACE;
+  if (!aligned(workspace, 256)) return VNDF_ERR_ALIGN;
+  return VNDF_OK;
+}
+
+AlbedoArgs albedo_args(int32_t n_queries, const float* wi_x, const float* wi_y, const float* wi_z,
+                       const float* alpha_x, const float* alpha_y, const int32_t* n_samples, int32_t max_samples,
+                       float f0, uint64_t seed, uint64_t counter_base, uint32_t stream_id, float* E,
+                       void* workspace) {
+  AlbedoArgs a;
+  a.wx = wi_x;
+  a.wy = wi_y;
+  a.wz = wi_z;
+  a.ax = alpha_x;
+  a.ay = alpha_y;
+  a.ns = n_samples;
+  a.nq = n_queries;
+  a.max_n = max_samples;
+  a.gmax = (max_samples + kGroupSamples - 1) / kGroupSamples;
+  a.groups_per_item = 1;
+  a.f0 = f0;
+  a.rng = make_rng(seed, counter_base, stream_id);
+  a.E = E;
+  a.ctl = static_cast<int32_t*>(workspace);
+  a.partials = reinterpret_cast<float*>(static_cast<char*>(workspace) + albedo_partials_offset(n_queries));
+  return a;
+}
+}  // namespace vndf
+
+extern "C" int vndf_albedo_batched(int32_t n_queries, const float* wi_x, const float* wi_y, const float* wi_z,
+                                   const float* alpha_x, const float* alpha_y, const int32_t* n_samples,
+                                   int32_t max_samples_per_query, float f0, uint64_t seed, uint64_t counter_base,
+                                   uint32_t stream_id, float* E, void* workspace, size_t workspace_bytes,
+                                   const int32_t* config, void* cuda_stream) {
+  const int st = albedo_validate(n_queries, wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples,
+                                 max_samples_per_query, E, workspace, workspace_bytes);
+  if (st != VNDF_OK || n_queries == 0) return st;
+  AlbedoConfig c = current_config();
+  if (config) {
+    c = AlbedoConfig{config[0], config[1], config[2]};
+    if (!config_ok(c)) return VNDF_ERR_ARG;
+  }
+  const AlbedoArgs a = albedo_args(n_queries, wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples,
+                                   max_samples_per_query, f0, seed, counter_base, stream_id, E, workspace);
+  return launch_albedo(a, c, static_cast<cudaStream_t>(cuda_stream));
+}
+
+extern "C" int vndf_albedo_autotune(int32_t n_queries, const float* wi_x, const float* wi_y, const float* wi_z,
+                                    const float* alpha_x, const float* alpha_y, const int32_t* n_samples,
+                                    int32_t max_samples_per_query, float f0, uint64_t seed,
+                                    uint64_t counter_base, uint32_t stream_id, float* E, void* workspace,
+                                    size_t workspace_bytes, int32_t* best_config, float* best_ms,
+                                    void* cuda_stream) {
+  const int st = albedo_validate(n_queries, wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples,
+                                 max_samples_per_query, E, workspace, workspace_bytes);
+  if (st != VNDF_OK) return st;
+  if (n_queries == 0) return VNDF_ERR_SIZE;
+  const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  AlbedoArgs a = albedo_args(n_queries, wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples, max_samples_per_query, f0,
+                             seed, counter_base, stream_id, E, workspace);
+  static const int32_t warps[] = {4, 8, 16};
+  static const int32_t gpis[] = {1, 2, 4, 8};
+  static const int32_t ctas[] = {2, 4, 8};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return VNDF_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return VNDF_ERR_CUDA;
+  }
+  AlbedoConfig best{8, 2, 4};
+  float best_t = INFINITY;
+  int rc = VNDF_OK;
+  for (int32_t w : warps)
+    for (int32_t g : gpis)
+      for (int32_t c : ctas) {
+        if (w * 32 * c > 2048) continue;  // more threads than an SM holds
+        const AlbedoConfig cfg{w, g, c};
+        rc = launch_albedo(a, cfg, s);  // warm-up
+        if (rc != VNDF_OK) break;
+        float t = INFINITY;
+        for (int rep = 0; rep < 3; ++rep) {
+          cudaEventRecord(e0, s);
+          rc = launch_albedo(a, cfg, s);
+          cudaEventRecord(e1, s);
+          if (rc != VNDF_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = VNDF_ERR_CUDA;
+            break;
+          }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          t = fminf(t, ms);
+        }
+        if (rc != VNDF_OK) break;
+        if (t < best_t) {
+          best_t = t;
+          best = cfg;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != VNDF_OK) return rc;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    if (dev >= 0 && dev < 64) {
+      g_tuned[dev] = best;
+      g_has_tuned[dev] = true;
+    }
+  }
+  if (best_config) {
+    best_config[0] = best.block_warps;
+    best_config[1] = best.groups_per_item;
+    best_config[2] = best.ctas_per_sm;
+  }
+  if (best_ms) *best_ms = best_t;
+  return VNDF_OK;
+}

@@ -91,3 +91,19 @@ def test_binding_fails_loudly_without_gpu_tensors(lib):
     x = torch.zeros(8)
     with pytest.raises(ValueError):
         v.vndf_sample(x, x, x, x)
+
+
+def test_albedo_rejects_bad_arguments(lib):
+    ws_need = lib.vndf_albedo_workspace_bytes(16, 1000)
+    assert ws_need > 0
+    assert lib.vndf_albedo_workspace_bytes(0, 1000) == 0
+    args = lambda nq, ws, wsb, cfg=None, mx=1000: (nq, FAKE, FAKE, FAKE, FAKE, None, FAKE, mx, 0.04, 1, 0, 0,  # noqa: E731
+                                                   FAKE, ws, wsb, cfg, None)
+    assert lib.vndf_albedo_batched(*args(0, None, 0)) == 0
+    assert lib.vndf_albedo_batched(*args(-1, FAKE, ws_need)) == -2
+    assert lib.vndf_albedo_batched(*args(16, None, ws_need)) == -5
+    assert lib.vndf_albedo_batched(*args(16, FAKE, ws_need - 1)) == -5
+    assert lib.vndf_albedo_batched(*args(16, FAKE + 16, ws_need)) == -3  # workspace not 256-byte aligned
+    import ctypes
+    bad = (ctypes.c_int32 * 3)(0, 1, 1)
+    assert lib.vndf_albedo_batched(*args(16, FAKE, ws_need, bad)) == -7
