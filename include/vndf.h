@@ -255,6 +255,40 @@ int vndf_albedo_autotune(int32_t n_queries,
                          float *E, void *workspace, size_t workspace_bytes,
                          int32_t *best_config, float *best_ms, void *cuda_stream);
 
+/* Size of the fixed device scratch array behind vndf_albedo_batched_noalloc:
+ * 8 MiB.  A batch fits when vndf_albedo_workspace_bytes(n_queries,
+ * max_samples_per_query) is at most this; 4096 queries of up to 65536 samples
+ * each need about 4.03 MiB. */
+#define VNDF_ALBEDO_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/*
+ * vndf_albedo_batched_noalloc -- vndf_albedo_batched for callers that cannot
+ * allocate device memory or pass a workspace (for instance a renderer's frame
+ * loop, where a cudaMalloc would synchronise the device, or a plugin that only
+ * receives pointers from a host application that owns all device memory).
+ * The paper has no counterpart; this is a deployment variant.
+ * It allocates nothing: its scratch is a file-scope device array of
+ * VNDF_ALBEDO_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds
+ * until the process exits.  The caller still provides all inputs and the output
+ * E, with the meaning and results of vndf_albedo_batched.
+ *   - Batches whose vndf_albedo_workspace_bytes(n_queries,
+ *     max_samples_per_query) exceeds the array are rejected with
+ *     VNDF_ERR_SIZE before anything is enqueued.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make that
+ *     first call before any stream capture.
+ *   - All calls on a device share the one array.  Each call resets the parts it
+ *     reads, but calls that overlap on the GPU (concurrent streams, or several
+ *     host threads) race on it: order them on one stream.
+ * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, ALIGN, ARG, CUDA).
+ */
+int vndf_albedo_batched_noalloc(int32_t n_queries,
+                                const float *wi_x, const float *wi_y, const float *wi_z,
+                                const float *alpha_x, const float *alpha_y,
+                                const int32_t *n_samples, int32_t max_samples_per_query,
+                                float f0, uint64_t seed, uint64_t counter_base, uint32_t stream_id,
+                                float *E, const int32_t *config, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

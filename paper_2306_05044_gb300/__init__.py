@@ -46,6 +46,8 @@ SIGNATURES = {
                                            _P, _P]),
     "vndf_albedo_autotune": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, _P, _I32, _F, _U64, _U64, _U32, _P, _P, _SZ,
                                             _P, _P, _P]),
+    "vndf_albedo_batched_noalloc": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, _P, _I32, _F, _U64, _U64, _U32, _P,
+                                                   _P, _P]),
 }
 
 

@@ -415,3 +415,54 @@ extern "C" int vndf_albedo_autotune(int32_t n_queries, const float* wi_x, const 
   if (best_ms) *best_ms = best_t;
   return VNDF_OK;
 }
+
+// ---------------------------------------------------------------- no-allocation variant
+// Some callers cannot hand the library a workspace: code on a renderer's
+// per-frame path, where a cudaMalloc would synchronise the device and stall the
+// frame, or a plugin that only receives the pointers a host application chose
+// to give it and owns no allocator.  For them, vndf_albedo_batched_noalloc runs
+// the same two kernels with the scratch held in this fixed device array instead
+// of a caller workspace.  The array exists on every GPU that loads the library
+// and stays allocated until the process exits.
+static __device__ __align__(256) unsigned char g_albedo_scratch[VNDF_ALBEDO_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_scratch_mutex;
+void* g_scratch_ptr[64] = {nullptr};
+
+// Device address of g_albedo_scratch on the current device.  Host code may not
+// use the symbol's name as a pointer (on the host it is only a stand-in), so
+// the address is looked up once per device, with that device current, and cached.
+int scratch_address(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return VNDF_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (g_scratch_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_albedo_scratch) != cudaSuccess || p == nullptr) return VNDF_ERR_CUDA;
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return VNDF_OK;
+}
+}  // namespace
+
+extern "C" int vndf_albedo_batched_noalloc(int32_t n_queries, const float* wi_x, const float* wi_y,
+                                           const float* wi_z, const float* alpha_x, const float* alpha_y,
+                                           const int32_t* n_samples, int32_t max_samples_per_query, float f0,
+                                           uint64_t seed, uint64_t counter_base, uint32_t stream_id, float* E,
+                                           const int32_t* config, void* cuda_stream) {
+  if (n_queries < 0 || max_samples_per_query < 0 || max_samples_per_query > (1 << 30)) return VNDF_ERR_SIZE;
+  if (n_queries == 0) return VNDF_OK;
+  if (vndf_albedo_workspace_bytes(n_queries, max_samples_per_query) > VNDF_ALBEDO_NOALLOC_SCRATCH_BYTES)
+    return VNDF_ERR_SIZE;
+  void* scratch = nullptr;
+  const int rc = scratch_address(&scratch);
+  if (rc != VNDF_OK) return rc;
+  // The prologue kernel rewrites every control word the persistent kernel reads,
+  // and each group partial is written before it is read, so what an earlier call
+  // left in the array never leaks into this one.
+  return vndf_albedo_batched(n_queries, wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples, max_samples_per_query, f0,
+                             seed, counter_base, stream_id, E, scratch, VNDF_ALBEDO_NOALLOC_SCRATCH_BYTES, config,
+                             cuda_stream);
+}
