@@ -55,6 +55,7 @@ def parse_args():
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--no-fwd-bwd", action="store_true")
     p.add_argument("--no-albedo", action="store_true")
+    p.add_argument("--no-fit", action="store_true")
     p.add_argument("--log2n-adjoint", type=int, default=24)
     return p.parse_args()
 
@@ -349,6 +350,10 @@ def run_ours(args, rank, world):
         result["albedo"] = albedo(vndf, dev, rank, world, timed)
         result["gpu_launches_albedo"] = 2 * result["albedo"]["steps"]
 
+    if not args.no_fit:
+        result["fit"] = fit_leg(vndf, dev, rank, world, timed)
+        result["gpu_launches_fit"] = 2 * result["fit"]["steps"]
+
     if not args.no_e2e:
         result["e2e"] = e2e(vndf, d, n, base, dev, stream, steps, warm, barrier, world)
 
@@ -411,6 +416,35 @@ def albedo(vndf, dev, rank, world, timed):
             "config": {"warps_per_cta": best[0], "groups_per_item": best[1], "ctas_per_sm": best[2]},
             "captured": "cuda graph (prologue + persistent kernel)",
             "E_range": [float(E.min().item()), float(E.max().item())]}
+
+
+def fit_leg(vndf, dev, rank, world, timed):
+    """Roughness-map fitting: 256 x 256 texels x 1024 samples, forward + adjoint + Adam as one captured graph."""
+    import torch
+
+    import workloads
+    d = workloads.roughness_map(device=dev)
+    nt = d["alpha_x"].numel()
+    st = vndf.fit_state(d["alpha_x"], d["alpha_y"])
+    loss = torch.empty(1, device=dev)
+    ws = torch.empty(vndf.vndf_fit_workspace_bytes(nt), dtype=torch.uint8, device=dev)
+    args = (d["wi_x"], d["wi_y"], d["wi_z"], d["target_x"], d["target_y"], d["target_z"])
+    side = torch.cuda.Stream(dev)
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        vndf.vndf_fit_step(st, *args, seed=5, stream_id=rank * nt, loss=loss, workspace=ws)
+    graph.replay()
+    torch.cuda.synchronize(dev)
+    first = float(loss.item())
+    steps = 20
+    tot, per, _ = timed(graph.replay, steps, 2)
+    ms = tot / steps
+    samples = nt * 1024
+    return {"workload": "roughness_map_256x256", "texels": nt, "samples_per_step": samples,
+            "value": world * samples / (ms * 1e-3) / 1e9, "unit": "Gsamples/s (fwd + adjoint per sample)",
+            "ms_per_step": ms, "steps": steps, "captured": "cuda graph (fit kernel + loss/step kernel)",
+            "loss_first": first, "loss_last": float(loss.item()), "steps_done": int(st["step"].item())}
 
 
 def e2e(vndf, d, n, base, dev, stream, steps, warm, barrier, world):

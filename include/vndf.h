@@ -255,6 +255,51 @@ int vndf_albedo_autotune(int32_t n_queries,
                          float *E, void *workspace, size_t workspace_bytes,
                          int32_t *best_config, float *best_ms, void *cuda_stream);
 
+/* Device workspace (bytes) for vndf_fit_step: one float per texel. */
+size_t vndf_fit_workspace_bytes(int32_t n_texels);
+
+/*
+ * vndf_fit_step -- one optimisation step of an anisotropic roughness map so
+ * that the mean of its sampled visible normals matches a target map: the
+ * reparameterised use of the sampler that its adjoint exists for.  Per texel
+ * t, S = samples_per_texel normals are drawn with the spherical-cap sampler
+ * (Sec. 2 steps (1)-(3), Sec. 3.3) from Philox stream stream_id + t at global
+ * indices counter_base + (step - 1) S + j, so every step draws fresh samples;
+ *   m_t  = (1/S) sum_j wm_tj,      loss = (1 / 3T) sum_t |m_t - target_t|^2,
+ * the gradient with respect to (alpha_x, alpha_y) goes through the adjoint of
+ * vndf_sample_backward, and Adam (Kingma & Ba 2015, with bias correction at
+ * the 1-based step) updates alpha, which is then clamped to
+ * [alpha_min, alpha_max].  The paper defines the sampler only; this loop is
+ * the library's use of it.
+ *   n_texels, samples_per_texel   T >= 0 and 1 <= S <= 2^20.
+ *   wi_*, target_*      per-texel incident direction and target mean (read).
+ *   alpha_x, alpha_y    per-texel roughness (read and updated in place).
+ *   adam_m_*, adam_v_*  Adam moments (read and updated; zero before step 1).
+ *   step                one int64 in device memory: the number of completed
+ *                       steps.  The call performs step *step + 1 and adds one
+ *                       at the end, in stream order, so a CUDA graph that
+ *                       captured this call advances on every replay.
+ *   lr, beta1, beta2, eps, alpha_min, alpha_max   optimiser settings
+ *                       (0 <= beta < 1, 0 < alpha_min <= alpha_max).
+ *   loss                output, one float (device; NULL = skip): the loss at
+ *                       the parameters before this step's update.
+ *   workspace           device scratch of >= vndf_fit_workspace_bytes(T)
+ *                       bytes (caller-owned; contents ignored on entry).
+ * All sums run in a fixed order, so a run is bit-reproducible and resumable
+ * from saved (alpha, moments, step).
+ * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, ALIGN, ARG,
+ * WORKSPACE, CUDA).
+ */
+int vndf_fit_step(int32_t n_texels, int32_t samples_per_texel,
+                  const float *wi_x, const float *wi_y, const float *wi_z,
+                  const float *target_x, const float *target_y, const float *target_z,
+                  float *alpha_x, float *alpha_y,
+                  float *adam_m_x, float *adam_m_y, float *adam_v_x, float *adam_v_y,
+                  int64_t *step,
+                  float lr, float beta1, float beta2, float eps, float alpha_min, float alpha_max,
+                  uint64_t seed, uint64_t counter_base, uint32_t stream_id,
+                  float *loss, void *workspace, size_t workspace_bytes, void *cuda_stream);
+
 /* Size of the fixed device scratch array behind vndf_albedo_batched_noalloc:
  * 8 MiB.  A batch fits when vndf_albedo_workspace_bytes(n_queries,
  * max_samples_per_query) is at most this; 4096 queries of up to 65536 samples

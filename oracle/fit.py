@@ -42,12 +42,17 @@ def lobe_means(u1, u2, wi, ax, ay):
     return wm.reshape(3, t, s).mean(axis=2)
 
 
-def loss_and_grad(u1, u2, wi, ax, ay, target):
-    """(L, dL/dax (T,), dL/day (T,), m (3, T)) at fixed uniforms."""
+def loss_and_grad(u1, u2, wi, ax, ay, target, n_total=None):
+    """(L, dL/dax (T,), dL/day (T,), m (3, T)) at fixed uniforms.
+
+    n_total: number of texels of the whole map when these T texels are a subset
+    of it (the MSE divides by 3 n_total); defaults to T.
+    """
     t, s = u1.shape
+    nt = t if n_total is None else int(n_total)
     m = lobe_means(u1, u2, wi, ax, ay)
     diff = m - target
-    loss = (diff ** 2).sum() / (3.0 * t)
+    loss = (diff ** 2).sum() / (3.0 * nt)
     wib = np.repeat(np.asarray(wi)[:, :, None], s, axis=2).reshape(3, -1).astype(np.complex128)
     g = []
     for which in (0, 1):
@@ -59,7 +64,7 @@ def loss_and_grad(u1, u2, wi, ax, ay, target):
             ayc = ayc + 1j * H_CS
         dwm = np.imag(sample_vndf(u1.reshape(-1), u2.reshape(-1), wib, axc, ayc)) / H_CS
         dm = dwm.reshape(3, t, s).mean(axis=2)
-        g.append((2.0 / (3.0 * t)) * (diff * dm).sum(axis=0))
+        g.append((2.0 / (3.0 * nt)) * (diff * dm).sum(axis=0))
     return loss, g[0], g[1], m
 
 
@@ -73,11 +78,15 @@ def adam(param, grad, m, v, step, lr, beta1, beta2, eps):
 
 
 def fit_step(state, wi, target, samples, step, seed, counter_base=0, stream_base=0, lr=1e-2, beta1=0.9,
-             beta2=0.999, eps=1e-8, alpha_min=1e-3, alpha_max=1.0):
-    """One fitting step.  state: dict with ax, ay, mx, my, vx, vy (each (T,)).  Returns (new state, loss)."""
+             beta2=0.999, eps=1e-8, alpha_min=1e-3, alpha_max=1.0, n_total=None):
+    """One fitting step.  state: dict with ax, ay, mx, my, vx, vy (each (T,)).
+
+    Returns (new state, loss, (dL/dax, dL/day)).  With n_total, the T texels are a
+    subset of a map of n_total texels that starts at stream stream_base.
+    """
     t = wi.shape[1]
     u1, u2 = texel_uniforms(t, samples, step, seed, counter_base, stream_base)
-    loss, gx, gy, _ = loss_and_grad(u1, u2, wi, state["ax"], state["ay"], target)
+    loss, gx, gy, _ = loss_and_grad(u1, u2, wi, state["ax"], state["ay"], target, n_total)
     ax, mx, vx = adam(state["ax"], gx, state["mx"], state["vx"], step, lr, beta1, beta2, eps)
     ay, my, vy = adam(state["ay"], gy, state["my"], state["vy"], step, lr, beta1, beta2, eps)
     new = {"ax": np.clip(ax, alpha_min, alpha_max), "ay": np.clip(ay, alpha_min, alpha_max),

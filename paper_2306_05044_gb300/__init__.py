@@ -46,6 +46,9 @@ SIGNATURES = {
                                            _P, _P]),
     "vndf_albedo_autotune": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, _P, _I32, _F, _U64, _U64, _U32, _P, _P, _SZ,
                                             _P, _P, _P]),
+    "vndf_fit_workspace_bytes": (_SZ, [_I32]),
+    "vndf_fit_step": (ctypes.c_int, [_I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _F, _F, _F, _F,
+                                     _F, _F, _U64, _U64, _U32, _P, _P, _SZ, _P]),
     "vndf_albedo_batched_noalloc": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, _P, _I32, _F, _U64, _U64, _U32, _P,
                                                    _P, _P]),
 }
@@ -272,3 +275,39 @@ def vndf_albedo_autotune(wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples, max_samp
                                      ctypes.byref(ms), _stream(stream, wi_x.device))
     _check("vndf_albedo_autotune", st)
     return tuple(best), ms.value
+
+
+def vndf_fit_workspace_bytes(n_texels):
+    return int(load().vndf_fit_workspace_bytes(int(n_texels)))
+
+
+def vndf_fit_step(state, wi_x, wi_y, wi_z, target_x, target_y, target_z, samples_per_texel=1024, lr=1e-2,
+                  beta1=0.9, beta2=0.999, eps=1e-8, alpha_min=1e-3, alpha_max=1.0, seed=5, counter_base=0,
+                  stream_id=0, loss=None, workspace=None, stream=None):
+    """One fitting step in place; see vndf_fit_step in include/vndf.h.
+
+    state: dict of device tensors alpha_x, alpha_y, m_x, m_y, v_x, v_y (float32, one per texel) and
+    step (int64, one element).  Returns the loss tensor (one float, before the update) or None.
+    """
+    nt = wi_x.numel()
+    if workspace is None:
+        workspace = torch.empty(max(vndf_fit_workspace_bytes(nt), 4), dtype=torch.uint8, device=wi_x.device)
+    st = load().vndf_fit_step(
+        nt, int(samples_per_texel), _ptr(wi_x, "wi_x"), _ptr(wi_y, "wi_y"), _ptr(wi_z, "wi_z"),
+        _ptr(target_x, "target_x"), _ptr(target_y, "target_y"), _ptr(target_z, "target_z"),
+        _ptr(state["alpha_x"], "alpha_x"), _ptr(state["alpha_y"], "alpha_y"), _ptr(state["m_x"], "m_x"),
+        _ptr(state["m_y"], "m_y"), _ptr(state["v_x"], "v_x"), _ptr(state["v_y"], "v_y"),
+        _ptr(state["step"], "step", torch.int64), float(lr), float(beta1), float(beta2), float(eps),
+        float(alpha_min), float(alpha_max), int(seed) & (2**64 - 1), int(counter_base) & (2**64 - 1),
+        int(stream_id) & 0xFFFFFFFF, _ptr(loss, "loss"), _ptr(workspace, "workspace", torch.uint8),
+        int(workspace.numel()), _stream(stream, wi_x.device))
+    _check("vndf_fit_step", st)
+    return loss
+
+
+def fit_state(alpha_x, alpha_y):
+    """Fresh optimiser state for vndf_fit_step (copies of the initial maps, zero moments, step 0)."""
+    z = torch.zeros_like(alpha_x)
+    return {"alpha_x": alpha_x.clone(), "alpha_y": alpha_y.clone(), "m_x": z.clone(), "m_y": z.clone(),
+            "v_x": z.clone(), "v_y": z.clone(),
+            "step": torch.zeros(1, dtype=torch.int64, device=alpha_x.device)}

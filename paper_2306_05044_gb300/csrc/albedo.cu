@@ -154,25 +154,6 @@ __device__ __forceinline__ float albedo_weight(const QueryConst& c, float f0, fl
   return oz > 0.f ? fr * g : 0.f;
 }
 
-// Uniforms of samples j0, j0+1 (j0 even) of one Philox stream.
-__device__ __forceinline__ void uniforms2(const Rng& r, uint64_t j0, float& a1, float& a2, float& b1, float& b2) {
-  const uint64_t g0 = r.base + j0;
-  if ((g0 & 1u) == 0) {
-    const uint4 w = philox_block(r, g0 >> 1);
-    a1 = word_to_unit(w.x);
-    a2 = word_to_unit(w.y);
-    b1 = word_to_unit(w.z);
-    b2 = word_to_unit(w.w);
-  } else {
-    const uint4 w = philox_block(r, g0 >> 1);
-    const uint4 x = philox_block(r, (g0 + 1) >> 1);
-    a1 = word_to_unit(w.z);
-    a2 = word_to_unit(w.w);
-    b1 = word_to_unit(x.x);
-    b2 = word_to_unit(x.y);
-  }
-}
-
 __device__ __forceinline__ float warp_tree(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

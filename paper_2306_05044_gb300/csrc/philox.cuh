@@ -84,4 +84,24 @@ __device__ __forceinline__ void uniforms4(const Rng& r, uint64_t i0, float (&u1)
   }
 }
 
+// Uniforms of samples j0, j0+1 (j0 even): one Philox call when the global index
+// of j0 is even, two when it is odd.
+__device__ __forceinline__ void uniforms2(const Rng& r, uint64_t j0, float& a1, float& a2, float& b1, float& b2) {
+  const uint64_t g0 = r.base + j0;
+  if ((g0 & 1u) == 0) {
+    const uint4 w = philox_block(r, g0 >> 1);
+    a1 = word_to_unit(w.x);
+    a2 = word_to_unit(w.y);
+    b1 = word_to_unit(w.z);
+    b2 = word_to_unit(w.w);
+  } else {
+    const uint4 w = philox_block(r, g0 >> 1);
+    const uint4 x = philox_block(r, (g0 + 1) >> 1);
+    a1 = word_to_unit(w.z);
+    a2 = word_to_unit(w.w);
+    b1 = word_to_unit(x.x);
+    b2 = word_to_unit(x.y);
+  }
+}
+
 }  // namespace vndf

@@ -30,6 +30,9 @@ struct Grad5 {
 
 // Adjoint of (wm, pdf) for one sample.  gmx, gmy, gmz: adjoint of wm; gpdf:
 // adjoint of pdf; glog: adjoint of log(pdf).  Also returns the forward values.
+// With PDF_TERMS = false the pdf adjoints are taken as zero at compile time and
+// the returned pdf is not computed (0).
+template <bool PDF_TERMS = true>
 __device__ __forceinline__ Grad5 cap_backward_one(float wx, float wy, float wz, float ax, float ay, float u1,
                                                   float u2, float gmx, float gmy, float gmz, float gpdf,
                                                   float glog, float& mx, float& my, float& mz, float& pdf) {
@@ -59,15 +62,22 @@ __device__ __forceinline__ Grad5 cap_backward_one(float wx, float wy, float wz, 
   mz = vz * rv;
   const float hh = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
   // one reciprocal of the pdf denominator gives 1/hh, 1/a, 1/ax and 1/ay
-  const float rden = __fdividef(1.f, kPi * ax * ay * a * hh);
-  pdf = vv * vv * rv * rden;
-  const float p_ = kPi * rden;
-  const float q1 = ax * ay * p_;
-  const float q2 = a * hh * p_;
-  const float rhh = q1 * a, ra = q1 * hh, rax = ay * q2, ray = ax * q2;
+  float rhh = 0.f, ra = 0.f, rax = 0.f, ray = 0.f, glp = 0.f;
+  pdf = 0.f;
+  if constexpr (PDF_TERMS) {
+    const float rden = __fdividef(1.f, kPi * ax * ay * a * hh);
+    pdf = vv * vv * rv * rden;
+    const float p_ = kPi * rden;
+    const float q1 = ax * ay * p_;
+    const float q2 = a * hh * p_;
+    rhh = q1 * a;
+    ra = q1 * hh;
+    rax = ay * q2;
+    ray = ax * q2;
+    glp = fmaf(gpdf, pdf, glog);  // adjoint of log pdf
+  }
 
   // ---- reverse
-  const float glp = fmaf(gpdf, pdf, glog);  // adjoint of log pdf
   // log pdf = 1.5 log vv - log pi - log ax - log ay - log a - log hh
   const float g_vv = 1.5f * glp * rv * rv;
   float g_ax = -glp * rax;
