@@ -56,6 +56,7 @@ def parse_args():
     p.add_argument("--no-fwd-bwd", action="store_true")
     p.add_argument("--no-albedo", action="store_true")
     p.add_argument("--no-fit", action="store_true")
+    p.add_argument("--no-microbench", action="store_true")
     p.add_argument("--log2n-adjoint", type=int, default=24)
     return p.parse_args()
 
@@ -350,6 +351,9 @@ def run_ours(args, rank, world):
         result["albedo"] = albedo(vndf, dev, rank, world, timed)
         result["gpu_launches_albedo"] = 2 * result["albedo"]["steps"]
 
+    if not args.no_microbench:
+        result["paper_protocol"] = microbench(vndf, dev, world, timed)
+
     if not args.no_fit:
         result["fit"] = fit_leg(vndf, dev, rank, world, timed)
         result["gpu_launches_fit"] = 2 * result["fit"]["steps"]
@@ -416,6 +420,22 @@ def albedo(vndf, dev, rank, world, timed):
             "config": {"warps_per_cta": best[0], "groups_per_item": best[1], "ctas_per_sm": best[2]},
             "captured": "cuda graph (prologue + persistent kernel)",
             "E_range": [float(E.min().item()), float(E.max().item())]}
+
+
+def microbench(vndf, dev, world, timed):
+    """The paper's GPU protocol: 64 samples per lane from register inputs, only sums written (ALU-bound)."""
+    import torch
+    lanes, spl = 1 << 22, 64
+    sums = torch.empty(lanes, 4, device=dev)
+    out = {"protocol": "64 samples per lane, inputs in registers, 16 B written per lane", "lanes": lanes,
+           "samples_per_step": lanes * spl}
+    for method in ("cap", "polar"):
+        tot, per, _ = timed(lambda: vndf.vndf_microbench(lanes, spl, method, 1, sums=sums), 20, 3)
+        ms = tot / 20
+        out[method] = {"value": world * lanes * spl / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms}
+    out["cap_over_prior"] = out["cap"]["value"] / out["polar"]["value"]
+    out["paper_reference"] = "paper: cap faster by 52.96 % (Arc A770) and 39.25 % (RTX 2080), DX12 compute"
+    return out
 
 
 def fit_leg(vndf, dev, rank, world, timed):

@@ -300,6 +300,26 @@ int vndf_fit_step(int32_t n_texels, int32_t samples_per_texel,
                   uint64_t seed, uint64_t counter_base, uint32_t stream_id,
                   float *loss, void *workspace, size_t workspace_bytes, void *cuda_stream);
 
+/*
+ * vndf_microbench -- the paper's GPU benchmark protocol (Sec. 4, "GPU
+ * Synthetic Benchmark": the GGX VNDF sampler called 64 times per lane) as a
+ * kernel.  Each lane draws its incident direction and roughness in registers,
+ * samples `samples_per_lane` normals with `method` and their fused pdf, and
+ * writes the four sums (sum wm.x, sum wm.y, sum wm.z, sum pdf), so only
+ * 16 bytes per lane reach memory and the time measures the sampler's
+ * arithmetic.  Lane l's inputs come from Philox4x32-10 block
+ * (l mod 2^32, l >> 32, 0xffffffff, 0) with key = seed, as 24-bit uniforms
+ * v0..v3: cos(theta_i) = 1e-4 + (1 - 1e-4) v0, phi_i = 2 pi v1,
+ * alpha_x = 1e-3^(1 - v2), alpha_y = 1e-3^(1 - v3).  Sample j of lane l uses
+ * the vndf_sample layout with stream 0 and global index l * samples_per_lane + j.
+ *   lanes              number of lanes (0 <= lanes < 2^40).
+ *   samples_per_lane   1 .. 2^20 (the paper uses 64).
+ *   sums               output, 4 floats per lane (device, 16-byte aligned).
+ * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, ALIGN, METHOD, CUDA).
+ */
+int vndf_microbench(int64_t lanes, int32_t samples_per_lane, int method, uint64_t seed,
+                    float *sums, void *cuda_stream);
+
 /* Size of the fixed device scratch array behind vndf_albedo_batched_noalloc:
  * 8 MiB.  A batch fits when vndf_albedo_workspace_bytes(n_queries,
  * max_samples_per_query) is at most this; 4096 queries of up to 65536 samples

@@ -1,0 +1,82 @@
+// The paper's GPU benchmark protocol (Sec. 4, "GPU Synthetic Benchmark": the
+// sampler called 64 times per lane) as a CUDA kernel: every lane draws its own
+// incident direction and roughness in registers, samples `samples_per_lane`
+// normals with the chosen hemisphere sampler and its fused pdf, and writes only
+// the four sums (sum wm.x, sum wm.y, sum wm.z, sum pdf).  Memory traffic is 16
+// bytes per lane, so the time measures the samplers' arithmetic, which is what
+// the paper compares between the spherical-cap and the cross-section sampler.
+//
+// Per-lane inputs, from Philox4x32-10 block (l mod 2^32, l >> 32, 0xffffffff, 0)
+// with key = seed (words w0..w3 as 24-bit uniforms v0..v3):
+//   cos(theta_i) = 1e-4 + (1 - 1e-4) v0,  phi_i = 2 pi v1,
+//   alpha_x = 1e-3^(1 - v2),  alpha_y = 1e-3^(1 - v3)   (log-uniform in [1e-3, 1]).
+// Sample j of lane l uses the sampling layout of vndf_sample with stream 0 and
+// global index l * samples_per_lane + j.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "philox.cuh"
+#include "vndf_math.cuh"
+
+namespace vndf {
+
+constexpr int kMicroBlock = 256;
+
+template <int METHOD>
+__global__ void __launch_bounds__(kMicroBlock) microbench_kernel(int64_t lanes, int32_t spl, Rng r, float4* out) {
+  const int64_t stride = int64_t(gridDim.x) * kMicroBlock;
+  for (int64_t l = int64_t(blockIdx.x) * kMicroBlock + threadIdx.x; l < lanes; l += stride) {
+    const uint4 w = philox4x32_10(make_uint4(uint32_t(l), uint32_t(uint64_t(l) >> 32), 0xffffffffu, 0u), r.k0, r.k1);
+    const float ct = fmaf(1.f - 1e-4f, word_to_unit(w.x), 1e-4f);
+    float sp, cp;
+    sincospi_taylor(2.f * word_to_unit(w.y), sp, cp);
+    const float st = sqrtf(fmaxf(fmaf(-ct, ct, 1.f), 0.f));
+    const float wx = st * cp, wy = st * sp, wz = ct;
+    constexpr float kLn1e3 = -6.90775527898213705f;  // ln(1e-3)
+    const float ax = __expf(kLn1e3 * (1.f - word_to_unit(w.z)));
+    const float ay = __expf(kLn1e3 * (1.f - word_to_unit(w.w)));
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint64_t j0 = uint64_t(l) * uint64_t(spl);
+    for (int32_t j = 0; j < spl; j += 2) {
+      float a1, a2, b1, b2;
+      uniforms2(r, j0 + uint64_t(j), a1, a2, b1, b2);
+      float mx, my, mz, p;
+      sample_one<METHOD, true>(wx, wy, wz, ax, ay, a1, a2, mx, my, mz, p);
+      acc.x += mx;
+      acc.y += my;
+      acc.z += mz;
+      acc.w += p;
+      if (j + 1 < spl) {
+        sample_one<METHOD, true>(wx, wy, wz, ax, ay, b1, b2, mx, my, mz, p);
+        acc.x += mx;
+        acc.y += my;
+        acc.z += mz;
+        acc.w += p;
+      }
+    }
+    out[l] = acc;
+  }
+}
+
+}  // namespace vndf
+
+using namespace vndf;
+
+extern "C" int vndf_microbench(int64_t lanes, int32_t samples_per_lane, int method, uint64_t seed, float* sums,
+                               void* cuda_stream) {
+  if (lanes < 0 || lanes >= (int64_t(1) << 40) || samples_per_lane < 1 || samples_per_lane > (1 << 20))
+    return VNDF_ERR_SIZE;
+  if (method != VNDF_METHOD_SPHERICAL_CAP && method != VNDF_METHOD_POLAR_DISK) return VNDF_ERR_METHOD;
+  if (lanes == 0) return VNDF_OK;
+  if (!sums) return VNDF_ERR_NULL;
+  if (!aligned(sums, 16)) return VNDF_ERR_ALIGN;
+  const Rng r = make_rng(seed, 0, 0);
+  const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const unsigned grid = grid_for(lanes, kMicroBlock, 8, 16);
+  float4* out = reinterpret_cast<float4*>(sums);
+  if (method == VNDF_METHOD_SPHERICAL_CAP)
+    microbench_kernel<kMethodCap><<<grid, kMicroBlock, 0, s>>>(lanes, samples_per_lane, r, out);
+  else
+    microbench_kernel<kMethodPolar><<<grid, kMicroBlock, 0, s>>>(lanes, samples_per_lane, r, out);
+  return launch_status();
+}
