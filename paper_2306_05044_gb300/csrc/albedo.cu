@@ -15,12 +15,13 @@
 //   adds the 32 lane sums with a fixed butterfly.  That order is a property of
 //   the data, not of the launch, so E is bit-identical for every launch shape.
 // * An item is `groups_per_item` consecutive groups of one query.  A one-block
-//   prologue computes per-query item counts and their exclusive scan; the
-//   persistent kernel's CTAs claim items from an atomic counter, write one
-//   partial per group, and the CTA that completes a query's last item sums the
-//   query's group partials (fixed lane-strided order + butterfly) into E_q.
+//   prologue computes per-query item counts and their exclusive scan; each warp
+//   of the persistent kernel then takes items w, w + W, w + 2W, ... (W = warps
+//   in the grid) on its own, with no block barrier, writes one partial per
+//   group, and the warp that completes a query's last item sums the query's
+//   group partials (fixed lane-strided order + butterfly) into E_q.
 // * Nothing waits on anything: completion is detected with an atomic counter
-//   per query (fence, then atomicAdd), so no CTA ever spins.
+//   per query (fence, then atomicAdd), so no warp ever spins.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -162,38 +163,29 @@ __device__ __forceinline__ float warp_tree(float v) {
 
 // ---------------------------------------------------------------- persistent kernel
 __global__ void __launch_bounds__(512) albedo_kernel(AlbedoArgs a) {
-  __shared__ int32_t s_item, s_q, s_last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
   const int32_t* offsets = a.ctl + 2;
   int32_t* done = a.ctl + 3 + a.nq;
   const int32_t total = a.ctl[1];
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const int32_t item = atomicAdd(a.ctl, 1);
-      int32_t q = -1;
-      if (item < total) {  // last q with offsets[q] <= item
-        int32_t lo = 0, hi = a.nq - 1;
-        while (lo < hi) {
-          const int32_t mid = (lo + hi + 1) >> 1;
-          if (offsets[mid] <= item) lo = mid;
-          else hi = mid - 1;
-        }
-        q = lo;
-      }
-      s_item = item;
-      s_q = q;
+  for (int64_t item = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); item < total;
+       item += warps) {
+    // the query of this item: last q with offsets[q] <= item (same search in every lane)
+    int32_t lo = 0, hi = a.nq - 1;
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if (offsets[mid] <= int32_t(item)) lo = mid;
+      else hi = mid - 1;
     }
-    __syncthreads();
-    const int32_t item = s_item, q = s_q;
-    if (item >= total) break;
+    const int32_t q = lo;
     const int32_t n = a.ns[q];
     const int32_t groups = (n + kGroupSamples - 1) / kGroupSamples;
-    const int32_t k = item - offsets[q];
+    const int32_t k = int32_t(item) - offsets[q];
     const int32_t g_end = min(groups, (k + 1) * a.groups_per_item);
     const QueryConst c = query_const(a, q);
     Rng r = a.rng;
     r.stream = a.rng.stream + uint32_t(q);
-    for (int32_t g = k * a.groups_per_item + warp; g < g_end; g += nwarps) {
+    for (int32_t g = k * a.groups_per_item; g < g_end; ++g) {
       const int32_t j0 = g * kGroupSamples + lane * kLaneSamples;
       float acc = 0.f;
 #pragma unroll
@@ -206,25 +198,21 @@ __global__ void __launch_bounds__(512) albedo_kernel(AlbedoArgs a) {
         acc += j0 + s + 1 < n ? w1 : 0.f;
       }
       acc = warp_tree(acc);
-      if (lane == 0) {
-        a.partials[size_t(q) * a.gmax + g] = acc;
-        __threadfence();
-      }
+      if (lane == 0) a.partials[size_t(q) * a.gmax + g] = acc;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    int32_t last = 0;
+    if (lane == 0) {
+      __threadfence();
       const int32_t items_q = offsets[q + 1] - offsets[q];
-      s_last = atomicAdd(done + q, 1) == items_q - 1;
+      last = atomicAdd(done + q, 1) == items_q - 1;
     }
-    __syncthreads();
-    if (s_last && warp == 0) {
+    if (__shfl_sync(0xffffffffu, last, 0)) {
       __threadfence();
       float sum = 0.f;
       for (int32_t g = lane; g < groups; g += 32) sum += __ldcg(a.partials + size_t(q) * a.gmax + g);
       sum = warp_tree(sum);
       if (lane == 0) a.E[q] = sum / float(n);
     }
-    __syncthreads();
   }
 }
 
@@ -248,7 +236,7 @@ AlbedoConfig current_config() {
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   if (dev >= 0 && dev < 64 && g_has_tuned[dev]) return g_tuned[dev];
-  return AlbedoConfig{8, 2, 4};
+  return AlbedoConfig{8, 1, 8};
 }
 
 int launch_albedo(AlbedoArgs a, const AlbedoConfig& c, cudaStream_t s) {
@@ -339,15 +327,15 @@ extern "C" int vndf_albedo_autotune(int32_t n_queries, const float* wi_x, const 
   AlbedoArgs a = albedo_args(n_queries, wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples, max_samples_per_query, f0,
                              seed, counter_base, stream_id, E, workspace);
   static const int32_t warps[] = {4, 8, 16};
-  static const int32_t gpis[] = {1, 2, 4, 8};
-  static const int32_t ctas[] = {2, 4, 8};
+  static const int32_t gpis[] = {1, 2, 4};
+  static const int32_t ctas[] = {4, 8, 16};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return VNDF_ERR_CUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) {
     cudaEventDestroy(e0);
     return VNDF_ERR_CUDA;
   }
-  AlbedoConfig best{8, 2, 4};
+  AlbedoConfig best{8, 1, 8};
   float best_t = INFINITY;
   int rc = VNDF_OK;
   for (int32_t w : warps)
