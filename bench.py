@@ -199,27 +199,33 @@ class ClockSampler:
                 "samples": len(rows), "source": "nvidia-smi 200 ms"}
 
 
-def time_oracle_sample(n, seed=2):
-    """Oracle (FP64 numpy) over the first n samples of the workload; returns seconds."""
+def time_oracle_sample(n, seed=2, chunk=1 << 22):
+    """Oracle (FP64 numpy) over the first n samples of the workload, timed in chunks; returns seconds."""
     import numpy as np
     import torch
 
     import workloads
     from oracle import philox, vndf
-    d = workloads.anisotropic_stream(n=n, device="cpu")
-    wi = np.stack([d[k].numpy() for k in ("wi_x", "wi_y", "wi_z")])
-    ax, ay = d["alpha_x"].numpy(), d["alpha_y"].numpy()
     torch.set_num_threads(1)
-    t0 = time.perf_counter()
-    u1, u2 = philox.sample_uniforms(seed, 0, 0, n)
-    vndf.sample_vndf_with_pdf(u1, u2, wi, ax, ay, "cap")
-    return time.perf_counter() - t0
+    d = workloads.anisotropic_stream(n=n, device="cpu")
+    cols = {k: d[k].numpy() for k in ("wi_x", "wi_y", "wi_z", "alpha_x", "alpha_y")}
+    del d
+    total = 0.0
+    for off in range(0, n, chunk):
+        m = min(chunk, n - off)
+        wi = np.stack([cols[k][off:off + m] for k in ("wi_x", "wi_y", "wi_z")])
+        ax, ay = cols["alpha_x"][off:off + m], cols["alpha_y"][off:off + m]
+        t0 = time.perf_counter()
+        u1, u2 = philox.sample_uniforms(seed, off, 0, m)
+        vndf.sample_vndf_with_pdf(u1, u2, wi, ax, ay, "cap")
+        total += time.perf_counter() - t0
+    return total
 
 
 def cpu_baseline(budget_s=15.0):
     probe = 1 << 16
     t = time_oracle_sample(probe)
-    n = int(min(1 << 24, max(probe, probe * budget_s / max(t, 1e-6))))
+    n = int(min(1 << 25, max(probe, probe * budget_s / max(t, 1e-6))))
     n = 1 << int(math.log2(n))
     t = time_oracle_sample(n)
     return {"value": n / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -109,6 +109,15 @@ __device__ __forceinline__ void cap_half_vector(const Stretched& i, float u1, fl
 }
 
 // Heitz 2018 cross-section sampler: returns a unit hemisphere normal h.
+// Same construction as the printed listing (basis (w1, w2, i), a uniform point
+// (t1, t2) on the unit disk, the far half compressed by s = (1 + i.z)/2, lifted
+// onto the hemisphere along i), with the rounding care the cap sampler gets:
+// every quantity that cancels near the rim of the disk is rewritten exactly,
+//   1 - t1^2     = (1 - u2) + u2 sin^2(phi)                       (= q^2),
+//   q -/+ t2o    = (1 - u2) / (q +/- t2o)      (t2o = sqrt(u2) sin(phi); q^2 - t2o^2 = 1 - u2),
+//   1 - s        = (i.x^2 + i.y^2) / (2 (1 + i.z)),
+//   1 - t1^2 - t2^2 = (q - t2)(q + t2) = s (q - t2o) (2 (1 - s) q + s (q + t2o)),
+// so all factors are sums of non-negative terms.
 __device__ __forceinline__ void polar_disk_normal(const Stretched& i, float u1, float u2,
                                                   float& hx, float& hy, float& hz) {
   const float tmp = fmaf(i.x, i.x, i.y * i.y);
@@ -126,11 +135,19 @@ __device__ __forceinline__ void polar_disk_normal(const Stretched& i, float u1, 
   sincospi_taylor(2.f * u1, sp, cp);
   const float r = sqrtf(u2);
   const float t1 = r * cp;
-  float t2 = r * sp;
-  const float s = 0.5f * (1.f + i.z);
-  const float one_m_t1sq = fmaf(-t1, t1, 1.f);
-  t2 = fmaf(1.f - s, sqrtf(one_m_t1sq), s * t2);
-  const float ti = sqrtf(fmaxf(fmaf(-t2, t2, one_m_t1sq), 0.f));
+  const float t2o = r * sp;
+  const float om = 1.f - u2;
+  const float q = sqrtf(fmaf(u2 * sp, sp, om));    // sqrt(1 - t1^2)
+  const float a = 1.f + i.z;
+  const float s = 0.5f * a;
+  const float oms = __fdividef(0.5f * tmp, a);     // 1 - s
+  const bool pos = t2o >= 0.f;
+  const float big = pos ? q + t2o : q - t2o;        // no cancellation either way
+  const float small = __fdividef(om, big);          // the other one of q -/+ t2o
+  const float qm = pos ? small : big;               // q - t2o
+  const float qp = pos ? big : small;               // q + t2o
+  const float t2 = fmaf(oms, q, s * t2o);
+  const float ti = sqrtf(s * qm * fmaf(2.f * oms, q, s * qp));
   hx = fmaf(t1, w1x, fmaf(t2, w2x, ti * i.x));
   hy = fmaf(t1, w1y, fmaf(t2, w2y, ti * i.y));
   hz = fmaf(t2, w2z, ti * i.z);

@@ -163,7 +163,8 @@ def test_domain_edges_and_extremes(v):
 
 
 def test_prior_sampler_parity(v):
-    """The prior (polar-disk) sampler against its own FP64 oracle, same I/O as the cap sampler."""
+    """The prior (polar-disk) sampler against its own FP64 oracle (the paper's prior sampler, Sec. 2
+    step (2)), same I/O as the cap sampler."""
     n = (1 << 20) + 1
     d = workloads.anisotropic_stream(n=n, device=DEV)
     wx, wy, wz, pdf = v.vndf_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], seed=2,
@@ -177,8 +178,10 @@ def test_prior_sampler_parity(v):
     rel = np.abs(pdf.cpu().numpy() / pref - 1.0)
     print(f"prior: max angle {ang.max():.3e} p99.99 {np.quantile(ang, 0.9999):.3e} "
           f"tail>4e-6 {(ang > 4e-6).mean():.2e}; pdf max rel {rel.max():.3e} tail>1e-5 {(rel > 1e-5).mean():.2e}")
-    assert np.median(ang) < 1e-7 and np.quantile(ang, 0.99) < 4e-6
-    assert np.median(rel) < 1e-6 and np.quantile(rel, 0.99) < 1e-5
+    # the prior kernel gets the same cancellation-free rewrites as the cap sampler, so it must
+    # meet the same accuracy: "faster at equal accuracy" compares like with like
+    assert (ang > 4e-6).mean() < 1e-4 and ang.max() < 1e-3
+    assert (rel > 1e-5).mean() < 1e-4
 
 
 def test_pdf_entry_at_given_normals(v):
