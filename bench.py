@@ -37,9 +37,10 @@ UNIT = "Gsamples/s"
 WORKLOAD = "anisotropic_stream_2e28"
 BYTES_PER_SAMPLE = 36  # in: wi xyz + alpha xy (20 B); out: wm xyz + pdf (16 B)
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ("paper_2306_05044_gb300/csrc/sample.cu", "paper_2306_05044_gb300/csrc/vndf_math.cuh",
-                  "paper_2306_05044_gb300/csrc/philox.cuh", "paper_2306_05044_gb300/csrc/common.cuh")
+CSRC = os.path.join(ROOT, "paper_2306_05044_gb300", "csrc")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "vndf_sample_cap_anisotropic_stream.md")
+ISSUE_FILE = os.path.join(ROOT, "profiles", "compute_kernels_issue.md")
+LANES_PER_SM = 4 * 32  # 4 schedulers x 32 lanes issue one instruction each per clock
 
 
 def parse_args():
@@ -62,32 +63,64 @@ def parse_args():
 
 
 # ----------------------------------------------------------------------------- helpers
-def kernel_source_hash():
+KERNEL_FILES = {
+    "stream": ("sample.cu", "vndf_math.cuh", "philox.cuh", "common.cuh"),
+    "microbench_cap": ("microbench.cu", "vndf_math.cuh", "philox.cuh", "common.cuh"),
+    "microbench_polar": ("microbench.cu", "vndf_math.cuh", "philox.cuh", "common.cuh"),
+    "loss_backward": ("backward.cu", "vndf_adjoint.cuh", "vndf_math.cuh", "philox.cuh", "common.cuh"),
+    "albedo": ("albedo.cu", "vndf_math.cuh", "philox.cuh", "common.cuh"),
+    "fit": ("fit.cu", "vndf_adjoint.cuh", "vndf_math.cuh", "philox.cuh", "common.cuh"),
+}
+
+
+def kernel_source_hash(kernel):
+    """Hash of the CUDA sources a kernel is built from: its profile figures are quoted only while it matches."""
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
+    for f in KERNEL_FILES[kernel]:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode())
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def measured_traffic_per_sample():
-    """DRAM bytes per sample from the committed ncu summary, if it matches the current kernel."""
+def _profile_values(path, kernel):
+    """`key: value` lines of a committed ncu summary for one kernel, or {} when its sources changed."""
     try:
-        text = open(TRAFFIC_FILE).read()
+        text = open(path).read()
     except OSError:
-        return None
+        return {}
     vals = {}
     for line in text.splitlines():
         line = line.strip().strip("-* ")
         if ":" in line:
             k, _, v = line.partition(":")
             vals[k.strip().strip("`")] = v.strip().strip("`")
-    if vals.get("kernel_source_sha") != kernel_source_hash():
-        return None
+    return vals if vals.get(f"kernel_source_sha.{kernel}") == kernel_source_hash(kernel) else {}
+
+
+def measured_traffic_per_sample():
+    """DRAM bytes per sample from the committed ncu summary, if it matches the current kernels."""
     try:
-        return float(vals["dram_bytes_per_sample"])
+        return float(_profile_values(TRAFFIC_FILE, "stream")["dram_bytes_per_sample"])
     except (KeyError, ValueError):
         return None
+
+
+def issue_roofline(kernel, samples, ms, clock_mhz):
+    """ALU issue roofline of a compute-bound kernel: thread instructions per second against
+    SMs x 4 schedulers x 32 lanes x SM clock.  Instructions per sample come from the committed
+    ncu summary (null when the kernel sources changed since)."""
+    import torch
+    try:
+        per = float(_profile_values(ISSUE_FILE, kernel)[f"tinst_per_sample.{kernel}"])
+    except (KeyError, ValueError):
+        return {"bound": "alu", "achieved": None, "peak": None, "frac": None, "unit": "Tinst/s",
+                "note": "instruction count not measured for the current kernel sources"}
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = sms * LANES_PER_SM * clock_mhz * 1e6 / 1e12
+    achieved = per * samples / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s", "frac": achieved / peak,
+            "thread_inst_per_sample": per, "peak_basis": f"{sms} SMs x 128 lanes x {clock_mhz:.0f} MHz"}
 
 
 def hbm_peak():
@@ -349,19 +382,29 @@ def run_ours(args, rank, world):
             "cap_over_prior": value / pv}
         result["gpu_launches_prior"] = steps
 
+    clk = (clock or {}).get("sm_mhz") or (clock or {}).get("sm_max_mhz") or 2070.0
     if not args.no_fwd_bwd:
         result["fwd_bwd"] = fwd_bwd(vndf, dev, rank, world, timed, peak, args.log2n_adjoint)
+        result["fwd_bwd"]["issue"] = issue_roofline("loss_backward", 1 << args.log2n_adjoint,
+                                                    result["fwd_bwd"]["ms_per_step"], clk)
         result["gpu_launches_fwd_bwd"] = 2 * steps
 
     if not args.no_albedo:
         result["albedo"] = albedo(vndf, dev, rank, world, timed)
+        result["albedo"]["issue"] = issue_roofline("albedo", result["albedo"]["samples"],
+                                                   result["albedo"]["ms_per_step"], clk)
         result["gpu_launches_albedo"] = 2 * result["albedo"]["steps"]
 
     if not args.no_microbench:
         result["paper_protocol"] = microbench(vndf, dev, world, timed)
+        for m, k in (("cap", "microbench_cap"), ("polar", "microbench_polar")):
+            result["paper_protocol"][m]["issue"] = issue_roofline(
+                k, result["paper_protocol"]["samples_per_step"], result["paper_protocol"][m]["ms_per_step"], clk)
 
     if not args.no_fit:
         result["fit"] = fit_leg(vndf, dev, rank, world, timed)
+        result["fit"]["issue"] = issue_roofline("fit", result["fit"]["samples_per_step"],
+                                                result["fit"]["ms_per_step"], clk)
         result["gpu_launches_fit"] = 2 * result["fit"]["steps"]
 
     if not args.no_e2e:

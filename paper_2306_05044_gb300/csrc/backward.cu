@@ -234,7 +234,8 @@ __global__ void __launch_bounds__(kBwdBlock, 3) loss_backward_kernel(BwdArgs a, 
 __global__ void __launch_bounds__(1024) sum_partials_kernel(const float* partials, int64_t m, float* out) {
   __shared__ float smem[32];
   float v = 0.f;
-  for (int64_t j = threadIdx.x; j < m; j += 1024) v += partials[j];
+#pragma unroll 8
+  for (int64_t j = threadIdx.x; j < m; j += 1024) v += partials[j];  // loads overlap; adds stay in order
   const float s = block_sum<1024>(v, smem);
   if (threadIdx.x == 0) *out = s;
 }

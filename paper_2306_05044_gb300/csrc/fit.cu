@@ -138,7 +138,8 @@ __global__ void __launch_bounds__(1024) fit_finish_kernel(FitArgs a) {
   float v = 0.f;
   const int32_t per = (a.nt + 1023) / 1024;
   const int32_t t0 = min(a.nt, int32_t(threadIdx.x) * per), t1 = min(a.nt, t0 + per);
-  for (int32_t t = t0; t < t1; ++t) v += a.texel_loss[t];
+#pragma unroll 16
+  for (int32_t t = t0; t < t1; ++t) v += a.texel_loss[t];  // loads overlap; adds stay in order
   v = warp_sum_fit(v);
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
   __syncthreads();
