@@ -300,7 +300,7 @@ def run_ours(args, rank, world):
 
     import paper_2306_05044_gb300 as vndf
     import workloads
-    from paper_2306_05044_gb300 import _build
+    from paper_2306_05044_gb300 import _build, sharding
 
     local = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(local)
@@ -310,8 +310,7 @@ def run_ours(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     vndf.load()
-    n = 1 << args.log2n
-    base = rank * n
+    base, n = sharding.sample_shard(rank, world, 1 << args.log2n)
     d = workloads.anisotropic_stream(n=n, device=dev)
     outs = [torch.empty(n, device=dev) for _ in range(4)]
     stream = torch.cuda.current_stream(dev)
@@ -341,11 +340,7 @@ def run_ours(args, rank, world):
         barrier()
         clock = sampler.stop() if sampler else None
         per = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
-        total = evs[0].elapsed_time(evs[-1])
-        if world > 1:
-            t = torch.tensor([total], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total = float(t.item())
+        total = sharding.max_over_ranks(evs[0].elapsed_time(evs[-1]), dev)
         return total, per, clock
 
     steps, warm = max(args.steps, 1), max(args.warmup, 3)
@@ -563,11 +558,8 @@ def e2e(vndf, d, n, base, dev, stream, steps, warm, barrier, world):
         one_step()
     e1.record(stream)
     barrier()
-    total = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
+    from paper_2306_05044_gb300 import sharding
+    total = sharding.max_over_ranks(e0.elapsed_time(e1), dev)
     return {"value": world * n * steps / (total * 1e-3) / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": 20 * n, "d2h_bytes_per_step": 16 * n,
             "ms_per_step": total / steps, "pipeline": f"{nstreams} streams, {chunk}-sample chunks, pinned host memory"}
