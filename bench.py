@@ -403,7 +403,10 @@ def run_ours(args, rank, world):
         result["gpu_launches_fit"] = 2 * result["fit"]["steps"]
 
     if not args.no_e2e:
-        result["e2e"] = e2e(vndf, d, n, base, dev, stream, steps, warm, barrier, world)
+        piped = e2e(vndf, d, n, base, dev, stream, steps, warm, barrier, world)
+        direct = e2e_zero_copy(vndf, d, n, base, dev, stream, steps, warm, barrier, world)
+        best = max((x for x in (piped, direct) if x is not None), key=lambda x: x["value"])
+        result["e2e"] = dict(best, alternatives={"copy_pipeline": piped, "zero_copy": direct})
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline()
@@ -563,6 +566,38 @@ def e2e(vndf, d, n, base, dev, stream, steps, warm, barrier, world):
     return {"value": world * n * steps / (total * 1e-3) / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": 20 * n, "d2h_bytes_per_step": 16 * n,
             "ms_per_step": total / steps, "pipeline": f"{nstreams} streams, {chunk}-sample chunks, pinned host memory"}
+
+
+def e2e_zero_copy(vndf, d, n, base, dev, stream, steps, warm, barrier, world):
+    """Same step with the kernel reading its inputs from, and writing its outputs to, pinned host memory
+    directly (NVLink-C2C); no staging copies.  None when the device cannot address pinned host memory."""
+    import torch
+
+    from paper_2306_05044_gb300 import sharding
+    keys = ("wi_x", "wi_y", "wi_z", "alpha_x", "alpha_y")
+    host_in = {k: d[k].cpu().pin_memory() for k in keys}
+    host_out = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in range(4)]
+    if not all(vndf.vndf_pointer_device_accessible(t) for t in (*host_in.values(), *host_out)):
+        return None
+
+    def one_step():
+        vndf.vndf_sample(host_in["wi_x"], host_in["wi_y"], host_in["wi_z"], host_in["alpha_x"], host_in["alpha_y"],
+                         seed=2, counter_base=base, wm_x=host_out[0], wm_y=host_out[1], wm_z=host_out[2],
+                         pdf=host_out[3], stream=stream)
+
+    for _ in range(warm):
+        one_step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        one_step()
+    e1.record(stream)
+    barrier()
+    total = sharding.max_over_ranks(e0.elapsed_time(e1), dev)
+    return {"value": world * n * steps / (total * 1e-3) / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": 20 * n, "d2h_bytes_per_step": 16 * n, "ms_per_step": total / steps,
+            "pipeline": "kernel reads and writes pinned host memory directly over NVLink-C2C (no staging copies)"}
 
 
 def main():

@@ -68,6 +68,14 @@ int vndf_abi_version(void);
 /* Static, NUL-terminated description of a status code (never NULL). */
 const char *vndf_status_string(int status);
 
+/* Whether the current CUDA device can dereference p: 1 for device or managed
+ * memory and for page-locked host memory mapped into the device's address
+ * space at the same address (on NVLink-C2C systems such host buffers can be
+ * passed to every entry point directly, and the kernels then read and write
+ * host memory without staging copies); 0 otherwise (including NULL and
+ * ordinary pageable host memory); VNDF_ERR_CUDA if the query fails. */
+int vndf_pointer_device_accessible(const void *p);
+
 /*
  * vndf_rng_uniform -- the uniforms (u1, u2) that sample i would draw in
  * Philox mode (see "Random numbers" above; the paper only requires u in

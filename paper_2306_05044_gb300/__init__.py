@@ -32,6 +32,7 @@ _SZ = ctypes.c_size_t
 SIGNATURES = {
     "vndf_abi_version": (ctypes.c_int, []),
     "vndf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "vndf_pointer_device_accessible": (ctypes.c_int, [_P]),
     "vndf_rng_uniform": (ctypes.c_int, [_I64, _U64, _U64, _U32, _P, _P, _P]),
     "vndf_sample": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _U64, _U64, _U32, ctypes.c_int,
                                    _P, _P, _P, _P, _P]),
@@ -90,6 +91,14 @@ def vndf_abi_version():
     return load().vndf_abi_version()
 
 
+def vndf_pointer_device_accessible(t):
+    """True when the current CUDA device can dereference the tensor's memory (device, or mapped pinned host)."""
+    st = load().vndf_pointer_device_accessible(t.data_ptr())
+    if st < 0:
+        raise VndfError("vndf_pointer_device_accessible", st)
+    return st == 1
+
+
 def _check(func, status):
     if status != VNDF_OK:
         raise VndfError(func, status)
@@ -100,8 +109,8 @@ def _ptr(t, name, dtype=torch.float32):
         return None
     if not isinstance(t, torch.Tensor):
         raise TypeError(f"{name} must be a torch.Tensor")
-    if not t.is_cuda:
-        raise ValueError(f"{name} must live on a CUDA device")
+    if not t.is_cuda and not (torch.cuda.is_available() and t.is_pinned() and vndf_pointer_device_accessible(t)):
+        raise ValueError(f"{name} must live on a CUDA device (or in pinned host memory the device can address)")
     if t.dtype != dtype:
         raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
     if not t.is_contiguous():
@@ -111,12 +120,19 @@ def _ptr(t, name, dtype=torch.float32):
 
 def _stream(stream, device):
     if stream is None:
-        stream = torch.cuda.current_stream(device)
+        stream = torch.cuda.current_stream(device if device.type == "cuda" else None)
     return ctypes.c_void_p(stream.cuda_stream)
 
 
 def _out(t, n, like):
-    return torch.empty(n, dtype=torch.float32, device=like.device) if t is None else t
+    """Output buffer: the given tensor, else device memory beside `like`, else pinned host memory when
+    `like` itself is pinned host memory the device can address."""
+    if t is not None:
+        return t
+    if like.is_cuda:
+        return torch.empty(n, dtype=torch.float32, device=like.device)
+    _ptr(like, "input")  # raises unless `like` is device-addressable pinned host memory
+    return torch.empty(n, dtype=torch.float32, pin_memory=True)
 
 
 def _method(method):

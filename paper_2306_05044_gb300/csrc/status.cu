@@ -16,3 +16,27 @@ extern "C" const char* vndf_status_string(int status) {
     default: return "unknown status";
   }
 }
+
+#include <cuda_runtime.h>
+
+// 1 when the current device can dereference p (device memory, managed memory,
+// or host memory that is page-locked and mapped into the device's address
+// space), 0 when it cannot, VNDF_ERR_CUDA when the query itself fails.
+extern "C" int vndf_pointer_device_accessible(const void* p) {
+  if (p == nullptr) return 0;
+  cudaPointerAttributes attr;
+  const cudaError_t e = cudaPointerGetAttributes(&attr, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error of an unregistered pointer
+    return e == cudaErrorInvalidValue ? 0 : VNDF_ERR_CUDA;
+  }
+  switch (attr.type) {
+    case cudaMemoryTypeDevice:
+    case cudaMemoryTypeManaged:
+      return 1;
+    case cudaMemoryTypeHost:
+      return attr.devicePointer == p ? 1 : 0;
+    default:
+      return 0;
+  }
+}
