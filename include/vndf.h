@@ -323,10 +323,15 @@ int vndf_fit_step(int32_t n_texels, int32_t samples_per_texel,
  * the vndf_sample layout with stream 0 and global index l * samples_per_lane + j.
  *   lanes              number of lanes (0 <= lanes < 2^40).
  *   samples_per_lane   1 .. 2^20 (the paper uses 64).
+ *   precise            spherical cap only: nonzero runs the sampler exactly as
+ *                      vndf_sample does (ill-conditioned samples recomputed in
+ *                      double-float, every sample within 4e-6 rad of FP64);
+ *                      0 runs the plain FP32 sampler, the accuracy class of
+ *                      the prior sampler (which has no such path).
  *   sums               output, 4 floats per lane (device, 16-byte aligned).
  * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, ALIGN, METHOD, CUDA).
  */
-int vndf_microbench(int64_t lanes, int32_t samples_per_lane, int method, uint64_t seed,
+int vndf_microbench(int64_t lanes, int32_t samples_per_lane, int method, int precise, uint64_t seed,
                     float *sums, void *cuda_stream);
 
 /* Size of the fixed device scratch array behind vndf_albedo_batched_noalloc:

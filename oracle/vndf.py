@@ -21,6 +21,8 @@ follow:
 * ``smith_g1``             App. A, Eq. g1 and its hemisphere form
 * ``vndf_pdf``             D_vis = G1(wi) max(0, wi.wm) D(wm) / wi.z (App. A + Eq. 2)
 * ``vndf_pdf_eq1``         Eq. 1 written out literally (transformed hemisphere VNDF)
+* ``vndf_pdf_at_cap_sample`` Eq. 1 at the cap sampler's own hemisphere sample (Sec. 3.2-3.3),
+                           the form that stays accurate near the visibility boundary
 
 Readings where the paper is silent (each is listed in the design notes):
 * Domain: wi.z > 0, alpha_x > 0, alpha_y > 0, all inputs finite.  Outside it a
@@ -263,6 +265,34 @@ def vndf_pdf_eq1(wm, wi, ax, ay):
     wm_std = t / n
     wi_std = warp_to_hemisphere(wi, ax, ay)
     return vndf_std(wm_std, wi_std) * (1.0 / (ax * ay)) / n ** 3
+
+
+def vndf_pdf_at_cap_sample(u1, u2, wi, ax, ay):
+    """Eq. 1 evaluated at the cap sampler's own hemisphere sample (Sec. 3.3).
+
+    For the sample wm = normalize(M^-T h) with h = c + wi' (wi' = M^-1 wi / |.|,
+    c the cap point), the hemisphere normal of Eq. 1 is M^T wm / |M^T wm| = h / |h|
+    and |M^T wm| = |h| / |v| with v = M^-T h.  Since c and wi' are unit vectors,
+    |h|^2 = 2 (1 + c.wi') and h.wi' = |h|^2 / 2, so Eqs. 1-4 give
+        D_vis = (|h| / 2) / (pi (1 + z_i') / 2) * |det M^T| * |v|^3 / |h|^3
+              = |v|^3 / (pi ax ay (1 + z_i') |h|^2).
+    This avoids forming wi . wm, which cancels near the visibility boundary;
+    it is the better-conditioned of the two forms there and equals vndf_pdf
+    elsewhere (a pinned test checks the two against each other).
+    """
+    wi = _stack(*[_as_f64(w) for w in wi])
+    ax = _as_f64(ax)
+    ay = _as_f64(ay)
+    ok = in_domain(wi, ax, ay)
+    wi = np.where(ok, wi, np.array([0.0, 0.0, 1.0]).reshape(3, *([1] * (wi.ndim - 1))))
+    ax = np.where(ok, ax, 1.0)
+    ay = np.where(ok, ay, 1.0)
+    wi_std = warp_to_hemisphere(wi, ax, ay)
+    h, _ = sample_cap(_as_f64(u1), _as_f64(u2), wi_std)
+    v = _stack(ax * h[0], ay * h[1], h[2])
+    vv = dot(v, v)
+    p = vv * np.sqrt(vv) / (PI * ax * ay * (1.0 + wi_std[2]) * dot(h, h))
+    return np.where(ok, p, 0.0)
 
 
 def sample_vndf_with_pdf(u1, u2, wi, ax, ay, method="cap"):

@@ -50,7 +50,7 @@ SIGNATURES = {
     "vndf_fit_workspace_bytes": (_SZ, [_I32]),
     "vndf_fit_step": (ctypes.c_int, [_I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _F, _F, _F, _F,
                                      _F, _F, _U64, _U64, _U32, _P, _P, _SZ, _P]),
-    "vndf_microbench": (ctypes.c_int, [_I64, _I32, ctypes.c_int, _U64, _P, _P]),
+    "vndf_microbench": (ctypes.c_int, [_I64, _I32, ctypes.c_int, ctypes.c_int, _U64, _P, _P]),
     "vndf_albedo_batched_noalloc": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, _P, _I32, _F, _U64, _U64, _U32, _P,
                                                    _P, _P]),
 }
@@ -330,12 +330,14 @@ def fit_state(alpha_x, alpha_y):
             "step": torch.zeros(1, dtype=torch.int64, device=alpha_x.device)}
 
 
-def vndf_microbench(lanes, samples_per_lane=64, method="cap", seed=1, sums=None, device=None, stream=None):
+def vndf_microbench(lanes, samples_per_lane=64, method="cap", seed=1, sums=None, precise=True, device=None,
+                    stream=None):
     """The paper's 64-samples-per-lane protocol; returns the (lanes, 4) sums tensor."""
     device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     if sums is None:
         sums = torch.empty(lanes, 4, dtype=torch.float32, device=device)
-    st = load().vndf_microbench(int(lanes), int(samples_per_lane), _method(method), int(seed) & (2**64 - 1),
+    st = load().vndf_microbench(int(lanes), int(samples_per_lane), _method(method), int(bool(precise)),
+                                int(seed) & (2**64 - 1),
                                 _ptr(sums, "sums"), _stream(stream, sums.device))
     _check("vndf_microbench", st)
     return sums

@@ -22,7 +22,7 @@ namespace vndf {
 
 constexpr int kMicroBlock = 256;
 
-template <int METHOD>
+template <int METHOD, bool PRECISE>
 __global__ void __launch_bounds__(kMicroBlock) microbench_kernel(int64_t lanes, int32_t spl, Rng r, float4* out) {
   const int64_t stride = int64_t(gridDim.x) * kMicroBlock;
   for (int64_t l = int64_t(blockIdx.x) * kMicroBlock + threadIdx.x; l < lanes; l += stride) {
@@ -40,18 +40,34 @@ __global__ void __launch_bounds__(kMicroBlock) microbench_kernel(int64_t lanes, 
     for (int32_t j = 0; j < spl; j += 2) {
       float a1, a2, b1, b2;
       uniforms2(r, j0 + uint64_t(j), a1, a2, b1, b2);
-      float mx, my, mz, p;
-      sample_one<METHOD, true>(wx, wy, wz, ax, ay, a1, a2, mx, my, mz, p);
+      float mx, my, mz, p, nx, ny, nz, q;
+      const bool ra = sample_one<METHOD, true, PRECISE>(wx, wy, wz, ax, ay, a1, a2, mx, my, mz, p);
+      const bool rb = sample_one<METHOD, true, PRECISE>(wx, wy, wz, ax, ay, b1, b2, nx, ny, nz, q);
+      if constexpr (METHOD == kMethodCap && PRECISE) {
+        if (ra) {
+          const float4 r = sample_one_precise<true>(wx, wy, wz, ax, ay, a1, a2);
+          mx = r.x;
+          my = r.y;
+          mz = r.z;
+          p = r.w;
+        }
+        if (rb) {
+          const float4 r = sample_one_precise<true>(wx, wy, wz, ax, ay, b1, b2);
+          nx = r.x;
+          ny = r.y;
+          nz = r.z;
+          q = r.w;
+        }
+      }
       acc.x += mx;
       acc.y += my;
       acc.z += mz;
       acc.w += p;
       if (j + 1 < spl) {
-        sample_one<METHOD, true>(wx, wy, wz, ax, ay, b1, b2, mx, my, mz, p);
-        acc.x += mx;
-        acc.y += my;
-        acc.z += mz;
-        acc.w += p;
+        acc.x += nx;
+        acc.y += ny;
+        acc.z += nz;
+        acc.w += q;
       }
     }
     out[l] = acc;
@@ -62,8 +78,8 @@ __global__ void __launch_bounds__(kMicroBlock) microbench_kernel(int64_t lanes, 
 
 using namespace vndf;
 
-extern "C" int vndf_microbench(int64_t lanes, int32_t samples_per_lane, int method, uint64_t seed, float* sums,
-                               void* cuda_stream) {
+extern "C" int vndf_microbench(int64_t lanes, int32_t samples_per_lane, int method, int precise, uint64_t seed,
+                               float* sums, void* cuda_stream) {
   if (lanes < 0 || lanes >= (int64_t(1) << 40) || samples_per_lane < 1 || samples_per_lane > (1 << 20))
     return VNDF_ERR_SIZE;
   if (method != VNDF_METHOD_SPHERICAL_CAP && method != VNDF_METHOD_POLAR_DISK) return VNDF_ERR_METHOD;
@@ -74,9 +90,11 @@ extern "C" int vndf_microbench(int64_t lanes, int32_t samples_per_lane, int meth
   const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const unsigned grid = grid_for(lanes, kMicroBlock, 8, 16);
   float4* out = reinterpret_cast<float4*>(sums);
-  if (method == VNDF_METHOD_SPHERICAL_CAP)
-    microbench_kernel<kMethodCap><<<grid, kMicroBlock, 0, s>>>(lanes, samples_per_lane, r, out);
+  if (method == VNDF_METHOD_SPHERICAL_CAP && precise)
+    microbench_kernel<kMethodCap, true><<<grid, kMicroBlock, 0, s>>>(lanes, samples_per_lane, r, out);
+  else if (method == VNDF_METHOD_SPHERICAL_CAP)
+    microbench_kernel<kMethodCap, false><<<grid, kMicroBlock, 0, s>>>(lanes, samples_per_lane, r, out);
   else
-    microbench_kernel<kMethodPolar><<<grid, kMicroBlock, 0, s>>>(lanes, samples_per_lane, r, out);
+    microbench_kernel<kMethodPolar, false><<<grid, kMicroBlock, 0, s>>>(lanes, samples_per_lane, r, out);
   return launch_status();
 }

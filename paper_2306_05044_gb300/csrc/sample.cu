@@ -10,9 +10,28 @@
 #include "philox.cuh"
 #include "vndf_math.cuh"
 
+// Launch shape of the streaming sampler (compile-time, so the shape can be
+// tuned per build without a runtime switch).
+#ifndef VNDF_SAMPLE_BLOCK
+#define VNDF_SAMPLE_BLOCK 256
+#endif
+#ifndef VNDF_SAMPLE_MIN_BLOCKS
+#define VNDF_SAMPLE_MIN_BLOCKS 3
+#endif
+#ifndef VNDF_SAMPLE_WAVES
+#define VNDF_SAMPLE_WAVES 32
+#endif
+#ifndef VNDF_SAMPLE_PREFETCH
+#define VNDF_SAMPLE_PREFETCH 1
+#endif
+#ifndef VNDF_SAMPLE_STAGES
+#define VNDF_SAMPLE_STAGES 2
+#endif
+
 namespace vndf {
 
 constexpr int kBlock = 256;
+constexpr int kSampleBlock = VNDF_SAMPLE_BLOCK;
 
 struct SampleArgs {
   const float *wx, *wy, *wz, *ax, *ay, *u1, *u2;
@@ -20,36 +39,169 @@ struct SampleArgs {
   Rng rng;
 };
 
+// Inputs of one 4-sample group (128-bit loads of every stream).
+struct Group4 {
+  float4 x, y, z, ax, ay, u1, u2;
+};
+
+template <bool PHILOX, bool ISO>
+__device__ __forceinline__ void load_group(const SampleArgs& a, int64_t e, Group4& g) {
+  g.x = ld_stream(a.wx + e);
+  g.y = ld_stream(a.wy + e);
+  g.z = ld_stream(a.wz + e);
+  g.ax = ld_stream(a.ax + e);
+  if constexpr (!ISO) g.ay = ld_stream(a.ay + e);
+  if constexpr (!PHILOX) {
+    g.u1 = ld_stream(a.u1 + e);
+    g.u2 = ld_stream(a.u2 + e);
+  }
+}
+
+// Grid-stride loop over 4-sample groups.  The loads of the thread's next group
+// are issued before the current group is computed (software pipelining), so a
+// warp keeps one group of loads in flight while its arithmetic runs.
 template <int METHOD, bool PHILOX, bool ISO, bool PDF>
-__global__ void __launch_bounds__(kBlock) sample_vec4_kernel(SampleArgs a, int64_t n4) {
-  const int64_t stride = int64_t(gridDim.x) * kBlock;
-  for (int64_t q = int64_t(blockIdx.x) * kBlock + threadIdx.x; q < n4; q += stride) {
+__global__ void __launch_bounds__(kSampleBlock, VNDF_SAMPLE_MIN_BLOCKS) sample_vec4_kernel(SampleArgs a, int64_t n4) {
+  const int64_t stride = int64_t(gridDim.x) * kSampleBlock;
+  int64_t q = int64_t(blockIdx.x) * kSampleBlock + threadIdx.x;
+  Group4 next;
+  if (q < n4) load_group<PHILOX, ISO>(a, 4 * q, next);
+  for (; q < n4; q += stride) {
+    const Group4 cur = next;
+    if (VNDF_SAMPLE_PREFETCH && q + stride < n4) load_group<PHILOX, ISO>(a, 4 * (q + stride), next);
     const int64_t e = 4 * q;
     float X[4], Y[4], Z[4], AX[4], AY[4], U1[4], U2[4];
-    *reinterpret_cast<float4*>(X) = ld_stream(a.wx + e);
-    *reinterpret_cast<float4*>(Y) = ld_stream(a.wy + e);
-    *reinterpret_cast<float4*>(Z) = ld_stream(a.wz + e);
-    *reinterpret_cast<float4*>(AX) = ld_stream(a.ax + e);
-    if constexpr (ISO) {
-      *reinterpret_cast<float4*>(AY) = *reinterpret_cast<float4*>(AX);
-    } else {
-      *reinterpret_cast<float4*>(AY) = ld_stream(a.ay + e);
-    }
+    *reinterpret_cast<float4*>(X) = cur.x;
+    *reinterpret_cast<float4*>(Y) = cur.y;
+    *reinterpret_cast<float4*>(Z) = cur.z;
+    *reinterpret_cast<float4*>(AX) = cur.ax;
+    *reinterpret_cast<float4*>(AY) = ISO ? cur.ax : cur.ay;
     if constexpr (PHILOX) {
       uniforms4(a.rng, uint64_t(e), U1, U2);
     } else {
-      *reinterpret_cast<float4*>(U1) = ld_stream(a.u1 + e);
-      *reinterpret_cast<float4*>(U2) = ld_stream(a.u2 + e);
+      *reinterpret_cast<float4*>(U1) = cur.u1;
+      *reinterpret_cast<float4*>(U2) = cur.u2;
     }
     float MX[4], MY[4], MZ[4], P[4];
+    unsigned rescue = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      sample_one<METHOD, PDF>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], MX[k], MY[k], MZ[k], P[k]);
+      rescue |= unsigned(sample_one<METHOD, PDF, true>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], MX[k], MY[k],
+                                                       MZ[k], P[k]))
+                << k;
+    if constexpr (METHOD == kMethodCap) {
+      if (rescue) {  // rare: ill-conditioned samples redone in double-float
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (rescue & (1u << k)) {
+            const float4 r = sample_one_precise<PDF>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k]);
+            MX[k] = r.x;
+            MY[k] = r.y;
+            MZ[k] = r.z;
+            P[k] = r.w;
+          }
+      }
+    }
+    st_stream(a.mx + e, *reinterpret_cast<float4*>(MX));
+    st_stream(a.my + e, *reinterpret_cast<float4*>(MY));
+    st_stream(a.mz + e, *reinterpret_cast<float4*>(MZ));
+    if constexpr (PDF) st_stream(a.pdf + e, *reinterpret_cast<float4*>(P));
+    if (!VNDF_SAMPLE_PREFETCH && q + stride < n4) load_group<PHILOX, ISO>(a, 4 * (q + stride), next);
+  }
+}
+
+// ---- shared-memory pipeline: each thread stages its own next groups with
+// cp.async (16-byte asynchronous global->shared copies, L2 only), so loads stay
+// in flight without occupying registers.  A thread only ever reads the bytes it
+// copied itself, so the only synchronisation is the per-thread
+// cp.async.wait_group; there is no barrier and no spin.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <bool PHILOX, bool ISO>
+__host__ __device__ constexpr int streams_in() { return 4 + (ISO ? 0 : 1) + (PHILOX ? 0 : 2); }
+
+template <bool PHILOX, bool ISO>
+__device__ __forceinline__ void stage_group(const SampleArgs& a, int64_t e, float4* slot) {
+  // slot[k * kSampleBlock] is stream k of this thread's group
+  cp_async16(slot + 0 * kSampleBlock, a.wx + e);
+  cp_async16(slot + 1 * kSampleBlock, a.wy + e);
+  cp_async16(slot + 2 * kSampleBlock, a.wz + e);
+  cp_async16(slot + 3 * kSampleBlock, a.ax + e);
+  int k = 4;
+  if constexpr (!ISO) cp_async16(slot + (k++) * kSampleBlock, a.ay + e);
+  if constexpr (!PHILOX) {
+    cp_async16(slot + (k++) * kSampleBlock, a.u1 + e);
+    cp_async16(slot + (k++) * kSampleBlock, a.u2 + e);
+  }
+}
+
+template <int METHOD, bool PHILOX, bool ISO, bool PDF>
+__global__ void __launch_bounds__(kSampleBlock, VNDF_SAMPLE_MIN_BLOCKS) sample_pipe_kernel(SampleArgs a, int64_t n4) {
+  constexpr int S = VNDF_SAMPLE_STAGES;
+  constexpr int NS = streams_in<PHILOX, ISO>();
+  extern __shared__ float4 smem[];  // [S][NS][kSampleBlock]
+  const int64_t stride = int64_t(gridDim.x) * kSampleBlock;
+  const int64_t q0 = int64_t(blockIdx.x) * kSampleBlock + threadIdx.x;
+  float4* mine = smem + threadIdx.x;
+#pragma unroll
+  for (int st = 0; st < S - 1; ++st) {
+    const int64_t q = q0 + st * stride;
+    if (q < n4) stage_group<PHILOX, ISO>(a, 4 * q, mine + st * NS * kSampleBlock);
+    cp_async_commit();  // one group per stage, possibly empty, keeps the count uniform
+  }
+  int slot = 0;
+  for (int64_t q = q0; q < n4; q += stride) {
+    const int64_t qn = q + (S - 1) * stride;
+    if (qn < n4) stage_group<PHILOX, ISO>(a, 4 * qn, mine + ((slot + S - 1) % S) * NS * kSampleBlock);
+    cp_async_commit();
+    cp_async_wait<S - 1>();  // this thread's copies for q have landed
+    const float4* cur = mine + slot * NS * kSampleBlock;
+    const int64_t e = 4 * q;
+    float X[4], Y[4], Z[4], AX[4], AY[4], U1[4], U2[4];
+    *reinterpret_cast<float4*>(X) = cur[0 * kSampleBlock];
+    *reinterpret_cast<float4*>(Y) = cur[1 * kSampleBlock];
+    *reinterpret_cast<float4*>(Z) = cur[2 * kSampleBlock];
+    *reinterpret_cast<float4*>(AX) = cur[3 * kSampleBlock];
+    *reinterpret_cast<float4*>(AY) = ISO ? cur[3 * kSampleBlock] : cur[4 * kSampleBlock];
+    if constexpr (PHILOX) {
+      uniforms4(a.rng, uint64_t(e), U1, U2);
+    } else {
+      *reinterpret_cast<float4*>(U1) = cur[(ISO ? 4 : 5) * kSampleBlock];
+      *reinterpret_cast<float4*>(U2) = cur[(ISO ? 5 : 6) * kSampleBlock];
+    }
+    slot = (slot + 1) % S;
+    float MX[4], MY[4], MZ[4], P[4];
+    unsigned rescue = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      rescue |= unsigned(sample_one<METHOD, PDF, true>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], MX[k], MY[k],
+                                                       MZ[k], P[k]))
+                << k;
+    if constexpr (METHOD == kMethodCap) {
+      if (rescue) {  // rare: ill-conditioned samples redone in double-float
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (rescue & (1u << k)) {
+            const float4 r = sample_one_precise<PDF>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k]);
+            MX[k] = r.x;
+            MY[k] = r.y;
+            MZ[k] = r.z;
+            P[k] = r.w;
+          }
+      }
+    }
     st_stream(a.mx + e, *reinterpret_cast<float4*>(MX));
     st_stream(a.my + e, *reinterpret_cast<float4*>(MY));
     st_stream(a.mz + e, *reinterpret_cast<float4*>(MZ));
     if constexpr (PDF) st_stream(a.pdf + e, *reinterpret_cast<float4*>(P));
   }
+  cp_async_wait<0>();
 }
 
 template <int METHOD, bool PHILOX, bool ISO, bool PDF>
@@ -66,7 +218,14 @@ __global__ void __launch_bounds__(kBlock) sample_scalar_kernel(SampleArgs a, int
       u2 = a.u2[e];
     }
     float mx, my, mz, p;
-    sample_one<METHOD, PDF>(a.wx[e], a.wy[e], a.wz[e], ax, ay, u1, u2, mx, my, mz, p);
+    const float wx = a.wx[e], wy = a.wy[e], wz = a.wz[e];
+    if (sample_one<METHOD, PDF, true>(wx, wy, wz, ax, ay, u1, u2, mx, my, mz, p)) {
+      const float4 r = sample_one_precise<PDF>(wx, wy, wz, ax, ay, u1, u2);
+      mx = r.x;
+      my = r.y;
+      mz = r.z;
+      p = r.w;
+    }
     a.mx[e] = mx;
     a.my[e] = my;
     a.mz[e] = mz;
@@ -80,7 +239,20 @@ int launch_sample(const SampleArgs& a, int64_t n, bool vec, cudaStream_t s) {
   if (vec) {
     const int64_t n4 = n / 4;
     if (n4 > 0) {
-      sample_vec4_kernel<METHOD, PHILOX, ISO, PDF><<<grid_for(n4, kBlock, 8, 32), kBlock, 0, s>>>(a, n4);
+      const unsigned grid = grid_for(n4, kSampleBlock, 2048 / kSampleBlock, VNDF_SAMPLE_WAVES);
+      if constexpr (VNDF_SAMPLE_STAGES >= 2) {
+        constexpr size_t smem = size_t(VNDF_SAMPLE_STAGES) * streams_in<PHILOX, ISO>() * kSampleBlock * 16;
+        static bool attr_set = false;  // per instantiation; setting it twice is harmless
+        if (!attr_set) {
+          if (cudaFuncSetAttribute(sample_pipe_kernel<METHOD, PHILOX, ISO, PDF>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+            return VNDF_ERR_CUDA;
+          attr_set = true;
+        }
+        sample_pipe_kernel<METHOD, PHILOX, ISO, PDF><<<grid, kSampleBlock, smem, s>>>(a, n4);
+      } else {
+        sample_vec4_kernel<METHOD, PHILOX, ISO, PDF><<<grid, kSampleBlock, 0, s>>>(a, n4);
+      }
       done = 4 * n4;
     }
   }

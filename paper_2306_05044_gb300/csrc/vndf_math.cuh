@@ -30,6 +30,8 @@
 #pragma once
 #include <cstdint>
 
+#include "precise.cuh"
+
 namespace vndf {
 
 constexpr float kPi = 3.14159265358979323846f;
@@ -153,21 +155,16 @@ __device__ __forceinline__ void polar_disk_normal(const Stretched& i, float u1, 
   hz = fmaf(t2, w2z, ti * i.z);
 }
 
-// One sample of Sec. 2 steps (1)-(3) with the chosen hemisphere sampler and,
-// if PDF, the fused density.  Out-of-domain inputs give wm = (0,0,1), pdf = 0.
+// Threshold on the condition number above which a cap sample is recomputed in
+// double-float (cap_half_vector_precise): with it every sample meets 4e-6 rad
+// for wm and 1e-5 relative for the pdf; about 4e-4 of the anisotropic
+// workload's samples take that path.
+constexpr float kRescueKappa = 32.f;
+
+// The FP32 tail of a sample: unstretch h, normalise, and (if PDF) the fused density.
 template <int METHOD, bool PDF>
-__device__ __forceinline__ void sample_one(float wx, float wy, float wz, float ax, float ay,
-                                           float u1, float u2,
-                                           float& mx, float& my, float& mz, float& pdf) {
-  const bool ok = in_domain(wx, wy, wz, ax, ay);
-  const Stretched i = stretch(wx, wy, wz, ax, ay);
-  float hx, hy, hz, a;
-  if constexpr (METHOD == kMethodCap) {
-    cap_half_vector(i, u1, u2, hx, hy, hz, a);
-  } else {
-    polar_disk_normal(i, u1, u2, hx, hy, hz);
-    a = 1.f + i.z;
-  }
+__device__ __forceinline__ void finish_sample(const Stretched& i, float ax, float ay, float hx, float hy, float hz,
+                                              float a, float& mx, float& my, float& mz, float& pdf) {
   const float vx = ax * hx, vy = ay * hy, vz = hz;
   const float vv = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
   const float rv = rsqrtf(vv);
@@ -184,12 +181,61 @@ __device__ __forceinline__ void sample_one(float wx, float wy, float wz, float a
       pdf = __fdividef(2.f * hi * v3, kPi * ax * ay * a);
     }
   }
+}
+
+// One sample of Sec. 2 steps (1)-(3) with the chosen hemisphere sampler and,
+// if PDF, the fused density.  Out-of-domain inputs give wm = (0,0,1), pdf = 0.
+// With PRECISE (cap sampler only) the return value flags an ill-conditioned
+// sample whose result must be replaced by sample_one_precise; the check costs a
+// few FP32 operations and keeps the rare slow path out of the unrolled loop.
+template <int METHOD, bool PDF, bool PRECISE = false>
+__device__ __forceinline__ bool sample_one(float wx, float wy, float wz, float ax, float ay,
+                                           float u1, float u2,
+                                           float& mx, float& my, float& mz, float& pdf) {
+  const bool ok = in_domain(wx, wy, wz, ax, ay);
+  const Stretched i = stretch(wx, wy, wz, ax, ay);
+  float hx, hy, hz, a;
+  if constexpr (METHOD == kMethodCap) {
+    cap_half_vector(i, u1, u2, hx, hy, hz, a);
+  } else {
+    polar_disk_normal(i, u1, u2, hx, hy, hz);
+    a = 1.f + i.z;
+  }
+  finish_sample<METHOD, PDF>(i, ax, ay, hx, hy, hz, a, mx, my, mz, pdf);
+  bool bad = false;
+  if constexpr (PRECISE && METHOD == kMethodCap) {
+    // |c.x| + |i.x| etc. bound the rounding of h; compare it with |v| and |h|
+    const float sx = fabsf(hx - i.x) + fabsf(i.x), sy = fabsf(hy - i.y) + fabsf(i.y);
+    const float vx = ax * hx, vy = ay * hy;
+    const float vv = fmaf(vx, vx, fmaf(vy, vy, hz * hz));
+    const float k2 = fmaf(ax * sx, ax * sx, fmaf(ay * sy, ay * sy, hz * hz));
+    bad = k2 > kRescueKappa * kRescueKappa * vv;
+    if constexpr (PDF) {
+      const float kh2 = fmaf(sx, sx, fmaf(sy, sy, hz * hz));
+      bad |= kh2 > kRescueKappa * kRescueKappa * fmaf(hx, hx, fmaf(hy, hy, hz * hz));
+    }
+    bad &= ok;
+  }
   if (!ok) {
     mx = 0.f;
     my = 0.f;
     mz = 1.f;
     if constexpr (PDF) pdf = 0.f;
   }
+  return bad;
+}
+
+// The cap sample recomputed with its half vector in double-float (in-domain
+// inputs only); returns (wm.x, wm.y, wm.z, pdf).  Not inlined, and returning by
+// value, so that the rare path neither bloats nor spills the FP32 path.
+template <bool PDF>
+__device__ __noinline__ float4 sample_one_precise(float wx, float wy, float wz, float ax, float ay, float u1,
+                                                  float u2) {
+  float hx, hy, hz, a;
+  cap_half_vector_precise(wx, wy, wz, ax, ay, u1, u2, hx, hy, hz, a);
+  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  finish_sample<kMethodCap, PDF>(Stretched{0.f, 0.f, 0.f}, ax, ay, hx, hy, hz, a, r.x, r.y, r.z, r.w);
+  return r;
 }
 
 // Density of a given normal (Eq. 1 through the App. A forms of D and G1):

@@ -12,7 +12,17 @@ sample must satisfy
     angle <= max(4e-6, K * kappa * 2^-24),
     rel   <= max(1e-5, K * (3 kappa + 2 kappa_h) * 2^-24),      K = 8,
 and the fraction of samples above the flat 4e-6 / 1e-5 limits (the
-ill-conditioned tail) is reported and bounded separately.
+ill-conditioned tail) is reported.
+
+The library's cap sampler recomputes the half vector of ill-conditioned
+samples in double-float, so for its outputs (strict=True) the flat limits
+themselves are asserted on every sample with wi.z >= 1e-4 and alpha >= 1e-3.
+
+The oracle's pdf G1 max(0, wi.wm) D(wm) / wz is evaluated at the FP64 normal,
+and wi.wm cancels near the visibility boundary: there its own error estimate
+2^-52 kappa (sum |wi_k wm_k|) / |wi.wm| can exceed 1e-7.  For those samples the
+strict pdf check uses the oracle's hemisphere-sample form of Eq. 1
+(vndf_pdf_at_cap_sample), which does not cancel; the count is reported.
 """
 import numpy as np
 
@@ -41,7 +51,7 @@ def conditioning(u1, u2, wi, ax, ay):
     return kap, kap_h
 
 
-def compare_cap(wm_gpu, pdf_gpu, u1, u2, wi, ax, ay):
+def compare_cap(wm_gpu, pdf_gpu, u1, u2, wi, ax, ay, strict=True):
     """Check GPU cap samples against the oracle; returns a stats dict (asserts the bounds)."""
     wi = np.asarray(wi, np.float64)
     ax = np.asarray(ax, np.float64)
@@ -68,17 +78,33 @@ def compare_cap(wm_gpu, pdf_gpu, u1, u2, wi, ax, ay):
         f"angle {ang[worst]:.3e} > bound {bound[worst]:.3e} (kappa {kap[worst]:.3g}) at {worst}")
     norm_err = np.abs(np.sqrt(vndf.dot(wm_gpu, wm_gpu)) - 1.0)
     assert norm_err.max() <= 2.0 ** -21
+    contract = (wi[2] / np.sqrt(vndf.dot(wi, wi)) >= 1e-4) & (ax >= 1e-3) & (ay >= 1e-3)
+    if strict and contract.any():
+        worst = np.argmax(np.where(contract, ang, 0))
+        assert ang[contract].max() <= ANGLE_TOL, (
+            f"angle {ang[worst]:.3e} rad > {ANGLE_TOL} at {worst} (kappa {kap[worst]:.3g})")
     stats.update(max_angle=float(ang.max(initial=0)), p9999_angle=float(np.quantile(ang, 0.9999)) if ang.size else 0.0,
                  tail_angle_frac=float((ang > ANGLE_TOL).mean()) if ang.size else 0.0,
                  max_kappa_ratio=float((ang / (kap * EPS32)).max(initial=0)))
     if pdf_gpu is not None:
         pg = np.asarray(pdf_gpu, np.float64)[ok]
         pr = pdf_ref[ok]
+        # where the definition-based oracle pdf is itself ill-conditioned, use the sample form
+        dwm = np.abs(vndf.dot(wi, wm_ref)) / np.sqrt(vndf.dot(wi, wi))
+        swm = (np.abs(wi * wm_ref).sum(axis=0)) / np.sqrt(vndf.dot(wi, wi))
+        oracle_err = 2.0 ** -52 * kap * swm / np.maximum(dwm, 1e-300)
+        weak = oracle_err > 1e-7
+        if weak.any():
+            pr = np.where(weak, vndf.vndf_pdf_at_cap_sample(u1, u2, wi, ax, ay), pr)
+        stats["oracle_pdf_form_switched"] = int(weak.sum())
         rel = np.abs(pg / pr - 1.0)
         pbound = np.maximum(PDF_TOL, K_ULP * (3.0 * kap + 2.0 * kap_h) * EPS32)
         worst = np.argmax(rel / pbound) if rel.size else 0
         assert np.all(rel <= pbound), (
             f"pdf rel {rel[worst]:.3e} > bound {pbound[worst]:.3e} at {worst}")
+        if strict and contract.any():
+            worst = np.argmax(np.where(contract, rel, 0))
+            assert rel[contract].max() <= PDF_TOL, f"pdf rel {rel[worst]:.3e} > {PDF_TOL} at {worst}"
         stats.update(max_pdf_rel=float(rel.max(initial=0)),
                      tail_pdf_frac=float((rel > PDF_TOL).mean()) if rel.size else 0.0)
     return stats

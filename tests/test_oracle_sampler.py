@@ -97,3 +97,15 @@ def test_prior_sampler_invariants_and_pole_case():
     pole = np.tile(np.array([[0.0], [0.0], [1.0]]), (1, n))
     wp = vndf.sample_vndf(u1, u2, pole, one, one, "polar")
     assert np.abs(wp[2] ** 2 - (1 - u2)).max() < 1e-13
+
+
+def test_pdf_at_cap_sample_equals_definition():
+    """The hemisphere-sample form of Eq. 1 agrees with G1 max(0, wi.wm) D / wz where the latter is
+    well conditioned (away from the visibility boundary)."""
+    u1, u2, wi, ax, ay = oc.random_batch(20000, 16, alpha_lo=1e-3)
+    wm = vndf.sample_vndf(u1, u2, wi, ax, ay)
+    p_def = vndf.vndf_pdf(wm, wi, ax, ay)
+    p_cap = vndf.vndf_pdf_at_cap_sample(u1, u2, wi, ax, ay)
+    good = vndf.dot(wm, wi) / np.sqrt(vndf.dot(wi, wi)) > 1e-3
+    assert good.mean() > 0.99
+    assert np.abs(p_cap[good] / p_def[good] - 1).max() < 1e-10
