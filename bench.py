@@ -58,13 +58,14 @@ def parse_args():
     p.add_argument("--no-albedo", action="store_true")
     p.add_argument("--no-fit", action="store_true")
     p.add_argument("--no-microbench", action="store_true")
+    p.add_argument("--no-reflection", action="store_true")
     p.add_argument("--log2n-adjoint", type=int, default=24)
     return p.parse_args()
 
 
 # ----------------------------------------------------------------------------- helpers
 KERNEL_FILES = {
-    "stream": ("sample.cu", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
+    "stream": ("sample.cu", "staging.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
     "microbench_cap": ("microbench.cu", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
     "microbench_cap_strict": ("microbench.cu", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
     "microbench_polar": ("microbench.cu", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
@@ -314,6 +315,7 @@ def run_ours(args, rank, world):
     base, n = sharding.sample_shard(rank, world, 1 << args.log2n)
     d = workloads.anisotropic_stream(n=n, device=dev)
     outs = [torch.empty(n, device=dev) for _ in range(4)]
+    refl_w = None if args.no_reflection else torch.empty(n, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step(method="cap"):
@@ -379,6 +381,16 @@ def run_ours(args, rank, world):
         result["gpu_launches_prior"] = steps
 
     clk = (clock or {}).get("sm_mhz") or (clock or {}).get("sm_max_mhz") or 2070.0
+    if not args.no_reflection:
+        rt, _, _ = timed(lambda: vndf.vndf_sample_reflection(
+            d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], seed=2, counter_base=base, wo_x=outs[0],
+            wo_y=outs[1], wo_z=outs[2], pdf=outs[3], weight=refl_w), steps, warm)
+        rv = world * n * steps / (rt * 1e-3) / 1e9
+        result["reflection"] = {"value": rv, "unit": UNIT, "ms_per_step": rt / steps,
+                                "roofline_frac": 40 * n / (rt / steps * 1e-3) / 1e9 / peak,
+                                "bytes_per_sample": 40, "note": "wo, pdf and F G2/G1 weight per sample (App. A)"}
+        result["gpu_launches_reflection"] = steps
+
     if not args.no_fwd_bwd:
         result["fwd_bwd"] = fwd_bwd(vndf, dev, rank, world, timed, peak, args.log2n_adjoint)
         result["fwd_bwd"]["issue"] = issue_roofline("loss_backward", 1 << args.log2n_adjoint,

@@ -116,6 +116,35 @@ int vndf_sample(int64_t n,
                 void *cuda_stream);
 
 /*
+ * vndf_sample_reflection -- sample a reflected direction from the GGX
+ * microfacet BRDF through the spherical-cap VNDF sampler (App. A, "Importance
+ * Sampling Using the GGX VNDF"): wm is drawn exactly as vndf_sample draws it
+ * (Sec. 2, Sec. 3.3), wi is reflected about it, wo = 2 (wi.wm) wm - wi
+ * (Eq. reflect), and the outputs are
+ *   pdf    = G1(wm, wi) D(wm) / (4 cos theta_i), the density of wo (App. A),
+ *   weight = f_r(wo, wi) |cos theta_o| / pdf = F(wi.wm) G2 / G1(wi), the
+ *            Monte Carlo weight of Eq. rendering_mc for unit radiance, with the
+ *            height-correlated G2 of App. A and Schlick's Fresnel
+ *            F0 + (1 - F0)(1 - wi.wm)^5; 0 when wo is below the surface.
+ * wi.wm and the pdf are evaluated from the sampler's hemisphere vectors, so
+ * they stay accurate next to the visibility boundary.
+ *   n, wi_*, alpha_*, u1, u2, seed, counter_base, stream_id   as in vndf_sample.
+ *   f0                 Schlick reflectance at normal incidence.
+ *   wo_x, wo_y, wo_z   output reflected direction (unit).
+ *   pdf, weight        outputs (each may be NULL to skip).
+ * Out-of-domain samples give wo = (0, 0, 1), pdf = 0, weight = 0.
+ * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, ALIGN, ARG, CUDA).
+ */
+int vndf_sample_reflection(int64_t n,
+                           const float *wi_x, const float *wi_y, const float *wi_z,
+                           const float *alpha_x, const float *alpha_y,
+                           const float *u1, const float *u2,
+                           uint64_t seed, uint64_t counter_base, uint32_t stream_id,
+                           float f0,
+                           float *wo_x, float *wo_y, float *wo_z, float *pdf, float *weight,
+                           void *cuda_stream);
+
+/*
  * vndf_pdf -- GGX VNDF density of given normals (Eq. 1, written through the
  * App. A forms of D and G1):
  *   pdf = 2 max(0, wi.wm) / (pi alpha_x alpha_y (|M^-1 wi| + wi.z) Q^2),

@@ -9,6 +9,7 @@ Paper sections followed:
 * ``reflect``         Eq. reflect (Sec. 3.2) and App. A step (2)
 * ``bsdf_pdf``        App. A: PDF(wb, wa) = G1(wm, wa) D(wm) / (4 cos_a)
 * ``estimator_weight`` App. A, Eq. rendering_mc with L = 1: f_r |cos_b| / PDF
+* ``sample_reflection`` App. A steps (1)-(2): reflected direction, its PDF and weight
 * ``albedo_estimate``  the Monte Carlo estimator over Philox streams
 * ``albedo_quadrature`` the same integral by a midpoint rule over (u1, u2)
 
@@ -69,6 +70,27 @@ def estimator_weight(wm, wa, ax, ay, f0):
     f = brdf(wa, wb_safe, ax, ay, f0)
     w = f * np.abs(wb_safe[2]) / bsdf_pdf(wm, wa, ax, ay)
     return np.where(below, 0.0, w)
+
+
+def sample_reflection(u1, u2, wa, ax, ay, f0):
+    """App. A steps (1)-(2) per sample: (wb (3, N), PDF(wb) (N,), weight (N,)).
+
+    wm is drawn with the cap sampler, wb = reflect(wm, wa) (Eq. reflect), PDF is the
+    BSDF sampling density of App. A and weight the term of Eq. rendering_mc with L = 1.
+    Out-of-domain samples give wb = (0, 0, 1), PDF = 0, weight = 0.
+    """
+    from .vndf import in_domain
+    wa = np.asarray(wa, dtype=np.float64)
+    ax = np.asarray(ax, dtype=np.float64)
+    ay = np.asarray(ay, dtype=np.float64)
+    ok = in_domain(wa, ax, ay)
+    wa_u = wa / np.sqrt(dot(wa, wa))
+    wm = sample_vndf(u1, u2, wa, ax, ay, "cap")
+    wb = reflect(wm, wa_u)
+    pdf = bsdf_pdf(wm, wa_u, ax, ay)
+    w = estimator_weight(wm, wa_u, ax, ay, f0)
+    fallback = np.array([0.0, 0.0, 1.0]).reshape(3, *([1] * (wb.ndim - 1)))
+    return np.where(ok, wb, fallback), np.where(ok, pdf, 0.0), np.where(ok, w, 0.0)
 
 
 def albedo_samples(wi, ax, ay, n, f0, seed, counter_base, stream_id):

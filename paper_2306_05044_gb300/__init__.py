@@ -37,6 +37,8 @@ SIGNATURES = {
     "vndf_sample": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _U64, _U64, _U32, ctypes.c_int,
                                    _P, _P, _P, _P, _P]),
     "vndf_pdf": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "vndf_sample_reflection": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _U64, _U64, _U32, _F,
+                                              _P, _P, _P, _P, _P, _P]),
     "vndf_sample_backward": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _U64, _U64, _U32,
                                             _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "vndf_loss_workspace_bytes": (_SZ, [_I64]),
@@ -182,6 +184,26 @@ def vndf_sample(wi_x, wi_y, wi_z, alpha_x, alpha_y=None, u1=None, u2=None, seed=
         _stream(stream, wi_x.device))
     _check("vndf_sample", st)
     return wm_x, wm_y, wm_z, pdf
+
+
+def vndf_sample_reflection(wi_x, wi_y, wi_z, alpha_x, alpha_y=None, u1=None, u2=None, seed=0, counter_base=0,
+                           stream_id=0, f0=0.04, wo_x=None, wo_y=None, wo_z=None, pdf=None, weight=None,
+                           with_pdf=True, with_weight=True, n=None, stream=None):
+    """Reflected direction, its pdf and the BRDF weight per sample; see vndf_sample_reflection in include/vndf.h.
+
+    Returns (wo_x, wo_y, wo_z, pdf or None, weight or None)."""
+    n = wi_x.numel() if n is None else int(n)
+    wo_x, wo_y, wo_z = (_out(t, n, wi_x) for t in (wo_x, wo_y, wo_z))
+    pdf = _out(pdf, n, wi_x) if with_pdf else None
+    weight = _out(weight, n, wi_x) if with_weight else None
+    st = load().vndf_sample_reflection(
+        n, _ptr(wi_x, "wi_x"), _ptr(wi_y, "wi_y"), _ptr(wi_z, "wi_z"), _ptr(alpha_x, "alpha_x"),
+        _ptr(alpha_y, "alpha_y"), _ptr(u1, "u1"), _ptr(u2, "u2"), int(seed) & (2**64 - 1),
+        int(counter_base) & (2**64 - 1), int(stream_id) & 0xFFFFFFFF, float(f0), _ptr(wo_x, "wo_x"),
+        _ptr(wo_y, "wo_y"), _ptr(wo_z, "wo_z"), _ptr(pdf, "pdf"), _ptr(weight, "weight"),
+        _stream(stream, wi_x.device))
+    _check("vndf_sample_reflection", st)
+    return wo_x, wo_y, wo_z, pdf, weight
 
 
 def vndf_pdf(wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf=None, n=None, stream=None):

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "staging.cuh"
 #include "philox.cuh"
 #include "vndf_math.cuh"
 
@@ -109,22 +110,6 @@ __global__ void __launch_bounds__(kSampleBlock, VNDF_SAMPLE_MIN_BLOCKS) sample_v
     if (!VNDF_SAMPLE_PREFETCH && q + stride < n4) load_group<PHILOX, ISO>(a, 4 * (q + stride), next);
   }
 }
-
-// ---- shared-memory pipeline: each thread stages its own next groups with
-// cp.async (16-byte asynchronous global->shared copies, L2 only), so loads stay
-// in flight without occupying registers.  A thread only ever reads the bytes it
-// copied itself, so the only synchronisation is the per-thread
-// cp.async.wait_group; there is no barrier and no spin.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-template <bool PHILOX, bool ISO>
-__host__ __device__ constexpr int streams_in() { return 4 + (ISO ? 0 : 1) + (PHILOX ? 0 : 2); }
 
 template <bool PHILOX, bool ISO>
 __device__ __forceinline__ void stage_group(const SampleArgs& a, int64_t e, float4* slot) {

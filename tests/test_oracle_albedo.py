@@ -56,3 +56,18 @@ def test_reflection_recovers_half_vector():
 
 def test_reflected_direction_density():
     assert oc.reflected_change_of_variables_error() < 1e-8
+
+
+def test_sample_reflection_composition():
+    """The per-sample reflection oracle is the composition of the pinned App. A pieces: its weights
+    average to the albedo quadrature, and its pdf integrates the reflected directions correctly."""
+    rng = np.random.default_rng(11)
+    n = 1 << 16
+    u1, u2 = rng.random(n), rng.random(n)
+    wi = oc.direction(40.0, 30.0)
+    wa = np.tile(wi.reshape(3, 1), (1, n))
+    wb, pdf, w = microfacet.sample_reflection(u1, u2, wa, np.full(n, 0.3), np.full(n, 0.3), 0.04)
+    assert np.abs(np.sqrt((wb * wb).sum(0)) - 1).max() < 1e-13
+    e_q = microfacet.albedo_quadrature(wi, 0.3, 0.3, 0.04, m=512)
+    assert abs(w.mean() - e_q) < 4 * w.std() / np.sqrt(n)
+    assert np.all(pdf > 0)
