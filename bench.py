@@ -59,6 +59,7 @@ def parse_args():
     p.add_argument("--no-fit", action="store_true")
     p.add_argument("--no-microbench", action="store_true")
     p.add_argument("--no-reflection", action="store_true")
+    p.add_argument("--no-cpu-protocol", action="store_true")
     p.add_argument("--log2n-adjoint", type=int, default=24)
     return p.parse_args()
 
@@ -421,6 +422,9 @@ def run_ours(args, rank, world):
         best = max((x for x in (piped, direct) if x is not None), key=lambda x: x["value"])
         result["e2e"] = dict(best, alternatives={"copy_pipeline": piped, "zero_copy": direct})
 
+    if rank == 0 and not args.no_cpu_protocol:
+        result["cpu_protocol"] = cpu_protocol(vndf)
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -499,6 +503,44 @@ def microbench(vndf, dev, world, timed):
     out["cap_strict_over_prior"] = out["cap_strict"]["value"] / out["polar"]["value"]
     out["paper_reference"] = "paper: cap faster by 52.96 % (Arc A770) and 39.25 % (RTX 2080), DX12 compute"
     return out
+
+
+def cpu_protocol(vndf, n=1 << 20, runs=100):
+    """The paper's CPU protocol (Sec. 4): the sampler in a loop, median time of 100 invocations.
+
+    Runs the library's host entry point (vndf_cpu_sample) over the first n samples of
+    the anisotropic workload, normals only (as the paper's benchmark), on one thread
+    and on all host threads, for both samplers."""
+    import numpy as np
+    import torch
+
+    import workloads
+    d = {k: t.numpy() for k, t in workloads.anisotropic_stream(n=n).items()}
+    g = torch.Generator().manual_seed(7)
+    u1, u2 = (t.numpy() for t in torch.rand(2, n, generator=g).unbind(0))
+    outs = [np.empty(n, np.float32) for _ in range(3)]
+    cores = os.cpu_count() or 1
+    res = {"protocol": f"median of {runs} invocations over {n} samples, wm only, inputs in host memory",
+           "samples": n}
+    for threads in (1, cores):
+        row = {}
+        for method in ("cap", "polar"):
+            def call():
+                vndf.vndf_cpu_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], u1, u2,
+                                     method=method, with_pdf=False, threads=threads, out=outs)
+            for _ in range(3):
+                call()
+            ts = []
+            for _ in range(runs):
+                t0 = time.perf_counter()
+                call()
+                ts.append(time.perf_counter() - t0)
+            med = statistics.median(ts)
+            row[method] = {"ms_median": 1e3 * med, "value": n / med / 1e9, "unit": UNIT}
+        row["cap_over_prior"] = row["polar"]["ms_median"] / row["cap"]["ms_median"]
+        res[f"threads_{threads}"] = row
+    res["paper_reference"] = "paper: cap faster by 37.67 % on an i7-13700K (C++ loop)"
+    return res
 
 
 def fit_leg(vndf, dev, rank, world, timed):

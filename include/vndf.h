@@ -363,6 +363,24 @@ int vndf_fit_step(int32_t n_texels, int32_t samples_per_texel,
 int vndf_microbench(int64_t lanes, int32_t samples_per_lane, int method, int precise, uint64_t seed,
                     float *sums, void *cuda_stream);
 
+/*
+ * vndf_cpu_sample -- the GGX VNDF sampler on the host CPU, for the paper's CPU
+ * benchmark (Sec. 4, "CPU Synthetic Benchmark", which calls the sampler in a
+ * loop).  An explicit host entry point, not a fallback of vndf_sample: all
+ * pointers are HOST memory, uniforms are explicit, and the arithmetic is FP32
+ * with the same rounding-aware formulas as the GPU kernels (both methods),
+ * vectorised by the compiler and split over `threads` host threads (0 = all
+ * hardware threads).  Results do not depend on the thread count.  It has no
+ * double-float path, so, like the prior sampler, about 1e-5 of samples lie
+ * beyond 4e-6 rad of an FP64 evaluation.
+ * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, METHOD).
+ */
+int vndf_cpu_sample(int64_t n,
+                    const float *wi_x, const float *wi_y, const float *wi_z,
+                    const float *alpha_x, const float *alpha_y,
+                    const float *u1, const float *u2, int method,
+                    float *wm_x, float *wm_y, float *wm_z, float *pdf, int threads);
+
 /* Size of the fixed device scratch array behind vndf_albedo_batched_noalloc:
  * 8 MiB.  A batch fits when vndf_albedo_workspace_bytes(n_queries,
  * max_samples_per_query) is at most this; 4096 queries of up to 65536 samples

@@ -53,6 +53,7 @@ SIGNATURES = {
     "vndf_fit_step": (ctypes.c_int, [_I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _F, _F, _F, _F,
                                      _F, _F, _U64, _U64, _U32, _P, _P, _SZ, _P]),
     "vndf_microbench": (ctypes.c_int, [_I64, _I32, ctypes.c_int, ctypes.c_int, _U64, _P, _P]),
+    "vndf_cpu_sample": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int, _P, _P, _P, _P, ctypes.c_int]),
     "vndf_albedo_batched_noalloc": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, _P, _I32, _F, _U64, _U64, _U32, _P,
                                                    _P, _P]),
 }
@@ -363,3 +364,28 @@ def vndf_microbench(lanes, samples_per_lane=64, method="cap", seed=1, sums=None,
                                 _ptr(sums, "sums"), _stream(stream, sums.device))
     _check("vndf_microbench", st)
     return sums
+
+
+def vndf_cpu_sample(wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, method="cap", with_pdf=True, threads=0,
+                    out=None):
+    """Host-CPU sampler on numpy float32 arrays; see vndf_cpu_sample in include/vndf.h.
+
+    ``out`` optionally gives preallocated contiguous float32 outputs (wm_x, wm_y, wm_z, pdf).
+    Returns (wm_x, wm_y, wm_z, pdf or None) as numpy arrays."""
+    import numpy as np
+    arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (wi_x, wi_y, wi_z, alpha_x)]
+    ay = None if alpha_y is None else np.ascontiguousarray(alpha_y, dtype=np.float32)
+    us = [np.ascontiguousarray(a, dtype=np.float32) for a in (u1, u2)]
+    n = arrs[0].size
+    if out is None:
+        out = [np.empty(n, dtype=np.float32) for _ in range(4 if with_pdf else 3)]
+    else:
+        out = list(out)[:4 if with_pdf else 3]
+        for o in out:
+            if o.dtype != np.float32 or not o.flags.c_contiguous or o.size != n:
+                raise ValueError("vndf_cpu_sample: outputs must be contiguous float32 arrays of the input size")
+    p = lambda a: None if a is None else a.ctypes.data  # noqa: E731
+    st = load().vndf_cpu_sample(n, *(p(a) for a in arrs), p(ay), p(us[0]), p(us[1]), _method(method),
+                                p(out[0]), p(out[1]), p(out[2]), p(out[3]) if with_pdf else None, int(threads))
+    _check("vndf_cpu_sample", st)
+    return out[0], out[1], out[2], (out[3] if with_pdf else None)

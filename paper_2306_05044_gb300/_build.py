@@ -1,7 +1,8 @@
 """Build libvndf.so in-tree with nvcc for sm_103a (no torch extension machinery).
 
-Each ``csrc/*.cu`` file is compiled in parallel into ``_build/*.o`` and the
-objects are linked into ``libvndf.so`` beside this file.  A rebuild happens
+Each ``csrc/*.cu`` file is compiled in parallel with nvcc, and each
+``csrc/*.cpp`` file (host-only code) with the host C++ compiler, into
+``_build/*.o``; the objects are linked into ``libvndf.so`` beside this file.  A rebuild happens
 only when a source or header is newer than the library.
 """
 import concurrent.futures
@@ -22,6 +23,16 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompil
               "--expt-relaxed-constexpr", "-Xptxas", "-O3"]
 
 
+HOST_FLAGS = ["-O3", "-std=c++17", "-fPIC", "-fopenmp-simd", "-fno-math-errno", "-pthread"]
+
+
+def _cxx():
+    for cand in (os.environ.get("CXX"), shutil.which("g++"), shutil.which("c++")):
+        if cand and shutil.which(cand):
+            return cand
+    raise RuntimeError("no host C++ compiler (g++) found")
+
+
 def _nvcc():
     for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
         if cand and os.path.exists(cand):
@@ -30,7 +41,7 @@ def _nvcc():
 
 
 def _sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
 
 def _deps():
@@ -54,8 +65,12 @@ def build(force=False, verbose=False, extra_flags=()):
     srcs = _sources()
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra_flags, "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
+        stem, ext = os.path.splitext(os.path.basename(src))
+        obj = os.path.join(BUILD_DIR, stem + ("_host" if ext == ".cpp" else "") + ".o")
+        if ext == ".cpp":
+            cmd = [_cxx(), *HOST_FLAGS, "-I", INCLUDE, "-c", src, "-o", obj]
+        else:
+            cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra_flags, "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stdout}\n{r.stderr}")
@@ -66,7 +81,7 @@ def build(force=False, verbose=False, extra_flags=()):
     with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB_PATH + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-pthread", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -1,0 +1,166 @@
+// Host (CPU) implementation of both hemisphere samplers wrapped in the GGX
+// VNDF routine, for the paper's CPU benchmark (Sec. 4, "CPU Synthetic
+// Benchmark": the sampler called in a loop, median time over 100 runs).
+// It is an explicit entry point for host callers, never a fallback of the GPU
+// entry points.  Plain portable C++17: FP32 arithmetic written branch-free so
+// that the compiler can vectorise the loop (omp simd), the same rounding-aware
+// formulas as the CUDA kernels (cancellation-free sin^2 for the cap sampler,
+// the rewritten disk lift for the prior one, sin/cos(pi x) from its Taylor
+// series), and std::thread for the split across cores.
+#include <cmath>
+#include <cstdint>
+#include <thread>
+#include <vector>
+
+#include "vndf.h"
+
+namespace {
+
+constexpr float kPiF = 3.14159265358979323846f;
+
+__attribute__((always_inline)) inline void sincospi_taylor_host(float x, float& s, float& c) {
+  // sin/cos(pi r) on r = x - j/2 in [-1/4, 1/4] (exact reduction), Taylor terms to r^9 / r^10;
+  // x = 2 u1 is in [0, 2), so j = int(2x + 1/2) is the nearest integer (a conversion, which
+  // vectorises on every baseline ISA, unlike rint)
+  const int ji = static_cast<int>(2.f * x + 0.5f);
+  const float j = static_cast<float>(ji);
+  const float r = std::fma(-0.5f, j, x);
+  const float r2 = r * r;
+  float ps = std::fma(r2, 0.0821458866111282288f, -0.599264529320792077f);
+  ps = std::fma(r2, ps, 2.55016403987734549f);
+  ps = std::fma(r2, ps, -5.16771278004997003f);
+  ps = std::fma(r2, ps, 3.14159265358979323846f);
+  ps *= r;
+  float pc = std::fma(r2, -0.0258068913900140009f, 0.235330630358893200f);
+  pc = std::fma(r2, pc, -1.33526276885458949f);
+  pc = std::fma(r2, pc, 4.05871212641676822f);
+  pc = std::fma(r2, pc, -4.93480220054467931f);
+  pc = std::fma(r2, pc, 1.f);
+  const int k = ji & 3;
+  const float a = (k & 1) ? pc : ps;
+  const float b = (k & 1) ? ps : pc;
+  s = (k & 2) ? -a : a;
+  c = ((k + 1) & 2) ? -b : b;
+}
+
+template <int METHOD>
+__attribute__((always_inline)) inline void sample_host(float wx, float wy, float wz, float ax, float ay, float u1, float u2, float& mx, float& my,
+                        float& mz, float& pdf) {
+  const bool ok = (wz > 0.f) & (ax > 0.f) & (ay > 0.f) & std::isfinite(wx) & std::isfinite(wy) &
+                  std::isfinite(wz) & std::isfinite(ax) & std::isfinite(ay);
+  // keep the arithmetic finite on out-of-domain lanes (their results are replaced below)
+  wz = ok ? wz : 1.f;
+  ax = ok ? ax : 1.f;
+  ay = ok ? ay : 1.f;
+  wx = ok ? wx : 0.f;
+  wy = ok ? wy : 0.f;
+  // Sec. 2 step (1): i = M^-1 wi / |M^-1 wi|
+  const float sx = ax * wx, sy = ay * wy;
+  const float l2 = std::fma(sx, sx, std::fma(sy, sy, wz * wz));
+  const float rl = 1.f / std::sqrt(l2);
+  const float ix = sx * rl, iy = sy * rl, iz = wz * rl;
+  const float a = 1.f + iz;
+  float sp, cp;
+  sincospi_taylor_host(2.f * u1, sp, cp);
+  float hx, hy, hz;
+  if constexpr (METHOD == VNDF_METHOD_SPHERICAL_CAP) {
+    // Sec. 3.3: c on the cap z in (-i.z, 1], h = c + i
+    const float rho2 = std::fma(ix, ix, iy * iy);
+    const float st = std::sqrt(u2 * std::fma(2.f * a, 1.f - u2, u2 * rho2));
+    hx = std::fma(st, cp, ix);
+    hy = std::fma(st, sp, iy);
+    hz = (1.f - u2) * a;
+  } else {
+    // Heitz 2018 cross-section sampler (Sec. 2 step (2))
+    const float tmp = std::fma(ix, ix, iy * iy);
+    const bool pole = !(tmp > 0.f);
+    const float rt = 1.f / std::sqrt(pole ? 1.f : tmp);
+    const float w1x = pole ? 1.f : -iy * rt, w1y = pole ? 0.f : ix * rt;
+    const float w2x = -iz * w1y, w2y = iz * w1x, w2z = std::fma(ix, w1y, -iy * w1x);
+    const float r = std::sqrt(u2);
+    const float t1 = r * cp, t2o = r * sp;
+    const float om = 1.f - u2;
+    const float q = std::sqrt(std::fma(u2 * sp, sp, om));
+    const float s = 0.5f * a, oms = 0.5f * tmp / a;
+    const bool pos = t2o >= 0.f;
+    const float big = pos ? q + t2o : q - t2o;
+    const float small = om / big;
+    const float qm = pos ? small : big, qp = pos ? big : small;
+    const float t2 = std::fma(oms, q, s * t2o);
+    const float ti = std::sqrt(s * qm * std::fma(2.f * oms, q, s * qp));
+    hx = std::fma(t1, w1x, std::fma(t2, w2x, ti * ix));
+    hy = std::fma(t1, w1y, std::fma(t2, w2y, ti * iy));
+    hz = std::fma(t2, w2z, ti * iz);
+  }
+  // Sec. 2 step (3) and the fused density of Eq. 1
+  const float vx = ax * hx, vy = ay * hy, vz = hz;
+  const float vv = std::fma(vx, vx, std::fma(vy, vy, vz * vz));
+  const float nv = std::sqrt(vv);
+  const float rv = 1.f / nv;
+  mx = ok ? vx * rv : 0.f;
+  my = ok ? vy * rv : 0.f;
+  mz = ok ? vz * rv : 1.f;
+  float p;
+  if constexpr (METHOD == VNDF_METHOD_SPHERICAL_CAP) {
+    const float hh = std::fma(hx, hx, std::fma(hy, hy, hz * hz));
+    p = vv * nv / (kPiF * ax * ay * a * hh);
+  } else {
+    const float hi = std::fmax(std::fma(hx, ix, std::fma(hy, iy, hz * iz)), 0.f);
+    p = 2.f * hi * vv * nv / (kPiF * ax * ay * a);
+  }
+  pdf = ok ? p : 0.f;
+}
+
+struct HostArgs {
+  const float *wx, *wy, *wz, *ax, *ay, *u1, *u2;
+  float *mx, *my, *mz, *pdf;
+};
+
+template <int METHOD, bool PDF>
+void run_range(const HostArgs& h, int64_t i0, int64_t i1) {
+  const float* ay = h.ay ? h.ay : h.ax;
+#pragma omp simd
+  for (int64_t i = i0; i < i1; ++i) {
+    float mx, my, mz, p;
+    sample_host<METHOD>(h.wx[i], h.wy[i], h.wz[i], h.ax[i], ay[i], h.u1[i], h.u2[i], mx, my, mz, p);
+    h.mx[i] = mx;
+    h.my[i] = my;
+    h.mz[i] = mz;
+    if constexpr (PDF) h.pdf[i] = p;
+  }
+}
+
+}  // namespace
+
+extern "C" int vndf_cpu_sample(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z,
+                               const float* alpha_x, const float* alpha_y, const float* u1, const float* u2,
+                               int method, float* wm_x, float* wm_y, float* wm_z, float* pdf, int threads) {
+  if (n < 0 || n >= (int64_t(1) << 62)) return VNDF_ERR_SIZE;
+  if (method != VNDF_METHOD_SPHERICAL_CAP && method != VNDF_METHOD_POLAR_DISK) return VNDF_ERR_METHOD;
+  if (n == 0) return VNDF_OK;
+  if (!wi_x || !wi_y || !wi_z || !alpha_x || !u1 || !u2 || !wm_x || !wm_y || !wm_z) return VNDF_ERR_NULL;
+  const HostArgs h{wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, wm_x, wm_y, wm_z, pdf};
+  auto body = [&](int64_t i0, int64_t i1) {
+    if (method == VNDF_METHOD_SPHERICAL_CAP)
+      pdf ? run_range<VNDF_METHOD_SPHERICAL_CAP, true>(h, i0, i1) : run_range<VNDF_METHOD_SPHERICAL_CAP, false>(h, i0, i1);
+    else
+      pdf ? run_range<VNDF_METHOD_POLAR_DISK, true>(h, i0, i1) : run_range<VNDF_METHOD_POLAR_DISK, false>(h, i0, i1);
+  };
+  int t = threads > 0 ? threads : static_cast<int>(std::thread::hardware_concurrency());
+  if (t < 1) t = 1;
+  if (int64_t(t) > n / 4096) t = static_cast<int>(n / 4096 > 0 ? n / 4096 : 1);
+  if (t == 1) {
+    body(0, n);
+    return VNDF_OK;
+  }
+  std::vector<std::thread> pool;
+  pool.reserve(t);
+  const int64_t chunk = ((n + t - 1) / t + 15) / 16 * 16;
+  for (int k = 0; k < t; ++k) {
+    const int64_t i0 = int64_t(k) * chunk, i1 = i0 + chunk < n ? i0 + chunk : n;
+    if (i0 >= i1) break;
+    pool.emplace_back(body, i0, i1);
+  }
+  for (auto& th : pool) th.join();
+  return VNDF_OK;
+}

@@ -1,0 +1,78 @@
+"""The host-CPU sampler (vndf_cpu_sample) against the FP64 oracle; runs without a GPU.
+
+It carries no double-float path, so it is held to the condition-scaled bound
+of tests/parity.py (non-strict), like the GPU kernels were before their rescue;
+the prior sampler is checked in bulk.
+"""
+import numpy as np
+import pytest
+
+import parity
+import workloads
+from oracle import philox, vndf as ovndf
+
+
+@pytest.fixture(scope="module")
+def v():
+    from paper_2306_05044_gb300 import _build
+    _build.build()
+    import paper_2306_05044_gb300 as lib
+    lib.load()
+    return lib
+
+
+def _inputs(n, seed=12):
+    d = workloads.anisotropic_stream(n=n, seed=seed)
+    return {k: t.numpy() for k, t in d.items()}
+
+
+def test_cpu_cap_matches_oracle(v):
+    n = (1 << 18) + 3
+    d = _inputs(n)
+    u1, u2 = philox.sample_uniforms(2, 0, 0, n)
+    wx, wy, wz, pdf = v.vndf_cpu_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], u1, u2)
+    wi = np.stack([d["wi_x"], d["wi_y"], d["wi_z"]])
+    st = parity.compare_cap(np.stack([wx, wy, wz]), pdf, u1, u2, wi, d["alpha_x"], d["alpha_y"], strict=False)
+    print("cpu cap", st)
+    assert st["tail_angle_frac"] < 1e-4
+
+
+def test_cpu_prior_matches_oracle(v):
+    n = 1 << 16
+    d = _inputs(n, seed=13)
+    u1, u2 = philox.sample_uniforms(3, 0, 0, n)
+    wx, wy, wz, pdf = v.vndf_cpu_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], u1, u2,
+                                        method="polar")
+    wi = np.stack([d["wi_x"], d["wi_y"], d["wi_z"]]).astype(np.float64)
+    ref = ovndf.sample_vndf(u1, u2, wi, d["alpha_x"], d["alpha_y"], "polar")
+    pr = ovndf.vndf_pdf(ref, wi, d["alpha_x"], d["alpha_y"])
+    ang = parity.angle_between(np.stack([wx, wy, wz]).astype(np.float64), ref)
+    rel = np.abs(pdf / pr - 1)
+    assert np.median(ang) < 1e-7 and (ang > 4e-6).mean() < 1e-3
+    assert np.median(rel) < 1e-6 and (rel > 1e-5).mean() < 1e-3
+
+
+def test_cpu_results_independent_of_threads_and_isotropy(v):
+    n = 50001
+    d = _inputs(n, seed=14)
+    u1, u2 = philox.sample_uniforms(4, 0, 0, n)
+    one = v.vndf_cpu_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], u1, u2, threads=1)
+    many = v.vndf_cpu_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], u1, u2, threads=7)
+    for a, b in zip(one, many):
+        np.testing.assert_array_equal(a, b)
+    iso = v.vndf_cpu_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], None, u1, u2, threads=3)
+    same = v.vndf_cpu_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_x"], u1, u2, threads=3)
+    for a, b in zip(iso, same):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_cpu_domain_fallback_and_errors(v):
+    x = np.array([0.3, 0.3, np.nan], np.float32)
+    z = np.array([-0.1, 0.9, 0.9], np.float32)
+    a = np.array([0.5, 0.0, 0.5], np.float32)
+    u = np.full(3, 0.4, np.float32)
+    wx, wy, wz, pdf = v.vndf_cpu_sample(x, x, z, a, a, u, u)
+    np.testing.assert_array_equal(wz, np.ones(3, np.float32))
+    np.testing.assert_array_equal(pdf, np.zeros(3, np.float32))
+    with pytest.raises(v.VndfError):
+        v.vndf_cpu_sample(x, x, z, a, a, u, u, method=5)
