@@ -73,6 +73,7 @@ KERNEL_FILES = {
     "loss_backward": ("backward.cu", "vndf_adjoint.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
     "albedo": ("albedo.cu", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
     "fit": ("fit.cu", "vndf_adjoint.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
+    "reflection": ("reflect.cu", "staging.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
 }
 
 
@@ -366,7 +367,7 @@ def run_ours(args, rank, world):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": f"{peak_kind} copy bandwidth",
                      "traffic": (tps * n) if tps is not None else None,
-                     "algorithmic_bytes": BYTES_PER_SAMPLE * n, "kernel": "sample_vec4_kernel<cap, philox, aniso, pdf>"},
+                     "algorithmic_bytes": BYTES_PER_SAMPLE * n, "kernel": "sample_pipe_kernel<cap, philox, aniso, pdf>"},
         "gpu_launches": steps,
         "clocks": clock,
         "per_step_ms": {"min": min(per), "median": statistics.median(per), "max": max(per)},
@@ -389,7 +390,8 @@ def run_ours(args, rank, world):
         rv = world * n * steps / (rt * 1e-3) / 1e9
         result["reflection"] = {"value": rv, "unit": UNIT, "ms_per_step": rt / steps,
                                 "roofline_frac": 40 * n / (rt / steps * 1e-3) / 1e9 / peak,
-                                "bytes_per_sample": 40, "note": "wo, pdf and F G2/G1 weight per sample (App. A)"}
+                                "bytes_per_sample": 40, "note": "wo, pdf and F G2/G1 weight per sample (App. A)",
+                                "issue": issue_roofline("reflection", n, rt / steps, clk)}
         result["gpu_launches_reflection"] = steps
 
     if not args.no_fwd_bwd:
