@@ -58,12 +58,12 @@ def jacobian_central_difference(u1, u2, wi, ax, ay, rel_step=1e-6, method="cap")
     return np.stack(out)
 
 
-def u_jacobian_complex_step(u1, u2, wi, ax, ay):
+def u_jacobian_complex_step(u1, u2, wi, ax, ay, extended=False):
     """d wm / d u1 and d wm / d u2 (each (3, N)) for the cap sampler."""
     u1 = np.asarray(u1, np.float64)
     u2 = np.asarray(u2, np.float64)
-    d1 = np.imag(sample_vndf(u1 + 1j * H_CS, u2.astype(np.complex128), wi, ax, ay, "cap")) / H_CS
-    d2 = np.imag(sample_vndf(u1.astype(np.complex128), u2 + 1j * H_CS, wi, ax, ay, "cap")) / H_CS
+    d1 = np.imag(sample_vndf(u1 + 1j * H_CS, u2.astype(np.complex128), wi, ax, ay, "cap", extended)) / H_CS
+    d2 = np.imag(sample_vndf(u1.astype(np.complex128), u2 + 1j * H_CS, wi, ax, ay, "cap", extended)) / H_CS
     return d1, d2
 
 

@@ -23,10 +23,19 @@ follow:
 * ``vndf_pdf_eq1``         Eq. 1 written out literally (transformed hemisphere VNDF)
 * ``vndf_pdf_at_cap_sample`` Eq. 1 at the cap sampler's own hemisphere sample (Sec. 3.2-3.3),
                            the form that stays accurate near the visibility boundary
+* ``projected_area``       Eq. 4 carried through M (App. A): sigma(wi) = |M^-1 wi| sigma_std(z_i')
+* ``sample_hemisphere``    Sec. 3.3 used stand-alone: the cap sample normalised, with its Eq. 2 density
 
 Readings where the paper is silent (each is listed in the design notes):
 * Domain: wi.z > 0, alpha_x > 0, alpha_y > 0, all inputs finite.  Outside it a
   sample returns the defined fallback wm = (0, 0, 1) with pdf = 0.
+* Extended domain (``extended=True``): the construction of Sec. 3.2-3.3 never
+  uses wi.z > 0.  The cap z in (-z_i', 1] and sigma_std = (1 + z_i')/2 (Eq. 4)
+  stay valid for every z_i' > -1, i.e. for incident directions below the
+  horizon, and sample the normals with wm.z > 0 that face wi.  The paper is
+  silent on it; the extended domain requires 1 + z_i' >= MIN_CAP_A (the
+  stretched direction at least about 1.4e-6 rad from straight down), finite
+  inputs and positive roughness.
 * wi need not be unit length: every step normalises or is scale free.
 * u1 drives the azimuth and u2 the cap height, as in both printed samplers.
 
@@ -39,6 +48,10 @@ derivative is the derivative of the interior expression.
 import numpy as np
 
 PI = np.pi
+
+# Smallest 1 + z_i' of the extended domain (a reading: below it the cap has
+# shrunk to a point and FP32 results would be meaningless).
+MIN_CAP_A = 2.0 ** -40
 
 
 # ----------------------------------------------------------------------------
@@ -153,33 +166,49 @@ def sample_polar_disk(u1, u2, wi_std):
 # Sec. 2: the full GGX VNDF sampler
 # ----------------------------------------------------------------------------
 
-def in_domain(wi, ax, ay):
-    """Inputs on which the sampler is defined (a reading; see module docstring)."""
+def in_domain(wi, ax, ay, extended=False):
+    """Inputs on which the sampler is defined (a reading; see module docstring).
+
+    extended=False: wi.z > 0.  extended=True: 1 + z_i' >= MIN_CAP_A, where
+    z_i' is the height of the stretched direction M^-1 wi / |M^-1 wi|.
+    """
     wi = [np.real(_as_f64(w)) for w in wi]
     ax = np.real(_as_f64(ax))
     ay = np.real(_as_f64(ay))
-    ok = (wi[2] > 0) & (ax > 0) & (ay > 0)
+    ok = (ax > 0) & (ay > 0)
     for q in (wi[0], wi[1], wi[2], ax, ay):
         ok &= np.isfinite(q)
-    return ok
+    if not extended:
+        return ok & (wi[2] > 0)
+    with np.errstate(invalid="ignore", divide="ignore", over="ignore"):
+        sx, sy = ax * wi[0], ay * wi[1]
+        zi = wi[2] / np.sqrt(sx * sx + sy * sy + wi[2] * wi[2])
+        return ok & (1.0 + zi >= MIN_CAP_A)
 
 
-def sample_vndf(u1, u2, wi, ax, ay, method="cap"):
+def _fallback_inputs(ok, wi, ax, ay):
+    """Finite stand-in inputs on lanes outside the domain (their results are replaced)."""
+    wi = np.where(ok, wi, np.array([0.0, 0.0, 1.0]).reshape(3, *([1] * (wi.ndim - 1))))
+    return wi, np.where(ok, ax, 1.0), np.where(ok, ay, 1.0)
+
+
+def sample_vndf(u1, u2, wi, ax, ay, method="cap", extended=False):
     """Steps (1)-(3) of Sec. 2: wm for each (u1, u2, wi, ax, ay).
 
     method = "cap" uses the spherical-cap sampler (Sec. 3.3), "polar" the prior
-    sampler (Heitz 2018).  Out-of-domain samples return (0, 0, 1).
+    sampler (Heitz 2018).  extended=True (cap only) accepts the extended domain
+    (incident directions below the horizon).  Out-of-domain samples return (0, 0, 1).
     """
+    if extended and method != "cap":
+        raise ValueError("the extended domain is defined for the cap sampler only")
     wi = _stack(*[_as_f64(w) for w in wi])
     ax = _as_f64(ax)
     ay = _as_f64(ay)
     u1 = _as_f64(u1)
     u2 = _as_f64(u2)
-    ok = in_domain(wi, ax, ay)
+    ok = in_domain(wi, ax, ay, extended)
     # keep the arithmetic finite on fallback lanes
-    wi = np.where(ok, wi, np.array([0.0, 0.0, 1.0]).reshape(3, *([1] * (wi.ndim - 1))))
-    ax = np.where(ok, ax, 1.0)
-    ay = np.where(ok, ay, 1.0)
+    wi, ax, ay = _fallback_inputs(ok, wi, ax, ay)
     wi_std = warp_to_hemisphere(wi, ax, ay)
     if method == "cap":
         h, _ = sample_cap(u1, u2, wi_std)
@@ -237,22 +266,37 @@ def smith_g1(wm, wk, ax, ay):
     return chi * wk_std[2] / sigma_std(wk_std[2])
 
 
-def vndf_pdf(wm, wi, ax, ay):
+def projected_area(wi_unit, ax, ay):
+    """sigma(wi) = integral of max(0, wi.wm) D(wm) over wm, for unit wi.
+
+    Eq. 4 gives it for the hemisphere configuration; M maps projected areas by
+    |M^-1 wi| (App. A's derivation of G1 through the same transformation), so
+    sigma(wi) = |M^-1 wi| (1 + z_i') / 2 = (|M^-1 wi| + wi.z) / 2.
+    """
+    s = _stack(ax * wi_unit[0], ay * wi_unit[1], wi_unit[2])
+    return np.sqrt(dot(s, s)) * sigma_std(warp_to_hemisphere(wi_unit, ax, ay)[2])
+
+
+def vndf_pdf(wm, wi, ax, ay, extended=False):
     """GGX VNDF density of wm given wi: G1(wi) max(0, wi.wm) D(wm) / wi.z (wi normalised).
 
     This is Eq. 2's definition of a visible-normal density (Heitz & d'Eon 2014)
-    with the GGX D and G1 of App. A; it equals Eq. 1.  Out-of-domain inputs give 0.
+    with the GGX D and G1 of App. A; it equals Eq. 1.  On the extended domain
+    (wi.z may be <= 0, where G1 / wi.z is 0/0 at the horizon) it is written as
+    max(0, wi.wm) D(wm) / sigma(wi) with the projected area sigma, the same
+    quantity since G1(wi) / wi.z = 1 / sigma(wi).  Out-of-domain inputs give 0.
     """
     wm = _stack(*[_as_f64(w) for w in wm])
     wi = _stack(*[_as_f64(w) for w in wi])
     ax = _as_f64(ax)
     ay = _as_f64(ay)
-    ok = in_domain(wi, ax, ay)
-    wi = np.where(ok, wi, np.array([0.0, 0.0, 1.0]).reshape(3, *([1] * (wi.ndim - 1))))
-    ax = np.where(ok, ax, 1.0)
-    ay = np.where(ok, ay, 1.0)
+    ok = in_domain(wi, ax, ay, extended)
+    wi, ax, ay = _fallback_inputs(ok, wi, ax, ay)
     wi_unit = normalize(wi)
-    p = smith_g1(wm, wi_unit, ax, ay) * _pos(dot(wi_unit, wm)) * ndf(wm, ax, ay) / wi_unit[2]
+    if extended:
+        p = _pos(dot(wi_unit, wm)) * ndf(wm, ax, ay) / projected_area(wi_unit, ax, ay)
+    else:
+        p = smith_g1(wm, wi_unit, ax, ay) * _pos(dot(wi_unit, wm)) * ndf(wm, ax, ay) / wi_unit[2]
     return np.where(ok, p, 0.0)
 
 
@@ -267,7 +311,7 @@ def vndf_pdf_eq1(wm, wi, ax, ay):
     return vndf_std(wm_std, wi_std) * (1.0 / (ax * ay)) / n ** 3
 
 
-def vndf_pdf_at_cap_sample(u1, u2, wi, ax, ay):
+def vndf_pdf_at_cap_sample(u1, u2, wi, ax, ay, extended=False):
     """Eq. 1 evaluated at the cap sampler's own hemisphere sample (Sec. 3.3).
 
     For the sample wm = normalize(M^-T h) with h = c + wi' (wi' = M^-1 wi / |.|,
@@ -283,10 +327,8 @@ def vndf_pdf_at_cap_sample(u1, u2, wi, ax, ay):
     wi = _stack(*[_as_f64(w) for w in wi])
     ax = _as_f64(ax)
     ay = _as_f64(ay)
-    ok = in_domain(wi, ax, ay)
-    wi = np.where(ok, wi, np.array([0.0, 0.0, 1.0]).reshape(3, *([1] * (wi.ndim - 1))))
-    ax = np.where(ok, ax, 1.0)
-    ay = np.where(ok, ay, 1.0)
+    ok = in_domain(wi, ax, ay, extended)
+    wi, ax, ay = _fallback_inputs(ok, wi, ax, ay)
     wi_std = warp_to_hemisphere(wi, ax, ay)
     h, _ = sample_cap(_as_f64(u1), _as_f64(u2), wi_std)
     v = _stack(ax * h[0], ay * h[1], h[2])
@@ -295,7 +337,34 @@ def vndf_pdf_at_cap_sample(u1, u2, wi, ax, ay):
     return np.where(ok, p, 0.0)
 
 
-def sample_vndf_with_pdf(u1, u2, wi, ax, ay, method="cap"):
+def sample_vndf_with_pdf(u1, u2, wi, ax, ay, method="cap", extended=False):
     """(wm, pdf) per sample: the sampled normal and the VNDF density at it."""
-    wm = sample_vndf(u1, u2, wi, ax, ay, method)
-    return wm, vndf_pdf(wm, wi, ax, ay)
+    wm = sample_vndf(u1, u2, wi, ax, ay, method, extended)
+    return wm, vndf_pdf(wm, wi, ax, ay, extended)
+
+
+# ----------------------------------------------------------------------------
+# Sec. 3.3 used on its own: the hemisphere sampler with its normalisation
+# ----------------------------------------------------------------------------
+
+def sample_hemisphere(u1, u2, wi_std):
+    """Visible normal of the hemisphere configuration for direction wi_std, and its density.
+
+    Sec. 3.3 leaves the half vector h = c + wi_std unnormalised because the
+    GGX sampler normalises after unstretching; used on its own the sample is
+    h / |h| (the normalisation the paper says a stand-alone use needs).  The
+    density is Eq. 2, max(wm.wi, 0) D_std(wm) / sigma_std(z_i) with D_std and
+    sigma_std of Eqs. 3-4.  wi_std need not be unit length.  Its domain is the
+    extended one: finite, non-zero, 1 + z_i >= MIN_CAP_A.  Returns (wm (3, N),
+    pdf (N,)); out-of-domain lanes give ((0, 0, 1), 0).
+    """
+    w = _stack(*[_as_f64(x) for x in wi_std])
+    one = np.ones_like(np.real(w[0]))
+    ok = in_domain(w, one, one, extended=True)
+    w, _, _ = _fallback_inputs(ok, w, one, one)
+    w = normalize(w)
+    h, _ = sample_cap(_as_f64(u1), _as_f64(u2), w)
+    wm = normalize(h)
+    pdf = vndf_std(wm, w)
+    fallback = np.array([0.0, 0.0, 1.0]).reshape(3, *([1] * (wm.ndim - 1)))
+    return np.where(ok, wm, fallback), np.where(ok, pdf, 0.0)

@@ -337,3 +337,137 @@ def reflected_change_of_variables_error(n=2000, seed=14):
     d2 = np.imag(wb_of(u1.astype(np.complex128), u2 + 1j * grad.H_CS)) / grad.H_CS
     cr = np.cross(d1.T, d2.T).T
     return np.abs(pdf * np.sqrt(vndf.dot(cr, cr)) - 1.0).max()
+
+
+# ---------------------------------------------------------------- the extended domain (wi below the horizon)
+EXT_CASES = [
+    (100.0, 40.0, 0.5, 0.3),
+    (120.0, -60.0, 0.8, 0.6),
+    (95.0, 10.0, 0.2, 0.25),
+    (90.0, 30.0, 0.4, 0.7),
+    (150.0, 0.0, 1.0, 1.0),
+]
+
+
+def random_batch_extended(n, seed, alpha_lo=1e-2, cos_lo=-0.95):
+    """Directions with cos(theta_i) uniform in [cos_lo, 1] (most below the horizon when cos_lo ~ -1)."""
+    return random_batch(n, seed, alpha_lo=alpha_lo, cos_lo=cos_lo)
+
+
+def extended_mirror_cap_error(n=20000, seed=21):
+    """Sec. 3.2's mirror property below the horizon: reflecting wi' about h/|h| gives c back.
+
+    Rounding in h/|h| grows like eps/|h|, and below the horizon the whole cap can be small
+    (|h|^2 <= 2 (1 + z_i')), so the error is returned scaled by min(1, |h|)."""
+    u1, u2, wi, ax, ay = random_batch_extended(n, seed)
+    wi_std = vndf.warp_to_hemisphere(wi, ax, ay)
+    h, c = vndf.sample_cap(u1, u2, wi_std)
+    hl = np.sqrt(vndf.dot(h, h))
+    hn = h / hl
+    refl = 2.0 * vndf.dot(hn, wi_std) * hn - wi_std
+    return (np.abs(refl - c).max(axis=0) * np.minimum(hl, 1.0)).max()
+
+
+def extended_cap_uniformity_pvalues(n=200000, seed=22, zi=-0.6):
+    return cap_uniformity_pvalues(n=n, seed=seed, zi=zi)
+
+
+def extended_change_of_variables_error(n=5000, seed=23):
+    """pdf(wm(u)) |d wm/du1 x d wm/du2| = 1 pointwise for incident directions below the horizon."""
+    u1, u2, wi, ax, ay = random_batch_extended(n, seed, cos_lo=-0.9)
+    u2 = np.clip(u2, 1e-6, 1 - 1e-6)
+    wm = vndf.sample_vndf(u1, u2, wi, ax, ay, extended=True)
+    pdf = vndf.vndf_pdf(wm, wi, ax, ay, extended=True)
+    d1, d2 = grad.u_jacobian_complex_step(u1, u2, wi, ax, ay, extended=True)
+    cr = np.cross(d1.T, d2.T).T
+    return np.abs(pdf * np.sqrt(vndf.dot(cr, cr)) - 1.0).max()
+
+
+def extended_normalisation_errors(theta_deg, phi_deg, ax, ay):
+    """|int pdf - 1| and |int max(0, wi.wm) D - (|M^-1 wi| + wi.z)/2| by quadrature, any theta_i."""
+    wi = direction(theta_deg, phi_deg)
+    wm, w, _, _ = hemisphere_quadrature(ax, ay)
+    n = wm.shape[1]
+    wib = _bcast(wi, n)
+    axb = np.full(n, ax)
+    ayb = np.full(n, ay)
+    pdf = vndf.vndf_pdf(wm, wib, axb, ayb, extended=True)
+    proj = (np.maximum(vndf.dot(wm, wib), 0.0) * vndf.ndf(wm, axb, ayb) * w).sum()
+    closed = 0.5 * (math.sqrt((ax * wi[0]) ** 2 + (ay * wi[1]) ** 2 + wi[2] ** 2) + wi[2])
+    return abs((pdf * w).sum() - 1.0), abs(proj - closed) / closed
+
+
+def extended_alpha_one_errors(n=20000, seed=24):
+    """alpha = 1: wm = normalize(c + wi) and pdf = 2 max(0, wi.wm) / (pi (1 + wi.z)) for any wi.z > -1."""
+    u1, u2, wi, _, _ = random_batch_extended(n, seed)
+    one = np.ones(n)
+    wm = vndf.sample_vndf(u1, u2, wi, one, one, extended=True)
+    _, c = vndf.sample_cap(u1, u2, wi)
+    ref = (c + wi) / np.sqrt(vndf.dot(c + wi, c + wi))
+    pdf = vndf.vndf_pdf(wm, wi, one, one, extended=True)
+    closed = 2.0 * np.maximum(vndf.dot(wi, wm), 0.0) / (np.pi * (1.0 + wi[2]))
+    return np.abs(wm - ref).max(), np.abs(pdf / closed - 1.0).max()
+
+
+def horizon_continuity_error(n=5000, seed=25, eps=1e-9):
+    """The extended sampler is one construction across the horizon: wi.z = +eps and -eps give the
+    same normals and densities up to O(eps)."""
+    rng = np.random.default_rng(seed)
+    u1, u2 = rng.random(n), rng.random(n)
+    ph = rng.uniform(0, 2 * np.pi, n)
+    ax = np.exp(rng.uniform(np.log(0.05), 0.0, n))
+    ay = np.exp(rng.uniform(np.log(0.05), 0.0, n))
+    out = []
+    for z in (eps, -eps):
+        wi = np.stack([np.cos(ph), np.sin(ph), np.full(n, z)])
+        out.append(vndf.sample_vndf_with_pdf(u1, u2, wi, ax, ay, extended=True))
+    (wa, pa), (wb, pb) = out
+    return np.abs(wa - wb).max(), np.abs(pa / pb - 1.0).max()
+
+
+def extended_expected_bin_probabilities(wi, ax, ay):
+    wm, w, tau, phi = hemisphere_quadrature(ax, ay)
+    n = wm.shape[1]
+    pdf = vndf.vndf_pdf(wm, _bcast(wi, n), np.full(n, ax), np.full(n, ay), extended=True)
+    it = np.clip((tau / (0.5 * np.pi) * N_TAU_BINS).astype(int), 0, N_TAU_BINS - 1)
+    ip = np.clip((phi / (2 * np.pi) * N_PHI_BINS).astype(int), 0, N_PHI_BINS - 1)
+    return np.bincount(it * N_PHI_BINS + ip, weights=pdf * w, minlength=N_TAU_BINS * N_PHI_BINS)
+
+
+def _extended_case(theta_deg, phi_deg, ax, ay, n, seed):
+    rng = np.random.default_rng(seed)
+    u1, u2 = rng.random(n), rng.random(n)
+    return vndf.sample_vndf(u1, u2, _bcast(direction(theta_deg, phi_deg), n), np.full(n, ax), np.full(n, ay),
+                            extended=True)
+
+
+def extended_chi2_vs_pdf_pvalue(theta_deg, phi_deg, ax, ay, n=1_000_000, seed=26):
+    wm = _extended_case(theta_deg, phi_deg, ax, ay, n, seed)
+    obs = counts(wm, ax, ay)
+    exp = n * extended_expected_bin_probabilities(direction(theta_deg, phi_deg), ax, ay)
+    keep = exp >= 5
+    o = np.append(obs[keep], obs[~keep].sum())
+    e = np.append(exp[keep], exp[~keep].sum())
+    m = e > 0
+    chi2 = (((o - e) ** 2) / e)[m].sum()
+    return stats.chi2.sf(chi2, m.sum() - 1)
+
+
+def extended_brute_force_pvalue(theta_deg, phi_deg, ax, ay, n=1_000_000, seed=27):
+    """Ray casting from below the horizon: first hits on the ellipsoid with z >= 0 (Sec. 2's definition)."""
+    rng = np.random.default_rng(seed)
+    ref = brute.visible_normals(direction(theta_deg, phi_deg), ax, ay, n, rng)
+    wm = _extended_case(theta_deg, phi_deg, ax, ay, n, seed + 1)
+    return two_sample_chi2_pvalue(counts(wm, ax, ay), counts(ref, ax, ay))
+
+
+def hemisphere_sampler_errors(n=20000, seed=28):
+    """The stand-alone hemisphere sampler against the GGX sampler at alpha = 1 (where D = 1/pi, the
+    hemisphere configuration itself) and its density against Eq. 2 evaluated at the sample."""
+    u1, u2, wi, _, _ = random_batch_extended(n, seed)
+    scale = np.exp(np.random.default_rng(seed + 1).uniform(-3, 3, n))  # any length
+    wm, pdf = vndf.sample_hemisphere(u1, u2, wi * scale)
+    one = np.ones(n)
+    ref, ref_pdf = vndf.sample_vndf_with_pdf(u1, u2, wi, one, one, extended=True)
+    unit = np.abs(np.sqrt(vndf.dot(wm, wm)) - 1.0).max()
+    return np.abs(wm - ref).max(), np.abs(pdf / ref_pdf - 1.0).max(), unit

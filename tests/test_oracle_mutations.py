@@ -115,6 +115,18 @@ def _words_same_pair(seed, counter_base, stream_id, n):
     return out[0], out[1]
 
 
+def _projected_area_abs(wi_unit, ax, ay):
+    s = _stack(ax * wi_unit[0], ay * wi_unit[1], wi_unit[2])
+    return 0.5 * (np.sqrt(vndf.dot(s, s)) + np.abs(wi_unit[2]))
+
+
+def _cap_abs_height(u1, u2, wi_std):
+    # the cap height range built from |z_i|: identical above the horizon, wrong below it
+    w = _stack(wi_std[0], wi_std[1], np.abs(wi_std[2]))
+    h, c = _CAP(u1, u2, w)
+    return c + wi_std, c
+
+
 _CAP = vndf.sample_cap
 _EQ1 = vndf.vndf_pdf_eq1
 _BSDF = microfacet.bsdf_pdf
@@ -138,6 +150,8 @@ MUTANTS = {
     "g2_separable": [(microfacet, "smith_g2", _g2_separable)],
     "philox_operands_swapped": [(philox, "philox4x32_10", _philox_swapped)],
     "philox_pair_words": [(philox, "sample_words", _words_same_pair)],
+    "projected_area_abs_wz": [(vndf, "projected_area", _projected_area_abs)],
+    "cap_height_abs_zi": [(vndf, "sample_cap", _cap_abs_height)],
 }
 
 
@@ -215,7 +229,18 @@ def _detectors():
     def reflected_density():
         return oc.reflected_change_of_variables_error(n=200) > 1e-8
 
-    return dict(reflection=reflection, reflected_density=reflected_density, philox_vs_curand=philox_vs_curand, pair_words=pair_words, invariants=invariants,
+    def extended_normalisation():
+        return max(oc.extended_normalisation_errors(120.0, -60.0, 0.8, 0.6)) > 1e-6
+
+    def extended_cov():
+        return oc.extended_change_of_variables_error(n=500) > 1e-8
+
+    def extended_alpha_one():
+        a, b = oc.extended_alpha_one_errors(n=2000)
+        return a > 1e-13 or b > 1e-12
+
+    return dict(extended_normalisation=extended_normalisation, extended_cov=extended_cov,
+                extended_alpha_one=extended_alpha_one, reflection=reflection, reflected_density=reflected_density, philox_vs_curand=philox_vs_curand, pair_words=pair_words, invariants=invariants,
                 mirror=mirror, cov=cov, alpha_one=alpha_one, symmetry=symmetry,
                 normalisation=normalisation, eq1=eq1, brute_force=brute_force, prior=prior,
                 g_textbook=g_textbook, albedo=albedo)
