@@ -60,6 +60,7 @@ def parse_args():
     p.add_argument("--no-microbench", action="store_true")
     p.add_argument("--no-reflection", action="store_true")
     p.add_argument("--no-cpu-protocol", action="store_true")
+    p.add_argument("--no-extended", action="store_true")
     p.add_argument("--log2n-adjoint", type=int, default=24)
     return p.parse_args()
 
@@ -74,6 +75,7 @@ KERNEL_FILES = {
     "albedo": ("albedo.cu", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
     "fit": ("fit.cu", "vndf_adjoint.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
     "reflection": ("reflect.cu", "staging.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
+    "hemisphere": ("hemisphere.cu", "staging.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
 }
 
 
@@ -394,6 +396,10 @@ def run_ours(args, rank, world):
                                 "issue": issue_roofline("reflection", n, rt / steps, clk)}
         result["gpu_launches_reflection"] = steps
 
+    if not args.no_extended:
+        result["extended"] = extended_legs(vndf, dev, base, n, outs, timed, steps, warm, world, peak)
+        result["gpu_launches_extended"] = 2 * steps
+
     if not args.no_fwd_bwd:
         result["fwd_bwd"] = fwd_bwd(vndf, dev, rank, world, timed, peak, args.log2n_adjoint)
         result["fwd_bwd"]["issue"] = issue_roofline("loss_backward", 1 << args.log2n_adjoint,
@@ -505,6 +511,36 @@ def microbench(vndf, dev, world, timed):
     out["cap_strict_over_prior"] = out["cap_strict"]["value"] / out["polar"]["value"]
     out["paper_reference"] = "paper: cap faster by 52.96 % (Arc A770) and 39.25 % (RTX 2080), DX12 compute"
     return out
+
+
+def extended_legs(vndf, dev, base, n, outs, timed, steps, warm, world, peak):
+    """The extended domain (2^28 sphere workload, half below the horizon) and the stand-alone
+    hemisphere sampler (2^28 directions of mixed length), HBM-resident, Philox in-kernel."""
+    import torch
+
+    import workloads
+    res = {}
+    d = workloads.sphere_stream(n=n, device=dev)
+    t, _, _ = timed(lambda: vndf.vndf_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], seed=2,
+                                             counter_base=base, method="cap_extended", wm_x=outs[0], wm_y=outs[1],
+                                             wm_z=outs[2], pdf=outs[3]), steps, warm)
+    ms = t / steps
+    res["sphere"] = {"workload": "sphere_stream_2e28", "value": world * n / (ms * 1e-3) / 1e9, "unit": UNIT,
+                     "ms_per_step": ms, "bytes_per_sample": BYTES_PER_SAMPLE,
+                     "roofline_frac": BYTES_PER_SAMPLE * n / (ms * 1e-3) / 1e9 / peak,
+                     "method": "spherical_cap_extended"}
+    del d
+    h = workloads.hemisphere_stream(n=n, device=dev)
+    t, _, _ = timed(lambda: vndf.vndf_sample_hemisphere(h["wi_x"], h["wi_y"], h["wi_z"], seed=2, counter_base=base,
+                                                        wm_x=outs[0], wm_y=outs[1], wm_z=outs[2], pdf=outs[3]),
+                    steps, warm)
+    ms = t / steps
+    res["hemisphere"] = {"workload": "hemisphere_stream_2e28", "value": world * n / (ms * 1e-3) / 1e9,
+                         "unit": UNIT, "ms_per_step": ms, "bytes_per_sample": 28,
+                         "roofline_frac": 28 * n / (ms * 1e-3) / 1e9 / peak}
+    del h
+    torch.cuda.empty_cache()
+    return res
 
 
 def cpu_protocol(vndf, n=1 << 20, runs=100):

@@ -61,6 +61,19 @@ extern "C" {
 /* The prior sampler of Heitz 2018 that the paper improves on: uniform point on
  * the projected cross section of the hemisphere (Sec. 2, step (2)). */
 #define VNDF_METHOD_POLAR_DISK 1
+/* The spherical-cap sampler on the extended domain: incident directions
+ * below the horizon as well.  Sec. 3.2-3.3 and Eq. 4 never use wi.z > 0: for
+ * every stretched direction i with i.z > -1 the cap z in (-i.z, 1] and
+ * sigma_std = (1 + i.z)/2 stay valid, and the samples are the normals with
+ * wm.z > 0 that face wi, distributed as max(0, wi.wm) D(wm) / sigma(wi) with
+ * sigma(wi) = (|M^-1 wi| + wi.z)/2 for unit wi (the projected area of the
+ * microsurface).  Random walks on a microsurface meet such directions.  The
+ * paper states the method for the upper hemisphere only; this extension is a
+ * reading of it.  Domain: alpha_x, alpha_y > 0, all finite, and
+ * 1 + i.z >= 2^-40 (i at least about 1.4e-6 rad from straight down); outside
+ * it the usual fallback.  For wi.z > 0 results equal VNDF_METHOD_SPHERICAL_CAP
+ * bit for bit.  Accepted by vndf_sample only. */
+#define VNDF_METHOD_SPHERICAL_CAP_EXTENDED 2
 
 /* Version of this ABI; bumped on any incompatible change. */
 int vndf_abi_version(void);
@@ -101,7 +114,8 @@ int vndf_rng_uniform(int64_t n, uint64_t seed, uint64_t counter_base, uint32_t s
  *   alpha_x, alpha_y   roughness; alpha_y = NULL means isotropic (alpha_y = alpha_x).
  *   u1, u2             explicit uniforms in [0, 1), or both NULL for in-kernel Philox.
  *   seed, counter_base, stream_id   Philox parameters (ignored with explicit u).
- *   method             VNDF_METHOD_SPHERICAL_CAP or VNDF_METHOD_POLAR_DISK.
+ *   method             VNDF_METHOD_SPHERICAL_CAP, VNDF_METHOD_POLAR_DISK or
+ *                      VNDF_METHOD_SPHERICAL_CAP_EXTENDED.
  *   wm_x, wm_y, wm_z   outputs: unit microfacet normal.
  *   pdf                output density (solid angle of wm), or NULL to skip it.
  * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, ALIGN, METHOD, ARG, CUDA).
@@ -158,6 +172,47 @@ int vndf_pdf(int64_t n,
              const float *alpha_x, const float *alpha_y,
              const float *wm_x, const float *wm_y, const float *wm_z,
              float *pdf, void *cuda_stream);
+
+/*
+ * vndf_pdf_extended -- vndf_pdf on the domain of
+ * VNDF_METHOD_SPHERICAL_CAP_EXTENDED (wi may lie below the horizon):
+ *   pdf = max(0, wi.wm) D(wm) / sigma(wi),  sigma(wi) = (|M^-1 wi| + wi.z)/2
+ * for unit wi (Eq. 1 with the projected area of Eq. 4 carried through M; it
+ * equals the G1 form of vndf_pdf wherever wi.z > 0).  Same arguments, layout
+ * and errors as vndf_pdf; inputs outside the extended domain, or wm.z <= 0,
+ * give 0.
+ */
+int vndf_pdf_extended(int64_t n,
+                      const float *wi_x, const float *wi_y, const float *wi_z,
+                      const float *alpha_x, const float *alpha_y,
+                      const float *wm_x, const float *wm_y, const float *wm_z,
+                      float *pdf, void *cuda_stream);
+
+/*
+ * vndf_sample_hemisphere -- the spherical-cap sampler of Sec. 3.3 used on its
+ * own: visible normals of the hemisphere configuration (D_std = 1/pi on the
+ * upper hemisphere, Eq. 3) seen from direction wi.  Sec. 3.3 leaves the half
+ * vector h = c + wi unnormalised because the GGX sampler normalises after
+ * unstretching; here the output is h / |h|, the normalisation a stand-alone
+ * use needs, and the density is Eq. 2,
+ *   pdf = max(0, wi.wm) / (pi sigma_std(wi.z)),  sigma_std = (1 + wi.z)/2 (Eq. 4),
+ * which equals |h| / (pi (1 + wi.z)) at the sample.  It is the GGX sampler
+ * with alpha_x = alpha_y = 1 (where D = 1/pi) without the roughness streams.
+ *   n                  number of samples (0 <= n < 2^62).
+ *   wi_x, wi_y, wi_z   direction (any length; normalised internally); the
+ *                      extended domain applies: 1 + wi.z/|wi| >= 2^-40, finite.
+ *   u1, u2             explicit uniforms in [0, 1), or both NULL for in-kernel Philox.
+ *   seed, counter_base, stream_id   Philox parameters (ignored with explicit u).
+ *   wm_x, wm_y, wm_z   outputs: unit normal (wm.z > 0); (0, 0, 1) outside the domain.
+ *   pdf                output density (solid angle), or NULL to skip it; 0 outside the domain.
+ * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, ALIGN, ARG, CUDA).
+ */
+int vndf_sample_hemisphere(int64_t n,
+                           const float *wi_x, const float *wi_y, const float *wi_z,
+                           const float *u1, const float *u2,
+                           uint64_t seed, uint64_t counter_base, uint32_t stream_id,
+                           float *wm_x, float *wm_y, float *wm_z, float *pdf,
+                           void *cuda_stream);
 
 /*
  * vndf_sample_backward -- reparameterised gradients of the spherical-cap

@@ -1,0 +1,48 @@
+"""The cap sampler and its density in 50-digit arithmetic (mpmath): test infrastructure.
+
+Below the horizon at small roughness, 1 + z_i' (z_i' the height of the
+stretched incident direction) can be as small as 1e-10, and the FP64 oracle
+(``oracle.vndf``) then loses digits to cancellation in 1 + z_i', in the cap
+height and in 1 - z^2.  This module evaluates the same steps at 50 significant
+digits, one sample at a time, as the reference for those samples.  Only tests
+import it; it shares no code with the CUDA library.
+
+Steps (Dupuy & Benyoub, HPG 2023):
+* Sec. 2 step (1): i = M^-1 wi / |M^-1 wi|, M^-1 = diag(ax, ay, 1)
+* Sec. 3.3: phi = 2 pi u1, z = (1 - u2)(1 + i.z) - i.z, c = (sqrt(1 - z^2) cos phi,
+  sqrt(1 - z^2) sin phi, z), h = c + i
+* Sec. 2 step (3): v = (ax hx, ay hy, hz), wm = v / |v|
+* Eqs. 1-4 at the sample: pdf = |v|^3 / (pi ax ay (1 + i.z) |h|^2)
+"""
+import mpmath
+
+DIGITS = 50
+
+
+def sample_with_pdf(u1, u2, wi, ax, ay):
+    """(wm (3 floats), pdf float) for one sample; inputs are exact binary floats."""
+    with mpmath.workdps(DIGITS):
+        u1, u2, ax, ay = (mpmath.mpf(float(t)) for t in (u1, u2, ax, ay))
+        wx, wy, wz = (mpmath.mpf(float(t)) for t in wi)
+        sx, sy = ax * wx, ay * wy
+        el = mpmath.sqrt(sx * sx + sy * sy + wz * wz)
+        ix, iy, iz = sx / el, sy / el, wz / el
+        phi = 2 * mpmath.pi * u1
+        z = (1 - u2) * (1 + iz) - iz
+        st = mpmath.sqrt(max(1 - z * z, mpmath.mpf(0)))
+        hx = st * mpmath.cos(phi) + ix
+        hy = st * mpmath.sin(phi) + iy
+        hz = z + iz
+        vx, vy, vz = ax * hx, ay * hy, hz
+        vn = mpmath.sqrt(vx * vx + vy * vy + vz * vz)
+        hh = hx * hx + hy * hy + hz * hz
+        pdf = vn ** 3 / (mpmath.pi * ax * ay * (1 + iz) * hh)
+        return (float(vx / vn), float(vy / vn), float(vz / vn)), float(pdf)
+
+
+def one_plus_zi(wi, ax, ay):
+    """1 + z_i' of the stretched direction, in 50 digits (for selecting and reporting samples)."""
+    with mpmath.workdps(DIGITS):
+        sx, sy = mpmath.mpf(float(ax)) * mpmath.mpf(float(wi[0])), mpmath.mpf(float(ay)) * mpmath.mpf(float(wi[1]))
+        wz = mpmath.mpf(float(wi[2]))
+        return float(1 + wz / mpmath.sqrt(sx * sx + sy * sy + wz * wz))

@@ -17,7 +17,8 @@ import torch
 _PKG_DIR = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG_DIR, "libvndf.so")
 
-METHODS = {"cap": 0, "spherical_cap": 0, "polar": 1, "polar_disk": 1}
+METHODS = {"cap": 0, "spherical_cap": 0, "polar": 1, "polar_disk": 1, "cap_extended": 2,
+           "spherical_cap_extended": 2}
 
 VNDF_OK = 0
 _P = ctypes.c_void_p
@@ -37,6 +38,8 @@ SIGNATURES = {
     "vndf_sample": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _U64, _U64, _U32, ctypes.c_int,
                                    _P, _P, _P, _P, _P]),
     "vndf_pdf": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "vndf_pdf_extended": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "vndf_sample_hemisphere": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _U64, _U64, _U32, _P, _P, _P, _P, _P]),
     "vndf_sample_reflection": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _U64, _U64, _U32, _F,
                                               _P, _P, _P, _P, _P, _P]),
     "vndf_sample_backward": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _U64, _U64, _U32,
@@ -207,16 +210,40 @@ def vndf_sample_reflection(wi_x, wi_y, wi_z, alpha_x, alpha_y=None, u1=None, u2=
     return wo_x, wo_y, wo_z, pdf, weight
 
 
-def vndf_pdf(wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf=None, n=None, stream=None):
-    """GGX VNDF density of the given normals; see vndf_pdf in include/vndf.h."""
+def vndf_pdf(wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf=None, n=None, stream=None,
+             extended=False):
+    """GGX VNDF density of the given normals; see vndf_pdf (and, with extended=True,
+    vndf_pdf_extended) in include/vndf.h."""
     n = wi_x.numel() if n is None else int(n)
     pdf = _out(pdf, n, wi_x)
-    st = load().vndf_pdf(n, _ptr(wi_x, "wi_x"), _ptr(wi_y, "wi_y"), _ptr(wi_z, "wi_z"),
-                         _ptr(alpha_x, "alpha_x"), _ptr(alpha_y, "alpha_y"), _ptr(wm_x, "wm_x"),
-                         _ptr(wm_y, "wm_y"), _ptr(wm_z, "wm_z"), _ptr(pdf, "pdf"),
-                         _stream(stream, wi_x.device))
-    _check("vndf_pdf", st)
+    name = "vndf_pdf_extended" if extended else "vndf_pdf"
+    st = getattr(load(), name)(n, _ptr(wi_x, "wi_x"), _ptr(wi_y, "wi_y"), _ptr(wi_z, "wi_z"),
+                               _ptr(alpha_x, "alpha_x"), _ptr(alpha_y, "alpha_y"), _ptr(wm_x, "wm_x"),
+                               _ptr(wm_y, "wm_y"), _ptr(wm_z, "wm_z"), _ptr(pdf, "pdf"),
+                               _stream(stream, wi_x.device))
+    _check(name, st)
     return pdf
+
+
+def vndf_pdf_extended(wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf=None, n=None, stream=None):
+    """vndf_pdf on the extended domain (wi below the horizon too); see include/vndf.h."""
+    return vndf_pdf(wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf, n, stream, extended=True)
+
+
+def vndf_sample_hemisphere(wi_x, wi_y, wi_z, u1=None, u2=None, seed=0, counter_base=0, stream_id=0, wm_x=None,
+                           wm_y=None, wm_z=None, pdf=None, with_pdf=True, n=None, stream=None):
+    """Stand-alone hemisphere sampler (Sec. 3.3, normalised, Eq. 2 density); see include/vndf.h.
+
+    Returns (wm_x, wm_y, wm_z, pdf or None)."""
+    n = wi_x.numel() if n is None else int(n)
+    wm_x, wm_y, wm_z = (_out(t, n, wi_x) for t in (wm_x, wm_y, wm_z))
+    pdf = _out(pdf, n, wi_x) if with_pdf else None
+    st = load().vndf_sample_hemisphere(
+        n, _ptr(wi_x, "wi_x"), _ptr(wi_y, "wi_y"), _ptr(wi_z, "wi_z"), _ptr(u1, "u1"), _ptr(u2, "u2"),
+        int(seed) & (2**64 - 1), int(counter_base) & (2**64 - 1), int(stream_id) & 0xFFFFFFFF,
+        _ptr(wm_x, "wm_x"), _ptr(wm_y, "wm_y"), _ptr(wm_z, "wm_z"), _ptr(pdf, "pdf"), _stream(stream, wi_x.device))
+    _check("vndf_sample_hemisphere", st)
+    return wm_x, wm_y, wm_z, pdf
 
 
 def vndf_sample_backward(wi_x, wi_y, wi_z, alpha_x, alpha_y=None, u1=None, u2=None, seed=0, counter_base=0,

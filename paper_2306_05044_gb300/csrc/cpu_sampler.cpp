@@ -6,7 +6,11 @@
 // that the compiler can vectorise the loop (omp simd), the same rounding-aware
 // formulas as the CUDA kernels (cancellation-free sin^2 for the cap sampler,
 // the rewritten disk lift for the prior one, sin/cos(pi x) from its Taylor
-// series), and std::thread for the split across cores.
+// series), and std::thread for the split across cores.  Where the ISA has a
+// fused multiply-add (every AArch64 core) the loop vectorises; on the x86-64
+// baseline, which has none, std::fma is a library call and the loop stays
+// scalar, with the same results.  -fno-trapping-math lets the compiler compute
+// both sides of the domain selects.
 #include <cmath>
 #include <cstdint>
 #include <thread>

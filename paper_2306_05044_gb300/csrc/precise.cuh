@@ -100,6 +100,7 @@ __device__ __forceinline__ void df_sincospi_reduced(float r, df& s, df& c) {
 
 // h = c + i for the cap sampler, with c and i carried in double-float and h
 // rounded once (same formulas as cap_half_vector).  Also returns a = 1 + i.z.
+template <bool EXT = false>
 __device__ __forceinline__ void cap_half_vector_precise(float wx, float wy, float wz, float ax, float ay, float u1,
                                                        float u2, float& hx, float& hy, float& hz, float& a_out) {
   // i = s / |s|, s = (ax wx, ay wy, wz): exact products, one Newton step on rsqrt
@@ -111,9 +112,19 @@ __device__ __forceinline__ void cap_half_vector_precise(float wx, float wy, floa
   const df rr = df_fast_two_sum(r0, 0.5f * r0 * res.hi);     // r0 (1 + res / 2)
   const df ix = df_mul(sx, rr), iy = df_mul(sy, rr), iz = df_mul(sz, rr);
   // sin^2 = u2 (2 a (1 - u2) + u2 (i.x^2 + i.y^2)), a = 1 + i.z
-  const df a = df_add_f(iz, 1.f);
-  const float om = 1.f - u2;  // exact
   const df rho2 = df_add(df_mul(ix, ix), df_mul(iy, iy));
+  df a = df_add_f(iz, 1.f);
+  if constexpr (EXT) {
+    if (iz.hi < 0.f) {
+      // a = rho2 / (1 - i.z): quotient q, then one correction (rho2 - q d) / d
+      const df d = df_add_f(df{-iz.hi, -iz.lo}, 1.f);
+      const float q = rho2.hi / d.hi;
+      const df qd = df_mul_f(d, q);
+      const df r = df_add(rho2, df{-qd.hi, -qd.lo});
+      a = df_fast_two_sum(q, r.hi / d.hi);
+    }
+  }
+  const float om = 1.f - u2;  // exact
   const df S = df_add(df_mul_f(a, 2.f * om), df_mul_f(rho2, u2));
   const df sin2 = df_mul_f(S, u2);
   const float s0 = sqrtf(sin2.hi);

@@ -90,12 +90,13 @@ __global__ void __launch_bounds__(kSampleBlock, VNDF_SAMPLE_MIN_BLOCKS) sample_v
       rescue |= unsigned(sample_one<METHOD, PDF, true>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], MX[k], MY[k],
                                                        MZ[k], P[k]))
                 << k;
-    if constexpr (METHOD == kMethodCap) {
+    if constexpr (is_cap<METHOD>()) {
       if (rescue) {  // rare: ill-conditioned samples redone in double-float
 #pragma unroll
         for (int k = 0; k < 4; ++k)
           if (rescue & (1u << k)) {
-            const float4 r = sample_one_precise<PDF>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k]);
+            const float4 r =
+                sample_one_precise<PDF, METHOD == kMethodCapExt>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k]);
             MX[k] = r.x;
             MY[k] = r.y;
             MZ[k] = r.z;
@@ -168,12 +169,13 @@ __global__ void __launch_bounds__(kSampleBlock, VNDF_SAMPLE_MIN_BLOCKS) sample_p
       rescue |= unsigned(sample_one<METHOD, PDF, true>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], MX[k], MY[k],
                                                        MZ[k], P[k]))
                 << k;
-    if constexpr (METHOD == kMethodCap) {
+    if constexpr (is_cap<METHOD>()) {
       if (rescue) {  // rare: ill-conditioned samples redone in double-float
 #pragma unroll
         for (int k = 0; k < 4; ++k)
           if (rescue & (1u << k)) {
-            const float4 r = sample_one_precise<PDF>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k]);
+            const float4 r =
+                sample_one_precise<PDF, METHOD == kMethodCapExt>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k]);
             MX[k] = r.x;
             MY[k] = r.y;
             MZ[k] = r.z;
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(kBlock) sample_scalar_kernel(SampleArgs a, int
     float mx, my, mz, p;
     const float wx = a.wx[e], wy = a.wy[e], wz = a.wz[e];
     if (sample_one<METHOD, PDF, true>(wx, wy, wz, ax, ay, u1, u2, mx, my, mz, p)) {
-      const float4 r = sample_one_precise<PDF>(wx, wy, wz, ax, ay, u1, u2);
+      const float4 r = sample_one_precise<PDF, METHOD == kMethodCapExt>(wx, wy, wz, ax, ay, u1, u2);
       mx = r.x;
       my = r.y;
       mz = r.z;
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(kBlock) rng_scalar_kernel(Rng r, float* u1, fl
 }
 
 // ---------------------------------------------------------------- pdf
-template <bool ISO>
+template <bool ISO, bool EXT>
 __global__ void __launch_bounds__(kBlock) pdf_vec4_kernel(const float* wx, const float* wy, const float* wz,
                                                           const float* ax, const float* ay, const float* mx,
                                                           const float* my, const float* mz, float* pdf,
@@ -309,12 +311,12 @@ __global__ void __launch_bounds__(kBlock) pdf_vec4_kernel(const float* wx, const
     *reinterpret_cast<float4*>(MY) = ld_stream(my + e);
     *reinterpret_cast<float4*>(MZ) = ld_stream(mz + e);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) P[k] = pdf_of_normal(X[k], Y[k], Z[k], AX[k], AY[k], MX[k], MY[k], MZ[k]);
+    for (int k = 0; k < 4; ++k) P[k] = pdf_of_normal<EXT>(X[k], Y[k], Z[k], AX[k], AY[k], MX[k], MY[k], MZ[k]);
     st_stream(pdf + e, *reinterpret_cast<float4*>(P));
   }
 }
 
-template <bool ISO>
+template <bool ISO, bool EXT>
 __global__ void __launch_bounds__(kBlock) pdf_scalar_kernel(const float* wx, const float* wy, const float* wz,
                                                             const float* ax, const float* ay, const float* mx,
                                                             const float* my, const float* mz, float* pdf,
@@ -322,22 +324,23 @@ __global__ void __launch_bounds__(kBlock) pdf_scalar_kernel(const float* wx, con
   const int64_t stride = int64_t(gridDim.x) * kBlock;
   for (int64_t e = begin + int64_t(blockIdx.x) * kBlock + threadIdx.x; e < n; e += stride) {
     const float a = ax[e];
-    pdf[e] = pdf_of_normal(wx[e], wy[e], wz[e], a, ISO ? a : ay[e], mx[e], my[e], mz[e]);
+    pdf[e] = pdf_of_normal<EXT>(wx[e], wy[e], wz[e], a, ISO ? a : ay[e], mx[e], my[e], mz[e]);
   }
 }
 
-template <bool ISO>
+template <bool ISO, bool EXT>
 int launch_pdf(int64_t n, const float* wx, const float* wy, const float* wz, const float* ax, const float* ay,
                const float* mx, const float* my, const float* mz, float* pdf, bool vec, cudaStream_t s) {
   int64_t done = 0;
   if (vec && n / 4 > 0) {
     const int64_t n4 = n / 4;
-    pdf_vec4_kernel<ISO><<<grid_for(n4, kBlock, 8, 32), kBlock, 0, s>>>(wx, wy, wz, ax, ay, mx, my, mz, pdf, n4);
+    pdf_vec4_kernel<ISO, EXT>
+        <<<grid_for(n4, kBlock, 8, 32), kBlock, 0, s>>>(wx, wy, wz, ax, ay, mx, my, mz, pdf, n4);
     done = 4 * n4;
   }
   if (done < n)
-    pdf_scalar_kernel<ISO><<<grid_for(n - done, kBlock, 8, 32), kBlock, 0, s>>>(wx, wy, wz, ax, ay, mx, my, mz,
-                                                                                  pdf, done, n);
+    pdf_scalar_kernel<ISO, EXT><<<grid_for(n - done, kBlock, 8, 32), kBlock, 0, s>>>(wx, wy, wz, ax, ay, mx, my,
+                                                                                       mz, pdf, done, n);
   return launch_status();
 }
 
@@ -368,7 +371,9 @@ extern "C" int vndf_sample(int64_t n, const float* wi_x, const float* wi_y, cons
                            uint64_t seed, uint64_t counter_base, uint32_t stream_id, int method, float* wm_x,
                            float* wm_y, float* wm_z, float* pdf, void* cuda_stream) {
   if (n < 0 || n >= kMaxN) return VNDF_ERR_SIZE;
-  if (method != VNDF_METHOD_SPHERICAL_CAP && method != VNDF_METHOD_POLAR_DISK) return VNDF_ERR_METHOD;
+  if (method != VNDF_METHOD_SPHERICAL_CAP && method != VNDF_METHOD_POLAR_DISK &&
+      method != VNDF_METHOD_SPHERICAL_CAP_EXTENDED)
+    return VNDF_ERR_METHOD;
   if (n == 0) return VNDF_OK;
   if (!wi_x || !wi_y || !wi_z || !alpha_x || !wm_x || !wm_y || !wm_z) return VNDF_ERR_NULL;
   if ((u1 == nullptr) != (u2 == nullptr)) return VNDF_ERR_ARG;
@@ -377,19 +382,33 @@ extern "C" int vndf_sample(int64_t n, const float* wi_x, const float* wi_y, cons
                make_rng(seed, counter_base, stream_id)};
   const bool vec = all_aligned16(wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, wm_x, wm_y, wm_z, pdf);
   const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  return method == VNDF_METHOD_SPHERICAL_CAP ? dispatch_rng<kMethodCap>(a, n, vec, s)
-                                             : dispatch_rng<kMethodPolar>(a, n, vec, s);
+  if (method == VNDF_METHOD_SPHERICAL_CAP) return dispatch_rng<kMethodCap>(a, n, vec, s);
+  if (method == VNDF_METHOD_POLAR_DISK) return dispatch_rng<kMethodPolar>(a, n, vec, s);
+  return dispatch_rng<kMethodCapExt>(a, n, vec, s);
 }
 
-extern "C" int vndf_pdf(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z, const float* alpha_x,
-                        const float* alpha_y, const float* wm_x, const float* wm_y, const float* wm_z, float* pdf,
-                        void* cuda_stream) {
+template <bool EXT>
+int pdf_entry(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z, const float* alpha_x,
+              const float* alpha_y, const float* wm_x, const float* wm_y, const float* wm_z, float* pdf,
+              void* cuda_stream) {
   if (n < 0 || n >= kMaxN) return VNDF_ERR_SIZE;
   if (n == 0) return VNDF_OK;
   if (!wi_x || !wi_y || !wi_z || !alpha_x || !wm_x || !wm_y || !wm_z || !pdf) return VNDF_ERR_NULL;
   if (!all_aligned4(wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf)) return VNDF_ERR_ALIGN;
   const bool vec = all_aligned16(wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf);
   const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  return alpha_y ? launch_pdf<false>(n, wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf, vec, s)
-                 : launch_pdf<true>(n, wi_x, wi_y, wi_z, alpha_x, alpha_x, wm_x, wm_y, wm_z, pdf, vec, s);
+  return alpha_y ? launch_pdf<false, EXT>(n, wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf, vec, s)
+                 : launch_pdf<true, EXT>(n, wi_x, wi_y, wi_z, alpha_x, alpha_x, wm_x, wm_y, wm_z, pdf, vec, s);
+}
+
+extern "C" int vndf_pdf(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z, const float* alpha_x,
+                        const float* alpha_y, const float* wm_x, const float* wm_y, const float* wm_z, float* pdf,
+                        void* cuda_stream) {
+  return pdf_entry<false>(n, wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf, cuda_stream);
+}
+
+extern "C" int vndf_pdf_extended(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z,
+                                 const float* alpha_x, const float* alpha_y, const float* wm_x, const float* wm_y,
+                                 const float* wm_z, float* pdf, void* cuda_stream) {
+  return pdf_entry<true>(n, wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf, cuda_stream);
 }

@@ -37,6 +37,19 @@ namespace vndf {
 constexpr float kPi = 3.14159265358979323846f;
 constexpr int kMethodCap = 0;
 constexpr int kMethodPolar = 1;
+// The cap sampler on the extended domain: incident directions below the
+// horizon too.  Nothing in Sec. 3.2-3.3 or Eq. 4 needs wi.z > 0: the cap
+// z in (-i.z, 1] and sigma_std = (1 + i.z)/2 hold for every i.z > -1, and the
+// samples are the normals with wm.z > 0 that face wi.  For i.z < 0 the value
+// a = 1 + i.z is formed as (i.x^2 + i.y^2) / (1 - i.z), which does not cancel.
+constexpr int kMethodCapExt = 2;
+// Smallest a = 1 + i.z of the extended domain: the stretched direction at
+// least about 1.4e-6 rad from straight down.  Below it the cap has shrunk to a
+// point and the inputs take the fallback.
+constexpr float kMinCapA = 0x1p-40f;
+
+template <int METHOD>
+constexpr bool is_cap() { return METHOD == kMethodCap || METHOD == kMethodCapExt; }
 
 __device__ __forceinline__ bool finite_f(float x) { return fabsf(x) < __int_as_float(0x7f800000); }
 
@@ -85,6 +98,20 @@ __device__ __forceinline__ bool in_domain(float wx, float wy, float wz, float ax
          finite_f(ax) & finite_f(ay);
 }
 
+// The part of the extended domain known before stretching (alphas > 0, all
+// finite); a >= kMinCapA is tested once a is formed (a NaN a fails it).
+__device__ __forceinline__ bool in_domain_ext_inputs(float wx, float wy, float wz, float ax, float ay) {
+  return (ax > 0.f) & (ay > 0.f) & finite_f(wx) & finite_f(wy) & finite_f(wz) & finite_f(ax) & finite_f(ay);
+}
+
+template <int METHOD>
+__device__ __forceinline__ bool in_domain_m(float wx, float wy, float wz, float ax, float ay) {
+  if constexpr (METHOD == kMethodCapExt)
+    return in_domain_ext_inputs(wx, wy, wz, ax, ay);
+  else
+    return in_domain(wx, wy, wz, ax, ay);
+}
+
 struct Stretched {
   float x, y, z;  // i = M^-1 wi / |M^-1 wi|
 };
@@ -96,11 +123,16 @@ __device__ __forceinline__ Stretched stretch(float wx, float wy, float wz, float
   return {sx * r, sy * r, wz * r};
 }
 
-// Spherical-cap hemisphere sample: returns h = c + i (unnormalised).
+// Spherical-cap hemisphere sample: returns h = c + i (unnormalised).  With
+// EXT, i.z may be negative and a = 1 + i.z is formed without cancellation.
+template <bool EXT = false>
 __device__ __forceinline__ void cap_half_vector(const Stretched& i, float u1, float u2,
                                                 float& hx, float& hy, float& hz, float& a) {
-  a = 1.f + i.z;
   const float rho2 = fmaf(i.x, i.x, i.y * i.y);                 // 1 - i.z^2
+  if constexpr (EXT)
+    a = i.z >= 0.f ? 1.f + i.z : __fdividef(rho2, 1.f - i.z);  // 1 - i.z in [1, 2]
+  else
+    a = 1.f + i.z;
   const float sin2 = u2 * fmaf(2.f * a, 1.f - u2, u2 * rho2);  // (1 - z)(1 + z)
   const float st = sqrtf(sin2);
   float sp, cp;
@@ -173,7 +205,7 @@ __device__ __forceinline__ void finish_sample(const Stretched& i, float ax, floa
   mz = vz * rv;
   if constexpr (PDF) {
     const float v3 = vv * vv * rv;  // |v|^3
-    if constexpr (METHOD == kMethodCap) {
+    if constexpr (is_cap<METHOD>()) {
       const float hh = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
       pdf = __fdividef(v3, kPi * ax * ay * a * hh);
     } else {
@@ -192,18 +224,19 @@ template <int METHOD, bool PDF, bool PRECISE = false>
 __device__ __forceinline__ bool sample_one(float wx, float wy, float wz, float ax, float ay,
                                            float u1, float u2,
                                            float& mx, float& my, float& mz, float& pdf) {
-  const bool ok = in_domain(wx, wy, wz, ax, ay);
+  bool ok = in_domain_m<METHOD>(wx, wy, wz, ax, ay);
   const Stretched i = stretch(wx, wy, wz, ax, ay);
   float hx, hy, hz, a;
-  if constexpr (METHOD == kMethodCap) {
-    cap_half_vector(i, u1, u2, hx, hy, hz, a);
+  if constexpr (is_cap<METHOD>()) {
+    cap_half_vector<METHOD == kMethodCapExt>(i, u1, u2, hx, hy, hz, a);
+    if constexpr (METHOD == kMethodCapExt) ok &= a >= kMinCapA;
   } else {
     polar_disk_normal(i, u1, u2, hx, hy, hz);
     a = 1.f + i.z;
   }
   finish_sample<METHOD, PDF>(i, ax, ay, hx, hy, hz, a, mx, my, mz, pdf);
   bool bad = false;
-  if constexpr (PRECISE && METHOD == kMethodCap) {
+  if constexpr (PRECISE && is_cap<METHOD>()) {
     // |c.x| + |i.x| etc. bound the rounding of h; compare it with |v| and |h|
     const float sx = fabsf(hx - i.x) + fabsf(i.x), sy = fabsf(hy - i.y) + fabsf(i.y);
     const float vx = ax * hx, vy = ay * hy;
@@ -228,11 +261,11 @@ __device__ __forceinline__ bool sample_one(float wx, float wy, float wz, float a
 // The cap sample recomputed with its half vector in double-float (in-domain
 // inputs only); returns (wm.x, wm.y, wm.z, pdf).  Not inlined, and returning by
 // value, so that the rare path neither bloats nor spills the FP32 path.
-template <bool PDF>
+template <bool PDF, bool EXT = false>
 __device__ __noinline__ float4 sample_one_precise(float wx, float wy, float wz, float ax, float ay, float u1,
                                                   float u2) {
   float hx, hy, hz, a;
-  cap_half_vector_precise(wx, wy, wz, ax, ay, u1, u2, hx, hy, hz, a);
+  cap_half_vector_precise<EXT>(wx, wy, wz, ax, ay, u1, u2, hx, hy, hz, a);
   float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
   finish_sample<kMethodCap, PDF>(Stretched{0.f, 0.f, 0.f}, ax, ay, hx, hy, hz, a, r.x, r.y, r.z, r.w);
   return r;
@@ -240,15 +273,24 @@ __device__ __noinline__ float4 sample_one_precise(float wx, float wy, float wz, 
 
 // Density of a given normal (Eq. 1 through the App. A forms of D and G1):
 // 2 max(0, wi.wm) / (pi ax ay (|M^-1 wi| + wi.z) Q^2), Q = mx^2/ax^2 + my^2/ay^2 + mz^2.
+// |M^-1 wi| + wi.z is twice the projected area of the microsurface seen from
+// wi (unit wi); with EXT (incident directions below the horizon) it is formed
+// as (sx^2 + sy^2) / (|M^-1 wi| - wi.z) when wi.z < 0, which does not cancel.
+template <bool EXT = false>
 __device__ __forceinline__ float pdf_of_normal(float wx, float wy, float wz, float ax, float ay,
                                                float mx, float my, float mz) {
-  const bool ok = in_domain(wx, wy, wz, ax, ay) & (mz > 0.f);
+  bool ok = (EXT ? in_domain_ext_inputs(wx, wy, wz, ax, ay) : in_domain(wx, wy, wz, ax, ay)) & (mz > 0.f);
   const float sx = ax * wx, sy = ay * wy;
   const float l = sqrtf(fmaf(sx, sx, fmaf(sy, sy, wz * wz)));
+  float lw = l + wz;
+  if constexpr (EXT) {
+    if (wz < 0.f) lw = fmaf(sx, sx, sy * sy) / (l - wz);
+    ok &= lw >= kMinCapA * l;  // a = 1 + i.z = lw / l
+  }
   const float qx = __fdividef(mx, ax), qy = __fdividef(my, ay);
   const float q = fmaf(qx, qx, fmaf(qy, qy, mz * mz));
   const float d = fmaxf(fmaf(wx, mx, fmaf(wy, my, wz * mz)), 0.f);
-  const float p = __fdividef(2.f * d, kPi * ax * ay * (l + wz) * q * q);
+  const float p = __fdividef(2.f * d, kPi * ax * ay * lw * q * q);
   return ok ? p : 0.f;
 }
 

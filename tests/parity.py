@@ -29,6 +29,7 @@ import numpy as np
 from oracle import vndf
 
 EPS32 = 2.0 ** -24
+A_MP = 1e-9  # below this 1 + z_i' the 50-digit reference replaces the FP64 oracle
 K_ULP = 8.0
 ANGLE_TOL = 4e-6
 PDF_TOL = 1e-5
@@ -51,17 +52,37 @@ def conditioning(u1, u2, wi, ax, ay):
     return kap, kap_h
 
 
-def compare_cap(wm_gpu, pdf_gpu, u1, u2, wi, ax, ay, strict=True):
-    """Check GPU cap samples against the oracle; returns a stats dict (asserts the bounds)."""
+def one_plus_zi(wi, ax, ay):
+    """1 + z_i' of the stretched direction without cancellation (FP64), for selecting samples."""
+    sx, sy, wz = ax * wi[0], ay * wi[1], wi[2]
+    el = np.sqrt(sx * sx + sy * sy + wz * wz)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(wz >= 0, 1.0 + wz / el, (sx * sx + sy * sy) / (el * (el - wz)))
+
+
+def compare_cap(wm_gpu, pdf_gpu, u1, u2, wi, ax, ay, strict=True, extended=False):
+    """Check GPU cap samples against the oracle; returns a stats dict (asserts the bounds).
+
+    With extended=True the inputs may lie below the horizon (the extended domain).  There
+    the FP64 oracle itself loses digits when 1 + z_i' < A_MP: such samples are excluded
+    here and checked against the 50-digit reference by ``compare_cap_mp``."""
     wi = np.asarray(wi, np.float64)
     ax = np.asarray(ax, np.float64)
     ay = np.asarray(ay, np.float64)
     u1 = np.asarray(u1, np.float64)
     u2 = np.asarray(u2, np.float64)
-    wm_ref, pdf_ref = vndf.sample_vndf_with_pdf(u1, u2, wi, ax, ay, "cap")
+    wm_ref, pdf_ref = vndf.sample_vndf_with_pdf(u1, u2, wi, ax, ay, "cap", extended)
     wm_gpu = np.asarray(wm_gpu, np.float64)
-    ok = vndf.in_domain(wi, ax, ay)
+    ok = vndf.in_domain(wi, ax, ay, extended)
     stats = {"n": int(u1.size), "out_of_domain": int((~ok).sum())}
+    if extended:
+        with np.errstate(invalid="ignore"):
+            tiny = ok & ~(one_plus_zi(wi, ax, ay) >= A_MP)
+        stats["left_to_mp_reference"] = int(tiny.sum())
+        keep = ~tiny
+        wm_ref, pdf_ref, wm_gpu = wm_ref[:, keep], pdf_ref[keep], wm_gpu[:, keep]
+        pdf_gpu = None if pdf_gpu is None else np.asarray(pdf_gpu)[keep]
+        u1, u2, wi, ax, ay, ok = u1[keep], u2[keep], wi[:, keep], ax[keep], ay[keep], ok[keep]
     # out-of-domain samples: the defined fallback, exactly
     if (~ok).any():
         assert np.all(wm_gpu[:, ~ok] == np.array([[0.0], [0.0], [1.0]]))
@@ -78,7 +99,10 @@ def compare_cap(wm_gpu, pdf_gpu, u1, u2, wi, ax, ay, strict=True):
         f"angle {ang[worst]:.3e} > bound {bound[worst]:.3e} (kappa {kap[worst]:.3g}) at {worst}")
     norm_err = np.abs(np.sqrt(vndf.dot(wm_gpu, wm_gpu)) - 1.0)
     assert norm_err.max() <= 2.0 ** -21
-    contract = (wi[2] / np.sqrt(vndf.dot(wi, wi)) >= 1e-4) & (ax >= 1e-3) & (ay >= 1e-3)
+    if extended:
+        contract = (ax >= 1e-3) & (ay >= 1e-3)
+    else:
+        contract = (wi[2] / np.sqrt(vndf.dot(wi, wi)) >= 1e-4) & (ax >= 1e-3) & (ay >= 1e-3)
     if strict and contract.any():
         worst = np.argmax(np.where(contract, ang, 0))
         assert ang[contract].max() <= ANGLE_TOL, (
@@ -95,7 +119,7 @@ def compare_cap(wm_gpu, pdf_gpu, u1, u2, wi, ax, ay, strict=True):
         oracle_err = 2.0 ** -52 * kap * swm / np.maximum(dwm, 1e-300)
         weak = oracle_err > 1e-7
         if weak.any():
-            pr = np.where(weak, vndf.vndf_pdf_at_cap_sample(u1, u2, wi, ax, ay), pr)
+            pr = np.where(weak, vndf.vndf_pdf_at_cap_sample(u1, u2, wi, ax, ay, extended), pr)
         stats["oracle_pdf_form_switched"] = int(weak.sum())
         rel = np.abs(pg / pr - 1.0)
         pbound = np.maximum(PDF_TOL, K_ULP * (3.0 * kap + 2.0 * kap_h) * EPS32)
@@ -108,3 +132,28 @@ def compare_cap(wm_gpu, pdf_gpu, u1, u2, wi, ax, ay, strict=True):
         stats.update(max_pdf_rel=float(rel.max(initial=0)),
                      tail_pdf_frac=float((rel > PDF_TOL).mean()) if rel.size else 0.0)
     return stats
+
+
+def compare_cap_mp(wm_gpu, pdf_gpu, u1, u2, wi, ax, ay, limit=2000):
+    """Extended-domain samples with 1 + z_i' < A_MP (the FP64 oracle's weak spot) against the
+    50-digit reference (oracle.vndf_mp), at the flat limits.  Checks at most ``limit`` of them."""
+    import pytest
+    mp = pytest.importorskip("oracle.vndf_mp")
+    wi = np.asarray(wi, np.float64)
+    ax = np.asarray(ax, np.float64)
+    ay = np.asarray(ay, np.float64)
+    ok = vndf.in_domain(wi, ax, ay, True)
+    with np.errstate(invalid="ignore"):
+        idx = np.flatnonzero(ok & ~(one_plus_zi(wi, ax, ay) >= A_MP))[:limit]
+    worst_a, worst_p = 0.0, 0.0
+    for k in idx:
+        m, p = mp.sample_with_pdf(u1[k], u2[k], wi[:, k], ax[k], ay[k])
+        g = np.asarray(wm_gpu, np.float64)[:, k]
+        ang = float(angle_between(g.reshape(3, 1), np.array(m).reshape(3, 1))[0])
+        worst_a = max(worst_a, ang)
+        assert ang <= ANGLE_TOL, f"angle {ang:.3e} at sample {k} (1 + z_i' = {mp.one_plus_zi(wi[:, k], ax[k], ay[k]):.3e})"
+        if pdf_gpu is not None:
+            rel = abs(float(pdf_gpu[k]) / p - 1.0)
+            worst_p = max(worst_p, rel)
+            assert rel <= PDF_TOL, f"pdf rel {rel:.3e} at sample {k}"
+    return {"n_mp": int(idx.size), "max_angle_mp": worst_a, "max_pdf_rel_mp": worst_p}

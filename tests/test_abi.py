@@ -84,6 +84,24 @@ def test_rng_and_pdf_reject_bad_arguments(lib):
     assert lib.vndf_pdf(0, FAKE, FAKE, FAKE, FAKE, None, FAKE, FAKE, FAKE, FAKE, None) == 0
 
 
+def test_extended_entry_points_reject_bad_arguments(lib):
+    assert _sample(lib, method=3) == -4
+    assert _sample(lib, method=2, n=-1) == -2
+    assert _sample(lib, method=2, ptrs=[FAKE, None, FAKE]) == -1
+    assert lib.vndf_pdf_extended(-1, FAKE, FAKE, FAKE, FAKE, None, FAKE, FAKE, FAKE, FAKE, None) == -2
+    assert lib.vndf_pdf_extended(4, FAKE, FAKE, FAKE, None, None, FAKE, FAKE, FAKE, FAKE, None) == -1
+    assert lib.vndf_pdf_extended(4, FAKE, FAKE, FAKE + 2, FAKE, None, FAKE, FAKE, FAKE, FAKE, None) == -3
+    hemi = lambda n, wx=FAKE, u1=None, u2=None, mx=FAKE: lib.vndf_sample_hemisphere(  # noqa: E731
+        n, wx, FAKE, FAKE, u1, u2, 0, 0, 0, mx, FAKE, FAKE, FAKE, None)
+    assert hemi(-1) == -2
+    assert hemi(1 << 62) == -2
+    assert hemi(4, wx=None) == -1
+    assert hemi(4, mx=None) == -1
+    assert hemi(4, u1=FAKE) == -7
+    assert hemi(4, wx=FAKE + 1) == -3
+    assert hemi(0, wx=None) == 0
+
+
 def test_binding_fails_loudly_without_gpu_tensors(lib):
     import torch
 

@@ -97,3 +97,34 @@ def test_extended_domain_edges():
         vndf.sample_vndf(u, u, wi, one, one, "polar", extended=True)
     # the upper-domain oracle keeps its fallback for wi.z <= 0
     assert np.all(vndf.vndf_pdf(wm, wi, one, one)[[1, 4]] == 0.0)
+
+
+def test_mp_reference_agrees_with_fp64_where_fp64_is_accurate():
+    """The 50-digit restatement against the FP64 oracle on well-conditioned samples, and against
+    the alpha = 1 closed form (Eqs. 2-4 with D = 1/pi) for directions below the horizon."""
+    mp = pytest.importorskip("oracle.vndf_mp")
+    u1, u2, wi, ax, ay = oc.random_batch_extended(200, 31, alpha_lo=0.1, cos_lo=-0.5)
+    wm, pdf = vndf.sample_vndf_with_pdf(u1, u2, wi, ax, ay, extended=True)
+    for k in range(200):
+        m, p = mp.sample_with_pdf(u1[k], u2[k], wi[:, k], ax[k], ay[k])
+        assert np.abs(np.array(m) - wm[:, k]).max() < 1e-12
+        assert abs(p / pdf[k] - 1) < 1e-10
+    for k in range(50):
+        m, p = mp.sample_with_pdf(u1[k], u2[k], wi[:, k], 1.0, 1.0)
+        closed = 2 * max(0.0, float(np.dot(wi[:, k], m))) / (np.pi * (1 + wi[2, k]))
+        assert abs(p / closed - 1) < 1e-13
+
+
+def test_fp64_oracle_loses_digits_at_tiny_one_plus_zi():
+    """Why the 50-digit reference exists: at 1 + z_i' ~ 1e-11 the FP64 oracle's pdf is off by far more
+    than its accuracy elsewhere, while the 50-digit value keeps the alpha = 1 closed form."""
+    mp = pytest.importorskip("oracle.vndf_mp")
+    wi = np.array([4.5e-6, 0.0, -1.0])
+    m, p = mp.sample_with_pdf(0.3, 0.7, wi, 1.0, 1.0)
+    a = mp.one_plus_zi(wi, 1.0, 1.0)
+    assert 1e-11 < a < 1e-10
+    closed = 2 * max(0.0, float(np.dot(wi / np.linalg.norm(wi), m))) / (np.pi * a)
+    assert abs(p / closed - 1) < 1e-6
+    wm, pd = vndf.sample_vndf_with_pdf(np.array([0.3]), np.array([0.7]), wi.reshape(3, 1), np.ones(1), np.ones(1),
+                                       extended=True)
+    assert abs(pd[0] / p - 1) > 1e-7 and np.abs(wm[:, 0] - m).max() > 1e-7  # FP64: ~1e-6 off here

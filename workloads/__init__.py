@@ -24,6 +24,11 @@ Workloads (sizes are the defaults):
 * ``roughness_map``    256 x 256 texels, alpha_x, alpha_y ~ U[0.05, 0.8],
                        cos(theta_i) ~ U[0.1, 1] per texel, and a smooth target
                        field of unit vectors.
+* ``sphere_stream``    2^28 samples for the extended domain: wi uniform on the
+                       whole sphere (cos(theta_i) ~ U[-1, 1], half of them below
+                       the horizon), alpha_x, alpha_y ~ log-U[1e-3, 1].
+* ``hemisphere_stream`` 2^28 directions for the stand-alone hemisphere sampler:
+                       uniform on the whole sphere, lengths ~ log-U[0.5, 2].
 """
 import math
 
@@ -115,3 +120,20 @@ def roughness_map(res=256, seed=5, device="cpu"):
     ax, ay, wx, wy, wz, tx, ty, tz = _f32(ax, ay, wx, wy, wz, a / n, b / n, 1.0 / n)
     return {"alpha_x": ax, "alpha_y": ay, "wi_x": wx, "wi_y": wy, "wi_z": wz,
             "target_x": tx, "target_y": ty, "target_z": tz}
+
+
+def sphere_stream(n=1 << 28, seed=13, device="cpu"):
+    g = _gen(seed, device)
+    wx, wy, wz = _directions(g, n, -1.0, 1.0, device)
+    ax = _log_uniform(g, n, 1e-3, 1.0, device)
+    ay = _log_uniform(g, n, 1e-3, 1.0, device)
+    wx, wy, wz, ax, ay = _f32(wx, wy, wz, ax, ay)
+    return {"wi_x": wx, "wi_y": wy, "wi_z": wz, "alpha_x": ax, "alpha_y": ay}
+
+
+def hemisphere_stream(n=1 << 28, seed=14, device="cpu"):
+    g = _gen(seed, device)
+    wx, wy, wz = _directions(g, n, -1.0, 1.0, device)
+    r = _log_uniform(g, n, 0.5, 2.0, device)
+    wx, wy, wz = _f32(wx * r, wy * r, wz * r)
+    return {"wi_x": wx, "wi_y": wy, "wi_z": wz}
