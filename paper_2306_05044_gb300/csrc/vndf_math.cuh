@@ -129,10 +129,13 @@ template <bool EXT = false>
 __device__ __forceinline__ void cap_half_vector(const Stretched& i, float u1, float u2,
                                                 float& hx, float& hy, float& hz, float& a) {
   const float rho2 = fmaf(i.x, i.x, i.y * i.y);                 // 1 - i.z^2
+  // an explicit add, never contracted with the stretch's product into an fma:
+  // both variants then round a the same way and agree bit for bit above the horizon
+  const float a_up = __fadd_rn(1.f, i.z);
   if constexpr (EXT)
-    a = i.z >= 0.f ? 1.f + i.z : __fdividef(rho2, 1.f - i.z);  // 1 - i.z in [1, 2]
+    a = i.z >= 0.f ? a_up : __fdividef(rho2, 1.f - i.z);  // 1 - i.z in [1, 2]
   else
-    a = 1.f + i.z;
+    a = a_up;
   const float sin2 = u2 * fmaf(2.f * a, 1.f - u2, u2 * rho2);  // (1 - z)(1 + z)
   const float st = sqrtf(sin2);
   float sp, cp;
