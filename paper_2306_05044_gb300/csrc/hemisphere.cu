@@ -6,11 +6,12 @@
 // sampler of vndf_math.cuh with both roughnesses fixed to 1: the compiler
 // folds the stretch away and the kernel streams 12 bytes in and 16 out per
 // sample (Philox mode).  Ill-conditioned samples (|h| small against its
-// summands) are redone in double-float as in vndf_sample.
+// summands) are redone in double-float as in vndf_sample, batched per warp.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
 #include "philox.cuh"
+#include "rescue.cuh"
 #include "staging.cuh"
 #include "vndf_math.cuh"
 
@@ -48,18 +49,30 @@ __device__ __forceinline__ float4 hemi_one(float wx, float wy, float wz, float u
 }
 
 // Four samples per thread per grid-stride step, inputs staged two steps deep
-// in shared memory with per-thread cp.async copies (no barriers).
+// in shared memory with per-thread cp.async copies (no barriers); flagged
+// samples are queued per warp and redone 32 at a time (rescue.cuh).
 template <bool PHILOX, bool PDF>
 __global__ void __launch_bounds__(kHemiBlock, 3) hemi_pipe_kernel(HemiArgs a, int64_t n4) {
   constexpr int NS = hemi_streams_in<PHILOX>();
-  extern __shared__ float4 smem_h[];  // [2][NS][kHemiBlock]
+  extern __shared__ float4 smem_h[];  // [2][NS][kHemiBlock], then one rescue queue per warp
+  RescueQueue<5>& rq = reinterpret_cast<RescueQueue<5>*>(smem_h + 2 * NS * kHemiBlock)[threadIdx.x >> 5];
+  int pending = 0;  // warp-uniform
   const int64_t stride = int64_t(gridDim.x) * kHemiBlock;
   const int64_t q0 = int64_t(blockIdx.x) * kHemiBlock + threadIdx.x;
+  const int64_t w0 = q0 - (threadIdx.x & 31);
   float4* mine = smem_h + threadIdx.x;
   if (q0 < n4) hemi_stage<PHILOX>(a, 4 * q0, mine);
   cp_async_commit();
+  auto redo = [&](const float (&v)[5], int64_t i) {
+    const float4 r = sample_one_precise<PDF, true>(v[0], v[1], v[2], 1.f, 1.f, v[3], v[4]);
+    a.mx[i] = r.x;
+    a.my[i] = r.y;
+    a.mz[i] = r.z;
+    if constexpr (PDF) a.pdf[i] = r.w;
+  };
   int slot = 0;
-  for (int64_t q = q0; q < n4; q += stride) {
+  for (int64_t q = q0, qw = w0; qw < n4; q += stride, qw += stride) {
+    const bool active = q < n4;
     if (q + stride < n4) hemi_stage<PHILOX>(a, 4 * (q + stride), mine + (slot ^ 1) * NS * kHemiBlock);
     cp_async_commit();
     cp_async_wait<1>();
@@ -83,22 +96,24 @@ __global__ void __launch_bounds__(kHemiBlock, 3) hemi_pipe_kernel(HemiArgs a, in
       rescue |= unsigned(sample_one<kMethodCapExt, PDF, true>(X[k], Y[k], Z[k], 1.f, 1.f, U1[k], U2[k], MX[k],
                                                               MY[k], MZ[k], P[k]))
                 << k;
-    if (rescue) {  // rare: ill-conditioned samples redone in double-float
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (rescue & (1u << k)) {
-          const float4 r = sample_one_precise<PDF, true>(X[k], Y[k], Z[k], 1.f, 1.f, U1[k], U2[k]);
-          MX[k] = r.x;
-          MY[k] = r.y;
-          MZ[k] = r.z;
-          P[k] = r.w;
-        }
+    if (active) {
+      st_stream(a.mx + e, *reinterpret_cast<float4*>(MX));
+      st_stream(a.my + e, *reinterpret_cast<float4*>(MY));
+      st_stream(a.mz + e, *reinterpret_cast<float4*>(MZ));
+      if constexpr (PDF) st_stream(a.pdf + e, *reinterpret_cast<float4*>(P));
+    } else {
+      rescue = 0;
     }
-    st_stream(a.mx + e, *reinterpret_cast<float4*>(MX));
-    st_stream(a.my + e, *reinterpret_cast<float4*>(MY));
-    st_stream(a.mz + e, *reinterpret_cast<float4*>(MZ));
-    if constexpr (PDF) st_stream(a.pdf + e, *reinterpret_cast<float4*>(P));
+    if (__any_sync(0xffffffffu, rescue != 0)) {  // rare
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float v[5] = {X[k], Y[k], Z[k], U1[k], U2[k]};
+        rescue_push(rq, pending, (rescue >> k) & 1u, v, e + k);
+        rescue_drain(rq, pending, false, redo);
+      }
+    }
   }
+  rescue_drain(rq, pending, true, redo);
   cp_async_wait<0>();
 }
 
@@ -126,7 +141,8 @@ int launch_hemi(const HemiArgs& a, int64_t n, bool vec, cudaStream_t s) {
   int64_t done = 0;
   if (vec && n / 4 > 0) {
     const int64_t n4 = n / 4;
-    constexpr size_t smem = size_t(2) * hemi_streams_in<PHILOX>() * kHemiBlock * 16;
+    constexpr size_t smem =
+        size_t(2) * hemi_streams_in<PHILOX>() * kHemiBlock * 16 + (kHemiBlock / 32) * sizeof(RescueQueue<5>);
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
       if (cudaFuncSetAttribute(hemi_pipe_kernel<PHILOX, PDF>, cudaFuncAttributeMaxDynamicSharedMemorySize,

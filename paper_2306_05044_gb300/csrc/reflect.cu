@@ -12,11 +12,12 @@
 //   PDF   = |wi| |v|^4 / (2 pi ax ay L (1 + i.z) |h|^4)
 //   (D(wm) = |v|^4 / (pi ax ay |h|^4) and G1 / (4 cos theta_i) = |wi| / (2 L (1 + i.z))).
 // Samples whose half vector is ill-conditioned get it recomputed in
-// double-float, as in vndf_sample.
+// double-float, as in vndf_sample (queued per warp and redone 32 at a time).
 #include <cuda_runtime.h>
 
 #include "common.cuh"
 #include "philox.cuh"
+#include "rescue.cuh"
 #include "staging.cuh"
 #include "vndf_math.cuh"
 
@@ -43,16 +44,26 @@ struct Reflected {
   float ox, oy, oz, pdf, weight;
 };
 
+// One reflected sample.  With PRECISE_H the half vector comes from the
+// double-float path; otherwise from FP32, and *bad reports whether it was
+// ill-conditioned (the caller then redoes the sample with PRECISE_H).
+template <bool PRECISE_H>
 __device__ __forceinline__ Reflected reflect_one(float wx, float wy, float wz, float ax, float ay, float u1,
-                                                 float u2, float f0) {
+                                                 float u2, float f0, bool* bad) {
   const bool ok = in_domain(wx, wy, wz, ax, ay);
   const float sx = ax * wx, sy = ay * wy;
   const float l2 = fmaf(sx, sx, fmaf(sy, sy, wz * wz));
   const float rl = rsqrtf(l2);
   const Stretched i{sx * rl, sy * rl, wz * rl};
   float hx, hy, hz, a;
-  cap_half_vector(i, u1, u2, hx, hy, hz, a);
-  {
+  if constexpr (PRECISE_H) {
+    const float4 p = half_vector_precise(wx, wy, wz, ax, ay, u1, u2);
+    hx = p.x;
+    hy = p.y;
+    hz = p.z;
+    a = p.w;
+  } else {
+    cap_half_vector(i, u1, u2, hx, hy, hz, a);
     // the condition check of sample_one<cap, PDF, PRECISE>
     const float cx = fabsf(hx - i.x) + fabsf(i.x), cy = fabsf(hy - i.y) + fabsf(i.y);
     const float vx = ax * hx, vy = ay * hy;
@@ -60,14 +71,7 @@ __device__ __forceinline__ Reflected reflect_one(float wx, float wy, float wz, f
     const float k2 = fmaf(ax * cx, ax * cx, fmaf(ay * cy, ay * cy, hz * hz));
     const float kh2 = fmaf(cx, cx, fmaf(cy, cy, hz * hz));
     const float hh = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
-    const bool bad = (k2 > kRescueKappa * kRescueKappa * vv) | (kh2 > kRescueKappa * kRescueKappa * hh);
-    if (ok && bad) {
-      const float4 p = half_vector_precise(wx, wy, wz, ax, ay, u1, u2);
-      hx = p.x;
-      hy = p.y;
-      hz = p.z;
-      a = p.w;
-    }
+    *bad = ok & ((k2 > kRescueKappa * kRescueKappa * vv) | (kh2 > kRescueKappa * kRescueKappa * hh));
   }
   const float vx = ax * hx, vy = ay * hy, vz = hz;
   const float vv = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
@@ -114,18 +118,31 @@ __device__ __forceinline__ void refl_stage(const ReflArgs& a, int64_t e, float4*
   }
 }
 
-// Four samples per thread per grid-stride step, inputs staged two steps deep.
+// Four samples per thread per grid-stride step, inputs staged two steps deep;
+// ill-conditioned samples are queued per warp and redone 32 at a time (rescue.cuh).
 template <bool PHILOX, bool ISO>
 __global__ void __launch_bounds__(kReflBlock, 3) reflect_pipe_kernel(ReflArgs a, int64_t n4) {
   constexpr int NS = streams_in<PHILOX, ISO>();
-  extern __shared__ float4 smem_r[];  // [2][NS][kReflBlock]
+  extern __shared__ float4 smem_r[];  // [2][NS][kReflBlock], then one rescue queue per warp
+  RescueQueue<7>& rq = reinterpret_cast<RescueQueue<7>*>(smem_r + 2 * NS * kReflBlock)[threadIdx.x >> 5];
+  int pending = 0;  // warp-uniform
   const int64_t stride = int64_t(gridDim.x) * kReflBlock;
   const int64_t q0 = int64_t(blockIdx.x) * kReflBlock + threadIdx.x;
+  const int64_t w0 = q0 - (threadIdx.x & 31);
   float4* mine = smem_r + threadIdx.x;
   if (q0 < n4) refl_stage<PHILOX, ISO>(a, 4 * q0, mine);
   cp_async_commit();
+  auto redo = [&](const float (&v)[7], int64_t i) {
+    const Reflected r = reflect_one<true>(v[0], v[1], v[2], v[3], v[4], v[5], v[6], a.f0, nullptr);
+    a.ox[i] = r.ox;
+    a.oy[i] = r.oy;
+    a.oz[i] = r.oz;
+    if (a.pdf) a.pdf[i] = r.pdf;
+    if (a.weight) a.weight[i] = r.weight;
+  };
   int slot = 0;
-  for (int64_t q = q0; q < n4; q += stride) {
+  for (int64_t q = q0, qw = w0; qw < n4; q += stride, qw += stride) {
+    const bool active = q < n4;
     if (q + stride < n4) refl_stage<PHILOX, ISO>(a, 4 * (q + stride), mine + (slot ^ 1) * NS * kReflBlock);
     cp_async_commit();
     cp_async_wait<1>();
@@ -145,21 +162,37 @@ __global__ void __launch_bounds__(kReflBlock, 3) reflect_pipe_kernel(ReflArgs a,
       *reinterpret_cast<float4*>(U2) = cur[(ISO ? 5 : 6) * kReflBlock];
     }
     float OX[4], OY[4], OZ[4], P[4], Wt[4];
+    unsigned rescue = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const Reflected r = reflect_one(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], a.f0);
+      bool bad;
+      const Reflected r = reflect_one<false>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], a.f0, &bad);
+      rescue |= unsigned(bad) << k;
       OX[k] = r.ox;
       OY[k] = r.oy;
       OZ[k] = r.oz;
       P[k] = r.pdf;
       Wt[k] = r.weight;
     }
-    st_stream(a.ox + e, *reinterpret_cast<float4*>(OX));
-    st_stream(a.oy + e, *reinterpret_cast<float4*>(OY));
-    st_stream(a.oz + e, *reinterpret_cast<float4*>(OZ));
-    if (a.pdf) st_stream(a.pdf + e, *reinterpret_cast<float4*>(P));
-    if (a.weight) st_stream(a.weight + e, *reinterpret_cast<float4*>(Wt));
+    if (active) {
+      st_stream(a.ox + e, *reinterpret_cast<float4*>(OX));
+      st_stream(a.oy + e, *reinterpret_cast<float4*>(OY));
+      st_stream(a.oz + e, *reinterpret_cast<float4*>(OZ));
+      if (a.pdf) st_stream(a.pdf + e, *reinterpret_cast<float4*>(P));
+      if (a.weight) st_stream(a.weight + e, *reinterpret_cast<float4*>(Wt));
+    } else {
+      rescue = 0;
+    }
+    if (__any_sync(0xffffffffu, rescue != 0)) {  // rare
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float v[7] = {X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k]};
+        rescue_push(rq, pending, (rescue >> k) & 1u, v, e + k);
+        rescue_drain(rq, pending, false, redo);
+      }
+    }
   }
+  rescue_drain(rq, pending, true, redo);
   cp_async_wait<0>();
 }
 
@@ -176,7 +209,9 @@ __global__ void __launch_bounds__(kReflBlock) reflect_scalar_kernel(ReflArgs a, 
       u1 = a.u1[e];
       u2 = a.u2[e];
     }
-    const Reflected r = reflect_one(a.wx[e], a.wy[e], a.wz[e], ax, ay, u1, u2, a.f0);
+    bool bad;
+    Reflected r = reflect_one<false>(a.wx[e], a.wy[e], a.wz[e], ax, ay, u1, u2, a.f0, &bad);
+    if (bad) r = reflect_one<true>(a.wx[e], a.wy[e], a.wz[e], ax, ay, u1, u2, a.f0, nullptr);
     a.ox[e] = r.ox;
     a.oy[e] = r.oy;
     a.oz[e] = r.oz;
@@ -190,7 +225,8 @@ int launch_reflect(const ReflArgs& a, int64_t n, bool vec, cudaStream_t s) {
   int64_t done = 0;
   if (vec && n / 4 > 0) {
     const int64_t n4 = n / 4;
-    constexpr size_t smem = size_t(2) * streams_in<PHILOX, ISO>() * kReflBlock * 16;
+    constexpr size_t smem =
+        size_t(2) * streams_in<PHILOX, ISO>() * kReflBlock * 16 + (kReflBlock / 32) * sizeof(RescueQueue<7>);
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
       if (cudaFuncSetAttribute(reflect_pipe_kernel<PHILOX, ISO>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -9,6 +9,7 @@
 #include "common.cuh"
 #include "staging.cuh"
 #include "philox.cuh"
+#include "rescue.cuh"
 #include "vndf_math.cuh"
 
 // Launch shape of the streaming sampler (compile-time, so the shape can be
@@ -131,9 +132,12 @@ template <int METHOD, bool PHILOX, bool ISO, bool PDF>
 __global__ void __launch_bounds__(kSampleBlock, VNDF_SAMPLE_MIN_BLOCKS) sample_pipe_kernel(SampleArgs a, int64_t n4) {
   constexpr int S = VNDF_SAMPLE_STAGES;
   constexpr int NS = streams_in<PHILOX, ISO>();
-  extern __shared__ float4 smem[];  // [S][NS][kSampleBlock]
+  extern __shared__ float4 smem[];  // [S][NS][kSampleBlock], then one rescue queue per warp
+  RescueQueue<7>& rq = reinterpret_cast<RescueQueue<7>*>(smem + S * NS * kSampleBlock)[threadIdx.x >> 5];
+  int pending = 0;  // warp-uniform
   const int64_t stride = int64_t(gridDim.x) * kSampleBlock;
   const int64_t q0 = int64_t(blockIdx.x) * kSampleBlock + threadIdx.x;
+  const int64_t w0 = q0 - (threadIdx.x & 31);  // first group of this warp: the loop runs warp-uniformly
   float4* mine = smem + threadIdx.x;
 #pragma unroll
   for (int st = 0; st < S - 1; ++st) {
@@ -141,8 +145,16 @@ __global__ void __launch_bounds__(kSampleBlock, VNDF_SAMPLE_MIN_BLOCKS) sample_p
     if (q < n4) stage_group<PHILOX, ISO>(a, 4 * q, mine + st * NS * kSampleBlock);
     cp_async_commit();  // one group per stage, possibly empty, keeps the count uniform
   }
+  auto redo = [&](const float (&v)[7], int64_t i) {
+    const float4 r = sample_one_precise<PDF, METHOD == kMethodCapExt>(v[0], v[1], v[2], v[3], v[4], v[5], v[6]);
+    a.mx[i] = r.x;
+    a.my[i] = r.y;
+    a.mz[i] = r.z;
+    if constexpr (PDF) a.pdf[i] = r.w;
+  };
   int slot = 0;
-  for (int64_t q = q0; q < n4; q += stride) {
+  for (int64_t q = q0, qw = w0; qw < n4; q += stride, qw += stride) {
+    const bool active = q < n4;  // false only for the tail lanes of the last step
     const int64_t qn = q + (S - 1) * stride;
     if (qn < n4) stage_group<PHILOX, ISO>(a, 4 * qn, mine + ((slot + S - 1) % S) * NS * kSampleBlock);
     cp_async_commit();
@@ -169,25 +181,26 @@ __global__ void __launch_bounds__(kSampleBlock, VNDF_SAMPLE_MIN_BLOCKS) sample_p
       rescue |= unsigned(sample_one<METHOD, PDF, true>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], MX[k], MY[k],
                                                        MZ[k], P[k]))
                 << k;
+    if (active) {
+      st_stream(a.mx + e, *reinterpret_cast<float4*>(MX));
+      st_stream(a.my + e, *reinterpret_cast<float4*>(MY));
+      st_stream(a.mz + e, *reinterpret_cast<float4*>(MZ));
+      if constexpr (PDF) st_stream(a.pdf + e, *reinterpret_cast<float4*>(P));
+    }
     if constexpr (is_cap<METHOD>()) {
-      if (rescue) {  // rare: ill-conditioned samples redone in double-float
+      // rare: ill-conditioned samples are queued and redone in double-float, 32 at a time
+      if (!active) rescue = 0;
+      if (__any_sync(0xffffffffu, rescue != 0)) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (rescue & (1u << k)) {
-            const float4 r =
-                sample_one_precise<PDF, METHOD == kMethodCapExt>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k]);
-            MX[k] = r.x;
-            MY[k] = r.y;
-            MZ[k] = r.z;
-            P[k] = r.w;
-          }
+        for (int k = 0; k < 4; ++k) {
+          const float v[7] = {X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k]};
+          rescue_push(rq, pending, (rescue >> k) & 1u, v, e + k);
+          rescue_drain(rq, pending, false, redo);
+        }
       }
     }
-    st_stream(a.mx + e, *reinterpret_cast<float4*>(MX));
-    st_stream(a.my + e, *reinterpret_cast<float4*>(MY));
-    st_stream(a.mz + e, *reinterpret_cast<float4*>(MZ));
-    if constexpr (PDF) st_stream(a.pdf + e, *reinterpret_cast<float4*>(P));
   }
+  if constexpr (is_cap<METHOD>()) rescue_drain(rq, pending, true, redo);
   cp_async_wait<0>();
 }
 
@@ -228,7 +241,8 @@ int launch_sample(const SampleArgs& a, int64_t n, bool vec, cudaStream_t s) {
     if (n4 > 0) {
       const unsigned grid = grid_for(n4, kSampleBlock, 2048 / kSampleBlock, VNDF_SAMPLE_WAVES);
       if constexpr (VNDF_SAMPLE_STAGES >= 2) {
-        constexpr size_t smem = size_t(VNDF_SAMPLE_STAGES) * streams_in<PHILOX, ISO>() * kSampleBlock * 16;
+        constexpr size_t smem = size_t(VNDF_SAMPLE_STAGES) * streams_in<PHILOX, ISO>() * kSampleBlock * 16 +
+                                (kSampleBlock / 32) * sizeof(RescueQueue<7>);
         static bool attr_set = false;  // per instantiation; setting it twice is harmless
         if (!attr_set) {
           if (cudaFuncSetAttribute(sample_pipe_kernel<METHOD, PHILOX, ISO, PDF>,
