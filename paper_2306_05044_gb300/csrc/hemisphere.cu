@@ -15,6 +15,11 @@
 #include "staging.cuh"
 #include "vndf_math.cuh"
 
+// 1: ill-conditioned samples queued per warp and redone 32 at a time (rescue.cuh); 0: in place.
+#ifndef VNDF_RESCUE_BATCHED
+#define VNDF_RESCUE_BATCHED 1
+#endif
+
 namespace vndf {
 
 constexpr int kHemiBlock = 256;
@@ -55,7 +60,7 @@ template <bool PHILOX, bool PDF>
 __global__ void __launch_bounds__(kHemiBlock, 3) hemi_pipe_kernel(HemiArgs a, int64_t n4) {
   constexpr int NS = hemi_streams_in<PHILOX>();
   extern __shared__ float4 smem_h[];  // [2][NS][kHemiBlock], then one rescue queue per warp
-  RescueQueue<5>& rq = reinterpret_cast<RescueQueue<5>*>(smem_h + 2 * NS * kHemiBlock)[threadIdx.x >> 5];
+  RescueQueue& rq = reinterpret_cast<RescueQueue*>(smem_h + 2 * NS * kHemiBlock)[threadIdx.x >> 5];
   int pending = 0;  // warp-uniform
   const int64_t stride = int64_t(gridDim.x) * kHemiBlock;
   const int64_t q0 = int64_t(blockIdx.x) * kHemiBlock + threadIdx.x;
@@ -63,16 +68,24 @@ __global__ void __launch_bounds__(kHemiBlock, 3) hemi_pipe_kernel(HemiArgs a, in
   float4* mine = smem_h + threadIdx.x;
   if (q0 < n4) hemi_stage<PHILOX>(a, 4 * q0, mine);
   cp_async_commit();
-  auto redo = [&](const float (&v)[5], int64_t i) {
-    const float4 r = sample_one_precise<PDF, true>(v[0], v[1], v[2], 1.f, 1.f, v[3], v[4]);
+  auto redo = [&](int64_t i) {  // sample i recomputed from its inputs in global memory
+    float u1, u2;
+    if constexpr (PHILOX) {
+      uniforms1(a.rng, uint64_t(i), u1, u2);
+    } else {
+      u1 = a.u1[i];
+      u2 = a.u2[i];
+    }
+    const float4 r = sample_one_precise<PDF, true>(a.wx[i], a.wy[i], a.wz[i], 1.f, 1.f, u1, u2);
     a.mx[i] = r.x;
     a.my[i] = r.y;
     a.mz[i] = r.z;
     if constexpr (PDF) a.pdf[i] = r.w;
   };
+  constexpr bool kBatched = VNDF_RESCUE_BATCHED;
   int slot = 0;
-  for (int64_t q = q0, qw = w0; qw < n4; q += stride, qw += stride) {
-    const bool active = q < n4;
+  for (int64_t q = q0, qw = w0; kBatched ? qw < n4 : q < n4; q += stride, qw += stride) {
+    const bool active = !kBatched || q < n4;
     if (q + stride < n4) hemi_stage<PHILOX>(a, 4 * (q + stride), mine + (slot ^ 1) * NS * kHemiBlock);
     cp_async_commit();
     cp_async_wait<1>();
@@ -96,6 +109,19 @@ __global__ void __launch_bounds__(kHemiBlock, 3) hemi_pipe_kernel(HemiArgs a, in
       rescue |= unsigned(sample_one<kMethodCapExt, PDF, true>(X[k], Y[k], Z[k], 1.f, 1.f, U1[k], U2[k], MX[k],
                                                               MY[k], MZ[k], P[k]))
                 << k;
+    if constexpr (!kBatched) {
+      if (rescue) {  // rare: redone in place
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (rescue & (1u << k)) {
+            const float4 r = sample_one_precise<PDF, true>(X[k], Y[k], Z[k], 1.f, 1.f, U1[k], U2[k]);
+            MX[k] = r.x;
+            MY[k] = r.y;
+            MZ[k] = r.z;
+            P[k] = r.w;
+          }
+      }
+    }
     if (active) {
       st_stream(a.mx + e, *reinterpret_cast<float4*>(MX));
       st_stream(a.my + e, *reinterpret_cast<float4*>(MY));
@@ -104,16 +130,13 @@ __global__ void __launch_bounds__(kHemiBlock, 3) hemi_pipe_kernel(HemiArgs a, in
     } else {
       rescue = 0;
     }
-    if (__any_sync(0xffffffffu, rescue != 0)) {  // rare
+    if (kBatched && __any_sync(0xffffffffu, rescue != 0)) {  // rare
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float v[5] = {X[k], Y[k], Z[k], U1[k], U2[k]};
-        rescue_push(rq, pending, (rescue >> k) & 1u, v, e + k);
-        rescue_drain(rq, pending, false, redo);
-      }
+      for (int k = 0; k < 4; ++k) rescue_push(rq, pending, (rescue >> k) & 1u, e + k);
+      rescue_drain(rq, pending, false, redo);
     }
   }
-  rescue_drain(rq, pending, true, redo);
+  if constexpr (kBatched) rescue_drain(rq, pending, true, redo);
   cp_async_wait<0>();
 }
 
@@ -142,7 +165,7 @@ int launch_hemi(const HemiArgs& a, int64_t n, bool vec, cudaStream_t s) {
   if (vec && n / 4 > 0) {
     const int64_t n4 = n / 4;
     constexpr size_t smem =
-        size_t(2) * hemi_streams_in<PHILOX>() * kHemiBlock * 16 + (kHemiBlock / 32) * sizeof(RescueQueue<5>);
+        size_t(2) * hemi_streams_in<PHILOX>() * kHemiBlock * 16 + (kHemiBlock / 32) * sizeof(RescueQueue);
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
       if (cudaFuncSetAttribute(hemi_pipe_kernel<PHILOX, PDF>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -21,6 +21,11 @@
 #include "staging.cuh"
 #include "vndf_math.cuh"
 
+// 1: ill-conditioned samples queued per warp and redone 32 at a time (rescue.cuh); 0: in place.
+#ifndef VNDF_RESCUE_BATCHED
+#define VNDF_RESCUE_BATCHED 1
+#endif
+
 namespace vndf {
 
 constexpr int kReflBlock = 256;
@@ -124,7 +129,7 @@ template <bool PHILOX, bool ISO>
 __global__ void __launch_bounds__(kReflBlock, 3) reflect_pipe_kernel(ReflArgs a, int64_t n4) {
   constexpr int NS = streams_in<PHILOX, ISO>();
   extern __shared__ float4 smem_r[];  // [2][NS][kReflBlock], then one rescue queue per warp
-  RescueQueue<7>& rq = reinterpret_cast<RescueQueue<7>*>(smem_r + 2 * NS * kReflBlock)[threadIdx.x >> 5];
+  RescueQueue& rq = reinterpret_cast<RescueQueue*>(smem_r + 2 * NS * kReflBlock)[threadIdx.x >> 5];
   int pending = 0;  // warp-uniform
   const int64_t stride = int64_t(gridDim.x) * kReflBlock;
   const int64_t q0 = int64_t(blockIdx.x) * kReflBlock + threadIdx.x;
@@ -132,17 +137,26 @@ __global__ void __launch_bounds__(kReflBlock, 3) reflect_pipe_kernel(ReflArgs a,
   float4* mine = smem_r + threadIdx.x;
   if (q0 < n4) refl_stage<PHILOX, ISO>(a, 4 * q0, mine);
   cp_async_commit();
-  auto redo = [&](const float (&v)[7], int64_t i) {
-    const Reflected r = reflect_one<true>(v[0], v[1], v[2], v[3], v[4], v[5], v[6], a.f0, nullptr);
+  auto redo = [&](int64_t i) {  // sample i recomputed from its inputs in global memory
+    const float ax = a.ax[i], ay = ISO ? ax : a.ay[i];
+    float u1, u2;
+    if constexpr (PHILOX) {
+      uniforms1(a.rng, uint64_t(i), u1, u2);
+    } else {
+      u1 = a.u1[i];
+      u2 = a.u2[i];
+    }
+    const Reflected r = reflect_one<true>(a.wx[i], a.wy[i], a.wz[i], ax, ay, u1, u2, a.f0, nullptr);
     a.ox[i] = r.ox;
     a.oy[i] = r.oy;
     a.oz[i] = r.oz;
     if (a.pdf) a.pdf[i] = r.pdf;
     if (a.weight) a.weight[i] = r.weight;
   };
+  constexpr bool kBatched = VNDF_RESCUE_BATCHED;
   int slot = 0;
-  for (int64_t q = q0, qw = w0; qw < n4; q += stride, qw += stride) {
-    const bool active = q < n4;
+  for (int64_t q = q0, qw = w0; kBatched ? qw < n4 : q < n4; q += stride, qw += stride) {
+    const bool active = !kBatched || q < n4;
     if (q + stride < n4) refl_stage<PHILOX, ISO>(a, 4 * (q + stride), mine + (slot ^ 1) * NS * kReflBlock);
     cp_async_commit();
     cp_async_wait<1>();
@@ -166,7 +180,8 @@ __global__ void __launch_bounds__(kReflBlock, 3) reflect_pipe_kernel(ReflArgs a,
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       bool bad;
-      const Reflected r = reflect_one<false>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], a.f0, &bad);
+      Reflected r = reflect_one<false>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], a.f0, &bad);
+      if (!kBatched && bad) r = reflect_one<true>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], a.f0, nullptr);
       rescue |= unsigned(bad) << k;
       OX[k] = r.ox;
       OY[k] = r.oy;
@@ -183,16 +198,13 @@ __global__ void __launch_bounds__(kReflBlock, 3) reflect_pipe_kernel(ReflArgs a,
     } else {
       rescue = 0;
     }
-    if (__any_sync(0xffffffffu, rescue != 0)) {  // rare
+    if (kBatched && __any_sync(0xffffffffu, rescue != 0)) {  // rare
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float v[7] = {X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k]};
-        rescue_push(rq, pending, (rescue >> k) & 1u, v, e + k);
-        rescue_drain(rq, pending, false, redo);
-      }
+      for (int k = 0; k < 4; ++k) rescue_push(rq, pending, (rescue >> k) & 1u, e + k);
+      rescue_drain(rq, pending, false, redo);
     }
   }
-  rescue_drain(rq, pending, true, redo);
+  if constexpr (kBatched) rescue_drain(rq, pending, true, redo);
   cp_async_wait<0>();
 }
 
@@ -226,7 +238,7 @@ int launch_reflect(const ReflArgs& a, int64_t n, bool vec, cudaStream_t s) {
   if (vec && n / 4 > 0) {
     const int64_t n4 = n / 4;
     constexpr size_t smem =
-        size_t(2) * streams_in<PHILOX, ISO>() * kReflBlock * 16 + (kReflBlock / 32) * sizeof(RescueQueue<7>);
+        size_t(2) * streams_in<PHILOX, ISO>() * kReflBlock * 16 + (kReflBlock / 32) * sizeof(RescueQueue);
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
       if (cudaFuncSetAttribute(reflect_pipe_kernel<PHILOX, ISO>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -29,6 +29,11 @@
 #ifndef VNDF_SAMPLE_STAGES
 #define VNDF_SAMPLE_STAGES 2
 #endif
+// Ill-conditioned samples: 1 = queued per warp and redone 32 at a time
+// (rescue.cuh); 0 = each redone in place by its own lane.
+#ifndef VNDF_RESCUE_BATCHED
+#define VNDF_RESCUE_BATCHED 1
+#endif
 
 namespace vndf {
 
@@ -133,7 +138,7 @@ __global__ void __launch_bounds__(kSampleBlock, VNDF_SAMPLE_MIN_BLOCKS) sample_p
   constexpr int S = VNDF_SAMPLE_STAGES;
   constexpr int NS = streams_in<PHILOX, ISO>();
   extern __shared__ float4 smem[];  // [S][NS][kSampleBlock], then one rescue queue per warp
-  RescueQueue<7>& rq = reinterpret_cast<RescueQueue<7>*>(smem + S * NS * kSampleBlock)[threadIdx.x >> 5];
+  RescueQueue& rq = reinterpret_cast<RescueQueue*>(smem + S * NS * kSampleBlock)[threadIdx.x >> 5];
   int pending = 0;  // warp-uniform
   const int64_t stride = int64_t(gridDim.x) * kSampleBlock;
   const int64_t q0 = int64_t(blockIdx.x) * kSampleBlock + threadIdx.x;
@@ -145,16 +150,26 @@ __global__ void __launch_bounds__(kSampleBlock, VNDF_SAMPLE_MIN_BLOCKS) sample_p
     if (q < n4) stage_group<PHILOX, ISO>(a, 4 * q, mine + st * NS * kSampleBlock);
     cp_async_commit();  // one group per stage, possibly empty, keeps the count uniform
   }
-  auto redo = [&](const float (&v)[7], int64_t i) {
-    const float4 r = sample_one_precise<PDF, METHOD == kMethodCapExt>(v[0], v[1], v[2], v[3], v[4], v[5], v[6]);
+  auto redo = [&](int64_t i) {  // sample i recomputed from its inputs in global memory
+    const float ax = a.ax[i], ay = ISO ? ax : a.ay[i];
+    float u1, u2;
+    if constexpr (PHILOX) {
+      uniforms1(a.rng, uint64_t(i), u1, u2);
+    } else {
+      u1 = a.u1[i];
+      u2 = a.u2[i];
+    }
+    const float4 r = sample_one_precise<PDF, METHOD == kMethodCapExt>(a.wx[i], a.wy[i], a.wz[i], ax, ay, u1, u2);
     a.mx[i] = r.x;
     a.my[i] = r.y;
     a.mz[i] = r.z;
     if constexpr (PDF) a.pdf[i] = r.w;
   };
+  constexpr bool kBatched = is_cap<METHOD>() && VNDF_RESCUE_BATCHED;
   int slot = 0;
-  for (int64_t q = q0, qw = w0; qw < n4; q += stride, qw += stride) {
-    const bool active = q < n4;  // false only for the tail lanes of the last step
+  // batched: the loop runs warp-uniformly (ballots need every lane); otherwise per thread
+  for (int64_t q = q0, qw = w0; kBatched ? qw < n4 : q < n4; q += stride, qw += stride) {
+    const bool active = !kBatched || q < n4;  // false only for the tail lanes of the last step
     const int64_t qn = q + (S - 1) * stride;
     if (qn < n4) stage_group<PHILOX, ISO>(a, 4 * qn, mine + ((slot + S - 1) % S) * NS * kSampleBlock);
     cp_async_commit();
@@ -181,26 +196,37 @@ __global__ void __launch_bounds__(kSampleBlock, VNDF_SAMPLE_MIN_BLOCKS) sample_p
       rescue |= unsigned(sample_one<METHOD, PDF, true>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], MX[k], MY[k],
                                                        MZ[k], P[k]))
                 << k;
+    if constexpr (is_cap<METHOD>() && !kBatched) {
+      if (rescue) {  // rare: ill-conditioned samples redone in double-float, in place
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (rescue & (1u << k)) {
+            const float4 r =
+                sample_one_precise<PDF, METHOD == kMethodCapExt>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k]);
+            MX[k] = r.x;
+            MY[k] = r.y;
+            MZ[k] = r.z;
+            P[k] = r.w;
+          }
+      }
+    }
     if (active) {
       st_stream(a.mx + e, *reinterpret_cast<float4*>(MX));
       st_stream(a.my + e, *reinterpret_cast<float4*>(MY));
       st_stream(a.mz + e, *reinterpret_cast<float4*>(MZ));
       if constexpr (PDF) st_stream(a.pdf + e, *reinterpret_cast<float4*>(P));
     }
-    if constexpr (is_cap<METHOD>()) {
+    if constexpr (kBatched) {
       // rare: ill-conditioned samples are queued and redone in double-float, 32 at a time
       if (!active) rescue = 0;
       if (__any_sync(0xffffffffu, rescue != 0)) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float v[7] = {X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k]};
-          rescue_push(rq, pending, (rescue >> k) & 1u, v, e + k);
-          rescue_drain(rq, pending, false, redo);
-        }
+        for (int k = 0; k < 4; ++k) rescue_push(rq, pending, (rescue >> k) & 1u, e + k);
+        rescue_drain(rq, pending, false, redo);
       }
     }
   }
-  if constexpr (is_cap<METHOD>()) rescue_drain(rq, pending, true, redo);
+  if constexpr (kBatched) rescue_drain(rq, pending, true, redo);
   cp_async_wait<0>();
 }
 
@@ -242,7 +268,7 @@ int launch_sample(const SampleArgs& a, int64_t n, bool vec, cudaStream_t s) {
       const unsigned grid = grid_for(n4, kSampleBlock, 2048 / kSampleBlock, VNDF_SAMPLE_WAVES);
       if constexpr (VNDF_SAMPLE_STAGES >= 2) {
         constexpr size_t smem = size_t(VNDF_SAMPLE_STAGES) * streams_in<PHILOX, ISO>() * kSampleBlock * 16 +
-                                (kSampleBlock / 32) * sizeof(RescueQueue<7>);
+                                (kSampleBlock / 32) * sizeof(RescueQueue);
         static bool attr_set = false;  // per instantiation; setting it twice is harmless
         if (!attr_set) {
           if (cudaFuncSetAttribute(sample_pipe_kernel<METHOD, PHILOX, ISO, PDF>,
