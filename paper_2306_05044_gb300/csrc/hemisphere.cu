@@ -19,6 +19,10 @@
 #ifndef VNDF_RESCUE_BATCHED
 #define VNDF_RESCUE_BATCHED 1
 #endif
+// Grid of the streaming kernel: at most this many waves of 8 CTAs per SM.
+#ifndef VNDF_SAMPLE_WAVES
+#define VNDF_SAMPLE_WAVES 4
+#endif
 
 namespace vndf {
 
@@ -173,7 +177,7 @@ int launch_hemi(const HemiArgs& a, int64_t n, bool vec, cudaStream_t s) {
         return VNDF_ERR_CUDA;
       attr_set = true;
     }
-    hemi_pipe_kernel<PHILOX, PDF><<<grid_for(n4, kHemiBlock, 8, 32), kHemiBlock, smem, s>>>(a, n4);
+    hemi_pipe_kernel<PHILOX, PDF><<<grid_for(n4, kHemiBlock, 8, VNDF_SAMPLE_WAVES), kHemiBlock, smem, s>>>(a, n4);
     done = 4 * n4;
   }
   if (done < n)

@@ -25,6 +25,10 @@
 #ifndef VNDF_RESCUE_BATCHED
 #define VNDF_RESCUE_BATCHED 1
 #endif
+// Grid of the streaming kernel: at most this many waves of 8 CTAs per SM.
+#ifndef VNDF_SAMPLE_WAVES
+#define VNDF_SAMPLE_WAVES 4
+#endif
 
 namespace vndf {
 
@@ -246,7 +250,7 @@ int launch_reflect(const ReflArgs& a, int64_t n, bool vec, cudaStream_t s) {
         return VNDF_ERR_CUDA;
       attr_set = true;
     }
-    reflect_pipe_kernel<PHILOX, ISO><<<grid_for(n4, kReflBlock, 8, 32), kReflBlock, smem, s>>>(a, n4);
+    reflect_pipe_kernel<PHILOX, ISO><<<grid_for(n4, kReflBlock, 8, VNDF_SAMPLE_WAVES), kReflBlock, smem, s>>>(a, n4);
     done = 4 * n4;
   }
   if (done < n)

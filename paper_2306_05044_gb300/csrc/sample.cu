@@ -21,7 +21,7 @@
 #define VNDF_SAMPLE_MIN_BLOCKS 3
 #endif
 #ifndef VNDF_SAMPLE_WAVES
-#define VNDF_SAMPLE_WAVES 32
+#define VNDF_SAMPLE_WAVES 4
 #endif
 #ifndef VNDF_SAMPLE_PREFETCH
 #define VNDF_SAMPLE_PREFETCH 1
