@@ -39,7 +39,8 @@ BYTES_PER_SAMPLE = 36  # in: wi xyz + alpha xy (20 B); out: wm xyz + pdf (16 B)
 FALLBACK_HBM_GBS = 6800.0
 CSRC = os.path.join(ROOT, "paper_2306_05044_gb300", "csrc")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "vndf_sample_cap_anisotropic_stream.md")
-ISSUE_FILE = os.path.join(ROOT, "profiles", "compute_kernels_issue.md")
+ISSUE_FILES = (os.path.join(ROOT, "profiles", "compute_kernels_issue.md"),
+               os.path.join(ROOT, "profiles", "vndf_sample_extended_sphere_and_hemisphere_stream.md"))
 LANES_PER_SM = 4 * 32  # 4 schedulers x 32 lanes issue one instruction each per clock
 
 
@@ -67,15 +68,18 @@ def parse_args():
 
 # ----------------------------------------------------------------------------- helpers
 KERNEL_FILES = {
-    "stream": ("sample.cu", "staging.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
+    "stream": ("sample.cu", "rescue.cuh", "staging.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
     "microbench_cap": ("microbench.cu", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
     "microbench_cap_strict": ("microbench.cu", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
     "microbench_polar": ("microbench.cu", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
     "loss_backward": ("backward.cu", "vndf_adjoint.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
     "albedo": ("albedo.cu", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
     "fit": ("fit.cu", "vndf_adjoint.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
-    "reflection": ("reflect.cu", "staging.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
-    "hemisphere": ("hemisphere.cu", "staging.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
+    "reflection": ("reflect.cu", "rescue.cuh", "staging.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh",
+                   "common.cuh"),
+    "hemisphere": ("hemisphere.cu", "rescue.cuh", "staging.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh",
+                   "common.cuh"),
+    "extended": ("sample.cu", "rescue.cuh", "staging.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
 }
 
 
@@ -118,7 +122,10 @@ def issue_roofline(kernel, samples, ms, clock_mhz):
     ncu summary (null when the kernel sources changed since)."""
     import torch
     try:
-        per = float(_profile_values(ISSUE_FILE, kernel)[f"tinst_per_sample.{kernel}"])
+        vals = {}
+        for path in ISSUE_FILES:
+            vals.update(_profile_values(path, kernel))
+        per = float(vals[f"tinst_per_sample.{kernel}"])
     except (KeyError, ValueError):
         return {"bound": "alu", "achieved": None, "peak": None, "frac": None, "unit": "Tinst/s",
                 "note": "instruction count not measured for the current kernel sources"}
@@ -397,7 +404,7 @@ def run_ours(args, rank, world):
         result["gpu_launches_reflection"] = steps
 
     if not args.no_extended:
-        result["extended"] = extended_legs(vndf, dev, base, n, outs, timed, steps, warm, world, peak)
+        result["extended"] = extended_legs(vndf, dev, base, n, outs, timed, steps, warm, world, peak, clk)
         result["gpu_launches_extended"] = 2 * steps
 
     if not args.no_fwd_bwd:
@@ -513,7 +520,7 @@ def microbench(vndf, dev, world, timed):
     return out
 
 
-def extended_legs(vndf, dev, base, n, outs, timed, steps, warm, world, peak):
+def extended_legs(vndf, dev, base, n, outs, timed, steps, warm, world, peak, clk):
     """The extended domain (2^28 sphere workload, half below the horizon) and the stand-alone
     hemisphere sampler (2^28 directions of mixed length), HBM-resident, Philox in-kernel."""
     import torch
@@ -528,7 +535,7 @@ def extended_legs(vndf, dev, base, n, outs, timed, steps, warm, world, peak):
     res["sphere"] = {"workload": "sphere_stream_2e28", "value": world * n / (ms * 1e-3) / 1e9, "unit": UNIT,
                      "ms_per_step": ms, "bytes_per_sample": BYTES_PER_SAMPLE,
                      "roofline_frac": BYTES_PER_SAMPLE * n / (ms * 1e-3) / 1e9 / peak,
-                     "method": "spherical_cap_extended"}
+                     "method": "spherical_cap_extended", "issue": issue_roofline("extended", n, ms, clk)}
     del d
     h = workloads.hemisphere_stream(n=n, device=dev)
     t, _, _ = timed(lambda: vndf.vndf_sample_hemisphere(h["wi_x"], h["wi_y"], h["wi_z"], seed=2, counter_base=base,
@@ -537,7 +544,8 @@ def extended_legs(vndf, dev, base, n, outs, timed, steps, warm, world, peak):
     ms = t / steps
     res["hemisphere"] = {"workload": "hemisphere_stream_2e28", "value": world * n / (ms * 1e-3) / 1e9,
                          "unit": UNIT, "ms_per_step": ms, "bytes_per_sample": 28,
-                         "roofline_frac": 28 * n / (ms * 1e-3) / 1e9 / peak}
+                         "roofline_frac": 28 * n / (ms * 1e-3) / 1e9 / peak,
+                         "issue": issue_roofline("hemisphere", n, ms, clk)}
     del h
     torch.cuda.empty_cache()
     return res
