@@ -62,6 +62,7 @@ def parse_args():
     p.add_argument("--no-reflection", action="store_true")
     p.add_argument("--no-cpu-protocol", action="store_true")
     p.add_argument("--no-extended", action="store_true")
+    p.add_argument("--no-isotropic", action="store_true")
     p.add_argument("--log2n-adjoint", type=int, default=24)
     return p.parse_args()
 
@@ -72,7 +73,8 @@ KERNEL_FILES = {
     "microbench_cap": ("microbench.cu", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
     "microbench_cap_strict": ("microbench.cu", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
     "microbench_polar": ("microbench.cu", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
-    "loss_backward": ("backward.cu", "vndf_adjoint.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
+    "loss_backward": ("backward.cu", "staging.cuh", "vndf_adjoint.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh",
+                      "common.cuh"),
     "albedo": ("albedo.cu", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
     "fit": ("fit.cu", "vndf_adjoint.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
     "reflection": ("reflect.cu", "rescue.cuh", "staging.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh",
@@ -132,8 +134,20 @@ def issue_roofline(kernel, samples, ms, clock_mhz):
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     peak = sms * LANES_PER_SM * clock_mhz * 1e6 / 1e12
     achieved = per * samples / (ms * 1e-3) / 1e12
+    max_mhz = max_sm_clock_mhz()
+    peak_max = sms * LANES_PER_SM * max_mhz * 1e6 / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s", "frac": achieved / peak,
-            "thread_inst_per_sample": per, "peak_basis": f"{sms} SMs x 128 lanes x {clock_mhz:.0f} MHz"}
+            "thread_inst_per_sample": per, "peak_basis": f"{sms} SMs x 128 lanes x {clock_mhz:.0f} MHz (sampled)",
+            "peak_at_max_clock": peak_max, "frac_at_max_clock": achieved / peak_max}
+
+
+def max_sm_clock_mhz():
+    """Maximum SM clock: the measured figure in MEASURED_PEAKS.json, else the GB300 nominal 2070 MHz."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh).get("sm_max_mhz") or 2070.0)
+    except (OSError, ValueError):
+        return 2070.0
 
 
 def hbm_peak():
@@ -407,6 +421,10 @@ def run_ours(args, rank, world):
         result["extended"] = extended_legs(vndf, dev, base, n, outs, timed, steps, warm, world, peak, clk)
         result["gpu_launches_extended"] = 2 * steps
 
+    if not args.no_isotropic:
+        result["isotropic"] = isotropic_leg(vndf, dev, rank, world, timed, peak)
+        result["gpu_launches_isotropic"] = result["isotropic"]["launches"]
+
     if not args.no_fwd_bwd:
         result["fwd_bwd"] = fwd_bwd(vndf, dev, rank, world, timed, peak, args.log2n_adjoint)
         result["fwd_bwd"]["issue"] = issue_roofline("loss_backward", 1 << args.log2n_adjoint,
@@ -469,7 +487,7 @@ def fwd_bwd(vndf, dev, rank, world, timed, peak, log2n):
             "ms_per_step": ms, "steps": steps,
             "hbm": {"algorithmic_bytes": 52 * n, "achieved_gbs": 52 * n / (ms * 1e-3) / 1e9,
                     "frac": 52 * n / (ms * 1e-3) / 1e9 / peak},
-            "kernels": "loss_backward_kernel + sum_partials_kernel"}
+            "kernels": "loss_backward_pipe_kernel (+ loss_backward_kernel for a ragged last chunk) + sum_partials_kernel"}
 
 
 def albedo(vndf, dev, rank, world, timed):
@@ -499,6 +517,37 @@ def albedo(vndf, dev, rank, world, timed):
             "config": {"warps_per_cta": best[0], "groups_per_item": best[1], "ctas_per_sm": best[2]},
             "captured": "cuda graph (prologue + persistent kernel)",
             "E_range": [float(E.min().item()), float(E.max().item())]}
+
+
+def isotropic_leg(vndf, dev, rank, world, timed, peak):
+    """2^20 isotropic samples with precomputed uniforms (Philox seed 1): 40 B/sample, 42 MB in all, so the
+    working set stays in L2 and a single launch is short; timed as replays of a graph of 100 launches."""
+    import torch
+
+    import workloads
+    n, reps, steps = 1 << 20, 100, 20
+    d = workloads.isotropic_2e20(n=n, device=dev)
+    u1, u2 = vndf.vndf_rng_uniform(n, 1, rank * n, 0, device=dev)
+    outs = [torch.empty(n, device=dev) for _ in range(4)]
+
+    def call():
+        vndf.vndf_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], None, u1, u2, wm_x=outs[0], wm_y=outs[1],
+                         wm_z=outs[2], pdf=outs[3])
+    side = torch.cuda.Stream(dev)
+    with torch.cuda.stream(side):
+        call()
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        for _ in range(reps):
+            call()
+    tot, _, _ = timed(graph.replay, steps, 3)
+    ms = tot / (steps * reps)
+    return {"workload": "isotropic_2e20", "samples": n, "value": world * n / (ms * 1e-3) / 1e9, "unit": UNIT,
+            "ms_per_launch": ms, "launches": steps * reps, "bytes_per_sample": 40,
+            "achieved_gbs": 40 * n / (ms * 1e-3) / 1e9, "hbm_frac": 40 * n / (ms * 1e-3) / 1e9 / peak,
+            "note": "L2-resident (42 MB < 129 MB L2): the HBM fraction can exceed 1; launch-bound at this size",
+            "captured": f"cuda graph of {reps} launches"}
 
 
 def microbench(vndf, dev, world, timed):

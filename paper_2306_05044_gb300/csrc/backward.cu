@@ -11,7 +11,20 @@
 
 #include "common.cuh"
 #include "philox.cuh"
+#include "staging.cuh"
 #include "vndf_adjoint.cuh"
+
+// Staged fused kernel: 1 = full chunks go through loss_backward_pipe_kernel; its grid
+// (at most this many waves of 8 CTAs per SM) and resident CTAs per SM.
+#ifndef VNDF_BWD_STAGED
+#define VNDF_BWD_STAGED 1
+#endif
+#ifndef VNDF_BWD_WAVES
+#define VNDF_BWD_WAVES 4
+#endif
+#ifndef VNDF_BWD_MIN_BLOCKS
+#define VNDF_BWD_MIN_BLOCKS 3
+#endif
 
 namespace vndf {
 
@@ -136,9 +149,9 @@ __device__ __forceinline__ float block_sum(float v, float* smem) {
 }
 
 template <bool PHILOX, bool ISO, bool VEC>
-__global__ void __launch_bounds__(kBwdBlock, 3) loss_backward_kernel(BwdArgs a, int64_t n, int64_t chunks,
-                                                                  float* partials) {
-  for (int64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
+__global__ void __launch_bounds__(kBwdBlock, 3) loss_backward_kernel(BwdArgs a, int64_t n, int64_t ch0,
+                                                                  int64_t chunks, float* partials) {
+  for (int64_t ch = ch0 + blockIdx.x; ch < chunks; ch += gridDim.x) {
     const int64_t e = ch * kChunk + 4 * int64_t(threadIdx.x);
     float X[4], Y[4], Z[4], AX[4], AY[4], U1[4], U2[4], CX[4], CY[4], CZ[4];
     const bool full = VEC && e + 3 < n;
@@ -230,6 +243,97 @@ __global__ void __launch_bounds__(kBwdBlock, 3) loss_backward_kernel(BwdArgs a, 
   }
 }
 
+template <bool PHILOX, bool ISO>
+__host__ __device__ constexpr int loss_streams_in() { return 7 + (ISO ? 0 : 1) + (PHILOX ? 0 : 2); }
+
+// This thread's 16-byte slice of every input stream of chunk ch, copied to shared memory.
+template <bool PHILOX, bool ISO>
+__device__ __forceinline__ void loss_stage(const BwdArgs& a, int64_t e, float4* slot) {
+  int k = 0;
+  cp_async16(slot + (k++) * kBwdBlock, a.wx + e);
+  cp_async16(slot + (k++) * kBwdBlock, a.wy + e);
+  cp_async16(slot + (k++) * kBwdBlock, a.wz + e);
+  cp_async16(slot + (k++) * kBwdBlock, a.ax + e);
+  if constexpr (!ISO) cp_async16(slot + (k++) * kBwdBlock, a.ay + e);
+  cp_async16(slot + (k++) * kBwdBlock, a.gmx + e);
+  cp_async16(slot + (k++) * kBwdBlock, a.gmy + e);
+  cp_async16(slot + (k++) * kBwdBlock, a.gmz + e);
+  if constexpr (!PHILOX) {
+    cp_async16(slot + (k++) * kBwdBlock, a.u1 + e);
+    cp_async16(slot + (k++) * kBwdBlock, a.u2 + e);
+  }
+}
+
+// The fused kernel over the full chunks [0, chunks), 16-byte aligned streams: each
+// thread's slice of the next chunk is staged in shared memory with cp.async while
+// the current one is computed (per-thread copies, no barrier).  Partials are those
+// of loss_backward_kernel, so the loss does not depend on which kernel ran.
+template <bool PHILOX, bool ISO>
+__global__ void __launch_bounds__(kBwdBlock, VNDF_BWD_MIN_BLOCKS) loss_backward_pipe_kernel(BwdArgs a, int64_t chunks,
+                                                                       float* partials) {
+  constexpr int NS = loss_streams_in<PHILOX, ISO>();
+  extern __shared__ float4 smem_l[];  // [2][NS][kBwdBlock]
+  float4* mine = smem_l + threadIdx.x;
+  if (int64_t(blockIdx.x) < chunks)
+    loss_stage<PHILOX, ISO>(a, int64_t(blockIdx.x) * kChunk + 4 * threadIdx.x, mine);
+  cp_async_commit();
+  int slot = 0;
+  for (int64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
+    const int64_t e = ch * kChunk + 4 * int64_t(threadIdx.x);
+    if (ch + gridDim.x < chunks)
+      loss_stage<PHILOX, ISO>(a, e + int64_t(gridDim.x) * kChunk, mine + (slot ^ 1) * NS * kBwdBlock);
+    cp_async_commit();
+    cp_async_wait<1>();
+    const float4* cur = mine + slot * NS * kBwdBlock;
+    slot ^= 1;
+    float X[4], Y[4], Z[4], AX[4], AY[4], U1[4], U2[4], CX[4], CY[4], CZ[4];
+    int k = 0;
+    *reinterpret_cast<float4*>(X) = cur[(k++) * kBwdBlock];
+    *reinterpret_cast<float4*>(Y) = cur[(k++) * kBwdBlock];
+    *reinterpret_cast<float4*>(Z) = cur[(k++) * kBwdBlock];
+    *reinterpret_cast<float4*>(AX) = cur[(k++) * kBwdBlock];
+    if constexpr (ISO) {
+      *reinterpret_cast<float4*>(AY) = *reinterpret_cast<float4*>(AX);
+    } else {
+      *reinterpret_cast<float4*>(AY) = cur[(k++) * kBwdBlock];
+    }
+    *reinterpret_cast<float4*>(CX) = cur[(k++) * kBwdBlock];
+    *reinterpret_cast<float4*>(CY) = cur[(k++) * kBwdBlock];
+    *reinterpret_cast<float4*>(CZ) = cur[(k++) * kBwdBlock];
+    if constexpr (PHILOX) {
+      uniforms4(a.rng, uint64_t(e), U1, U2);
+    } else {
+      *reinterpret_cast<float4*>(U1) = cur[(k++) * kBwdBlock];
+      *reinterpret_cast<float4*>(U2) = cur[(k++) * kBwdBlock];
+    }
+    float OWX[4], OWY[4], OWZ[4], OAX[4], OAY[4];
+    float local = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float mx, my, mz, pdf;
+      const Grad5 g = cap_backward_one(X[j], Y[j], Z[j], AX[j], AY[j], U1[j], U2[j], CX[j], CY[j], CZ[j], 0.f,
+                                       1.f, mx, my, mz, pdf);
+      const bool ok = pdf > 0.f;
+      local += ok ? fmaf(CX[j], mx, fmaf(CY[j], my, fmaf(CZ[j], mz, __logf(pdf)))) : 0.f;
+      OWX[j] = g.wx;
+      OWY[j] = g.wy;
+      OWZ[j] = g.wz;
+      OAX[j] = ISO ? g.ax + g.ay : g.ax;
+      OAY[j] = g.ay;
+    }
+    if (a.gwx) {
+      store4(a.gwx, e, OWX);
+      store4(a.gwy, e, OWY);
+      store4(a.gwz, e, OWZ);
+    }
+    if (a.gax) store4(a.gax, e, OAX);
+    if (!ISO && a.gay) store4(a.gay, e, OAY);
+    const float w = warp_sum(local);
+    if ((threadIdx.x & 31) == 0) partials[ch * (kChunk / kGroup) + (threadIdx.x >> 5)] = w;
+  }
+  cp_async_wait<0>();
+}
+
 // One block: thread t sums partials t, t + 1024, ... in order, then a fixed tree.
 __global__ void __launch_bounds__(1024) sum_partials_kernel(const float* partials, int64_t m, float* out) {
   __shared__ float smem[32];
@@ -257,11 +361,29 @@ template <bool PHILOX, bool ISO>
 int launch_loss(const BwdArgs& a, int64_t n, bool vec, float* partials, float* loss, cudaStream_t s) {
   const int64_t chunks = (n + kChunk - 1) / kChunk;
   const int64_t groups = (n + kGroup - 1) / kGroup;
-  const unsigned grid = grid_for(chunks * kBwdBlock, kBwdBlock, 8, 16);
-  if (vec)
-    loss_backward_kernel<PHILOX, ISO, true><<<grid, kBwdBlock, 0, s>>>(a, n, chunks, partials);
-  else
-    loss_backward_kernel<PHILOX, ISO, false><<<grid, kBwdBlock, 0, s>>>(a, n, chunks, partials);
+  if (vec && VNDF_BWD_STAGED) {
+    // full chunks through the staged kernel, the ragged last chunk (if any) through the plain one
+    const int64_t full = n / kChunk;
+    if (full > 0) {
+      constexpr size_t smem = size_t(2) * loss_streams_in<PHILOX, ISO>() * kBwdBlock * 16;
+      static bool attr_set = false;  // per instantiation
+      if (!attr_set) {
+        if (cudaFuncSetAttribute(loss_backward_pipe_kernel<PHILOX, ISO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(smem)) != cudaSuccess)
+          return VNDF_ERR_CUDA;
+        attr_set = true;
+      }
+      loss_backward_pipe_kernel<PHILOX, ISO>
+          <<<grid_for(full * kBwdBlock, kBwdBlock, 8, VNDF_BWD_WAVES), kBwdBlock, smem, s>>>(a, full, partials);
+    }
+    if (full < chunks) loss_backward_kernel<PHILOX, ISO, true><<<1, kBwdBlock, 0, s>>>(a, n, full, chunks, partials);
+  } else {
+    const unsigned grid = grid_for(chunks * kBwdBlock, kBwdBlock, 8, 16);
+    if (vec)
+      loss_backward_kernel<PHILOX, ISO, true><<<grid, kBwdBlock, 0, s>>>(a, n, 0, chunks, partials);
+    else
+      loss_backward_kernel<PHILOX, ISO, false><<<grid, kBwdBlock, 0, s>>>(a, n, 0, chunks, partials);
+  }
   sum_partials_kernel<<<1, 1024, 0, s>>>(partials, groups, loss);
   return launch_status();
 }
