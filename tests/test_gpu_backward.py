@@ -140,6 +140,27 @@ def test_fused_loss_ragged_and_unaligned(v):
             torch.testing.assert_close(a[:n], b[:n], rtol=1e-4, atol=1e-6)
 
 
+def test_fused_loss_staged_path(v):
+    """Above 16 x 3 x SMs full chunks the fused loss runs the shared-memory-staged kernel (plus the plain
+    kernel on a ragged last chunk): per-sample gradients equal, bit for bit, those of small calls that take
+    the plain kernel, and the loss equals the FP64 sum of the same per-sample terms."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = 16 * 3 * sms * 1024 + 517
+    d = workloads.adjoint_2e24(n=n, seed=43, device=DEV)
+    keys = ("wi_x", "wi_y", "wi_z", "alpha_x", "alpha_y", "c_x", "c_y", "c_z")
+    big = v.vndf_sample_loss_backward(*(d[k] for k in keys), seed=8)
+    for start, m in ((0, 3000), (n // 2 + 5, 1025), (n - 2000, 2000)):
+        part = v.vndf_sample_loss_backward(*(d[k][start:start + m].contiguous() for k in keys), seed=8,
+                                           counter_base=start)
+        for a, b in zip(big[1:], part[1:]):
+            assert torch.equal(a[start:start + m], b)
+    wx, wy, wz, pdf = v.vndf_sample(*(d[k] for k in keys[:5]), seed=8)
+    terms = (d["c_x"].double() * wx.double() + d["c_y"].double() * wy.double() + d["c_z"].double() * wz.double()
+             + torch.log(pdf.double()))
+    ref = terms.sum().item()
+    assert abs(big[0].item() - ref) <= 1e-5 * terms.abs().sum().item()
+
+
 def test_autograd_function(v):
     from paper_2306_05044_gb300.autograd import vndf_sample_autograd
     n = 5000
