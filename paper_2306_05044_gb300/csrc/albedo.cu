@@ -146,7 +146,7 @@ __device__ __forceinline__ float albedo_weight(const QueryConst& c, float f0, fl
   const float oz = fmaf(2.f * d, mz, -c.uz);
   const float sx = c.ax * ox, sy = c.ay * oy;
   const float po = fmaf(sx, sx, sy * sy);
-  const float lo = sqrtf(fmaf(oz, oz, po));
+  const float lo = sqrt_fast(fmaf(oz, oz, po));
   const float num = c.A * oz;
   const float g = __fdividef(num, fmaf(c.uz * po, __fdividef(1.f, lo + oz), num));
   const float t = 1.f - d;

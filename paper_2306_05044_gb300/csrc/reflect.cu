@@ -102,7 +102,7 @@ __device__ __forceinline__ Reflected reflect_one(float wx, float wy, float wz, f
   const float A = fmaf(L, rw, uz);                   // |M^-1 wi_unit| + wi_unit.z
   const float px = ax * r.ox, py = ay * r.oy;
   const float po = fmaf(px, px, py * py);
-  const float lo = sqrtf(fmaf(r.oz, r.oz, po));
+  const float lo = sqrt_fast(fmaf(r.oz, r.oz, po));
   const float num = A * r.oz;
   const float g = __fdividef(num, fmaf(uz * po, __fdividef(1.f, lo + r.oz), num));
   const float t = 1.f - d;
