@@ -35,6 +35,10 @@ namespace vndf {
 
 constexpr int kGroupSamples = 256;  // samples per reduction group (one warp)
 constexpr int kLaneSamples = 8;     // consecutive samples per lane
+// Up to this many item offsets (nq + 1) are copied into each CTA's shared
+// memory (48 KB, the default dynamic limit), so that finding an item's query
+// costs shared-memory rather than L2 latency; larger batches search in place.
+constexpr int32_t kCachedOffsets = 12288;
 
 struct AlbedoArgs {
   const float *wx, *wy, *wz, *ax, *ay;
@@ -163,9 +167,15 @@ __device__ __forceinline__ float warp_tree(float v) {
 
 // ---------------------------------------------------------------- persistent kernel
 __global__ void __launch_bounds__(512) albedo_kernel(AlbedoArgs a) {
+  extern __shared__ int32_t s_offsets[];
   const int lane = threadIdx.x & 31;
   const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
   const int32_t* offsets = a.ctl + 2;
+  if (a.nq + 1 <= kCachedOffsets) {  // uniform over the block
+    for (int32_t i = threadIdx.x; i <= a.nq; i += blockDim.x) s_offsets[i] = offsets[i];
+    __syncthreads();
+    offsets = s_offsets;
+  }
   int32_t* done = a.ctl + 3 + a.nq;
   const int32_t total = a.ctl[1];
   for (int64_t item = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); item < total;
@@ -243,7 +253,8 @@ int launch_albedo(AlbedoArgs a, const AlbedoConfig& c, cudaStream_t s) {
   a.groups_per_item = c.groups_per_item;
   albedo_prologue_kernel<<<1, 1024, 0, s>>>(a);
   const unsigned grid = static_cast<unsigned>(sm_count() * c.ctas_per_sm);
-  albedo_kernel<<<grid, 32 * c.block_warps, 0, s>>>(a);
+  const size_t smem = a.nq + 1 <= kCachedOffsets ? size_t(a.nq + 1) * sizeof(int32_t) : 0;
+  albedo_kernel<<<grid, 32 * c.block_warps, smem, s>>>(a);
   return launch_status();
 }
 

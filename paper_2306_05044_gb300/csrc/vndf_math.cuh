@@ -202,9 +202,10 @@ __device__ __forceinline__ void polar_disk_normal(const Stretched& i, float u1, 
 
 // Threshold on the condition number above which a cap sample is recomputed in
 // double-float (cap_half_vector_precise): with it every sample meets 4e-6 rad
-// for wm and 1e-5 relative for the pdf; about 4e-4 of the anisotropic
-// workload's samples take that path.
-constexpr float kRescueKappa = 32.f;
+// for wm and 1e-5 relative for the pdf with margin (the pdf's error grows like
+// 3 kappa + 2 kappa_h ulps, the angle's like kappa); about 7e-4 of the
+// anisotropic workload's samples take that path.
+constexpr float kRescueKappa = 24.f;
 
 // The FP32 tail of a sample: unstretch h, normalise, and (if PDF) the fused density.
 template <int METHOD, bool PDF>
