@@ -256,11 +256,10 @@ __device__ __forceinline__ bool sample_one(float wx, float wy, float wz, float a
     const float vx = ax * hx, vy = ay * hy;
     const float vv = fmaf(vx, vx, fmaf(vy, vy, hz * hz));
     const float k2 = fmaf(ax * sx, ax * sx, fmaf(ay * sy, ay * sy, hz * hz));
-    bad = k2 > kRescueKappa * kRescueKappa * vv;
-    if constexpr (PDF) {
-      const float kh2 = fmaf(sx, sx, fmaf(sy, sy, hz * hz));
-      bad |= kh2 > kRescueKappa * kRescueKappa * fmaf(hx, hx, fmaf(hy, hy, hz * hz));
-    }
+    // both tests whether or not the pdf is wanted, so the normals do not depend on it
+    const float kh2 = fmaf(sx, sx, fmaf(sy, sy, hz * hz));
+    bad = (k2 > kRescueKappa * kRescueKappa * vv) |
+          (kh2 > kRescueKappa * kRescueKappa * fmaf(hx, hx, fmaf(hy, hy, hz * hz)));
     bad &= ok;
   }
   if (!ok) {
