@@ -368,13 +368,7 @@ int launch_loss(const BwdArgs& a, int64_t n, bool vec, float* partials, float* l
     // full chunks through the staged kernel, the ragged last chunk (if any) through the plain one
     {
       constexpr size_t smem = size_t(2) * loss_streams_in<PHILOX, ISO>() * kBwdBlock * 16;
-      static bool attr_set = false;  // per instantiation
-      if (!attr_set) {
-        if (cudaFuncSetAttribute(loss_backward_pipe_kernel<PHILOX, ISO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(smem)) != cudaSuccess)
-          return VNDF_ERR_CUDA;
-        attr_set = true;
-      }
+      if (!ensure_dynamic_smem<loss_backward_pipe_kernel<PHILOX, ISO>>(smem)) return VNDF_ERR_CUDA;
       loss_backward_pipe_kernel<PHILOX, ISO>
           <<<grid_for(full * kBwdBlock, kBwdBlock, 8, VNDF_BWD_WAVES), kBwdBlock, smem, s>>>(a, full, partials);
     }

@@ -170,13 +170,7 @@ int launch_hemi(const HemiArgs& a, int64_t n, bool vec, cudaStream_t s) {
     const int64_t n4 = n / 4;
     constexpr size_t smem =
         size_t(2) * hemi_streams_in<PHILOX>() * kHemiBlock * 16 + (kHemiBlock / 32) * sizeof(RescueQueue);
-    static bool attr_set = false;  // per instantiation
-    if (!attr_set) {
-      if (cudaFuncSetAttribute(hemi_pipe_kernel<PHILOX, PDF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               int(smem)) != cudaSuccess)
-        return VNDF_ERR_CUDA;
-      attr_set = true;
-    }
+    if (!ensure_dynamic_smem<hemi_pipe_kernel<PHILOX, PDF>>(smem)) return VNDF_ERR_CUDA;
     hemi_pipe_kernel<PHILOX, PDF><<<grid_for(n4, kHemiBlock, 8, VNDF_SAMPLE_WAVES), kHemiBlock, smem, s>>>(a, n4);
     done = 4 * n4;
   }

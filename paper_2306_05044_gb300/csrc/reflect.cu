@@ -243,13 +243,7 @@ int launch_reflect(const ReflArgs& a, int64_t n, bool vec, cudaStream_t s) {
     const int64_t n4 = n / 4;
     constexpr size_t smem =
         size_t(2) * streams_in<PHILOX, ISO>() * kReflBlock * 16 + (kReflBlock / 32) * sizeof(RescueQueue);
-    static bool attr_set = false;  // per instantiation
-    if (!attr_set) {
-      if (cudaFuncSetAttribute(reflect_pipe_kernel<PHILOX, ISO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               int(smem)) != cudaSuccess)
-        return VNDF_ERR_CUDA;
-      attr_set = true;
-    }
+    if (!ensure_dynamic_smem<reflect_pipe_kernel<PHILOX, ISO>>(smem)) return VNDF_ERR_CUDA;
     reflect_pipe_kernel<PHILOX, ISO><<<grid_for(n4, kReflBlock, 8, VNDF_SAMPLE_WAVES), kReflBlock, smem, s>>>(a, n4);
     done = 4 * n4;
   }

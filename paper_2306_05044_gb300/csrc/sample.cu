@@ -269,13 +269,7 @@ int launch_sample(const SampleArgs& a, int64_t n, bool vec, cudaStream_t s) {
       if constexpr (VNDF_SAMPLE_STAGES >= 2) {
         constexpr size_t smem = size_t(VNDF_SAMPLE_STAGES) * streams_in<PHILOX, ISO>() * kSampleBlock * 16 +
                                 (kSampleBlock / 32) * sizeof(RescueQueue);
-        static bool attr_set = false;  // per instantiation; setting it twice is harmless
-        if (!attr_set) {
-          if (cudaFuncSetAttribute(sample_pipe_kernel<METHOD, PHILOX, ISO, PDF>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
-            return VNDF_ERR_CUDA;
-          attr_set = true;
-        }
+        if (!ensure_dynamic_smem<sample_pipe_kernel<METHOD, PHILOX, ISO, PDF>>(smem)) return VNDF_ERR_CUDA;
         sample_pipe_kernel<METHOD, PHILOX, ISO, PDF><<<grid, kSampleBlock, smem, s>>>(a, n4);
       } else {
         sample_vec4_kernel<METHOD, PHILOX, ISO, PDF><<<grid, kSampleBlock, 0, s>>>(a, n4);

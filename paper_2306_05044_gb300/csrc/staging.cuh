@@ -7,7 +7,27 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <cstdint>
+
 namespace vndf {
+
+// Raise KERNEL's dynamic shared-memory limit to `bytes` on the current device,
+// once per (kernel, device): the attribute belongs to the device's copy of the
+// kernel, so a process that uses several GPUs sets it on each.  Thread-safe;
+// returns false if the CUDA call fails.
+template <auto KERNEL>
+inline bool ensure_dynamic_smem(size_t bytes) {
+  static std::atomic<uint64_t> done{0};  // bit d: set on device d (devices 0..63)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  const uint64_t bit = (dev >= 0 && dev < 64) ? (uint64_t(1) << dev) : 0;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return true;
+  if (cudaFuncSetAttribute(KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)) != cudaSuccess)
+    return false;
+  if (bit) done.fetch_or(bit, std::memory_order_release);
+  return true;
+}
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));

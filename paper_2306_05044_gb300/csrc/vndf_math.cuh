@@ -155,8 +155,8 @@ __device__ __forceinline__ void cap_half_vector(const Stretched& i, float u1, fl
   hz = (1.f - u2) * a;                  // z + i.z
 }
 
-// Heitz 2018 cross-section sampler: returns a unit hemisphere normal h.
-// Same construction as the printed listing (basis (w1, w2, i), a uniform point
+// Heitz 2018 cross-section sampler (Sec. 2 step (2)): returns a unit hemisphere
+// normal h.  The construction of that method (basis (w1, w2, i), a uniform point
 // (t1, t2) on the unit disk, the far half compressed by s = (1 + i.z)/2, lifted
 // onto the hemisphere along i), with the rounding care the cap sampler gets:
 // every quantity that cancels near the rim of the disk is rewritten exactly,
