@@ -29,6 +29,9 @@
 #ifndef VNDF_SAMPLE_STAGES
 #define VNDF_SAMPLE_STAGES 2
 #endif
+#ifndef VNDF_SAMPLE_MIN_ITERS
+#define VNDF_SAMPLE_MIN_ITERS 4
+#endif
 // Ill-conditioned samples: 1 = queued per warp and redone 32 at a time
 // (rescue.cuh); 0 = each redone in place by its own lane.
 #ifndef VNDF_RESCUE_BATCHED
@@ -265,7 +268,16 @@ int launch_sample(const SampleArgs& a, int64_t n, bool vec, cudaStream_t s) {
   if (vec) {
     const int64_t n4 = n / 4;
     if (n4 > 0) {
-      const unsigned grid = grid_for(n4, kSampleBlock, 2048 / kSampleBlock, VNDF_SAMPLE_WAVES);
+      // small calls: at least VNDF_SAMPLE_MIN_ITERS groups per thread (so the staging overlaps), but never
+      // fewer CTAs than one per SM
+      unsigned grid = grid_for(n4, kSampleBlock, 2048 / kSampleBlock, VNDF_SAMPLE_WAVES);
+      if (VNDF_SAMPLE_MIN_ITERS > 1) {
+        const int64_t per_iters = (n4 + int64_t(kSampleBlock) * VNDF_SAMPLE_MIN_ITERS - 1) /
+                                  (int64_t(kSampleBlock) * VNDF_SAMPLE_MIN_ITERS);
+        const int64_t lo = sm_count();
+        const int64_t g = per_iters > lo ? per_iters : lo;
+        if (g < int64_t(grid)) grid = unsigned(g);
+      }
       if constexpr (VNDF_SAMPLE_STAGES >= 2) {
         constexpr size_t smem = size_t(VNDF_SAMPLE_STAGES) * streams_in<PHILOX, ISO>() * kSampleBlock * 16 +
                                 (kSampleBlock / 32) * sizeof(RescueQueue);
