@@ -9,6 +9,9 @@ Nothing here touches the CUDA library.
 import numpy as np
 import pytest
 
+# planted mistakes produce NaNs and divisions by zero; that is what the detectors catch
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
 import oracle_checks as oc
 from oracle import microfacet, philox, vndf
 
