@@ -21,7 +21,8 @@
 //   group, and the warp that completes a query's last item sums the query's
 //   group partials (fixed lane-strided order + butterfly) into E_q.
 // * Nothing waits on anything: completion is detected with an atomic counter
-//   per query (fence, then atomicAdd), so no warp ever spins.
+//   per query (fence, then atomicAdd), so no warp ever spins.  The one barrier
+//   is at CTA start, after the item offsets are copied into shared memory.
 #include <cuda_runtime.h>
 
 #include <cmath>
