@@ -63,6 +63,7 @@ def parse_args():
     p.add_argument("--no-cpu-protocol", action="store_true")
     p.add_argument("--no-extended", action="store_true")
     p.add_argument("--no-isotropic", action="store_true")
+    p.add_argument("--no-pdf", action="store_true")
     p.add_argument("--log2n-adjoint", type=int, default=24)
     return p.parse_args()
 
@@ -421,6 +422,14 @@ def run_ours(args, rank, world):
         result["extended"] = extended_legs(vndf, dev, base, n, outs, timed, steps, warm, world, peak, clk)
         result["gpu_launches_extended"] = 2 * steps
 
+    if not args.no_pdf:
+        pt, _, _ = timed(lambda: vndf.vndf_pdf(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], outs[0],
+                                               outs[1], outs[2], pdf=outs[3]), steps, warm)
+        result["pdf"] = {"value": world * n * steps / (pt * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": pt / steps,
+                         "bytes_per_sample": 36, "roofline_frac": 36 * n / (pt / steps * 1e-3) / 1e9 / peak,
+                         "note": "vndf_pdf at the headline's sampled normals (wi, alpha, wm in; pdf out)"}
+        result["gpu_launches_pdf"] = steps
+
     if not args.no_isotropic:
         result["isotropic"] = isotropic_leg(vndf, dev, rank, world, timed, peak)
         result["gpu_launches_isotropic"] = result["isotropic"]["launches"]
@@ -429,7 +438,9 @@ def run_ours(args, rank, world):
         result["fwd_bwd"] = fwd_bwd(vndf, dev, rank, world, timed, peak, args.log2n_adjoint)
         result["fwd_bwd"]["issue"] = issue_roofline("loss_backward", 1 << args.log2n_adjoint,
                                                     result["fwd_bwd"]["ms_per_step"], clk)
-        result["gpu_launches_fwd_bwd"] = 2 * steps
+        result["gpu_launches_fwd_bwd"] = 2 * result["fwd_bwd"]["steps"]
+        result["backward_generic"] = backward_generic(vndf, dev, rank, world, timed, peak, args.log2n_adjoint)
+        result["gpu_launches_backward_generic"] = result["backward_generic"]["steps"]
 
     if not args.no_albedo:
         result["albedo"] = albedo(vndf, dev, rank, world, timed)
@@ -488,6 +499,32 @@ def fwd_bwd(vndf, dev, rank, world, timed, peak, log2n):
             "hbm": {"algorithmic_bytes": 52 * n, "achieved_gbs": 52 * n / (ms * 1e-3) / 1e9,
                     "frac": 52 * n / (ms * 1e-3) / 1e9 / peak},
             "kernels": "loss_backward_pipe_kernel (+ loss_backward_kernel for a ragged last chunk) + sum_partials_kernel"}
+
+
+def backward_generic(vndf, dev, rank, world, timed, peak, log2n):
+    """Generic adjoint (vndf_sample_backward) on the 2^24-sample adjoint workload: g_wm = c and a uniform
+    g_pdf given, gradients of wi and both alphas returned (56 B/sample)."""
+    import torch
+
+    import workloads
+    n = 1 << log2n
+    d = workloads.adjoint_2e24(n=n, device=dev)
+    gp = torch.rand(n, device=dev, generator=torch.Generator(device=dev).manual_seed(9))
+    keys = ("wi_x", "wi_y", "wi_z", "alpha_x", "alpha_y")
+
+    def step():
+        vndf.vndf_sample_backward(*(d[k] for k in keys), seed=4, counter_base=rank * n, g_wm_x=d["c_x"],
+                                  g_wm_y=d["c_y"], g_wm_z=d["c_z"], g_pdf=gp)
+
+    steps = 100
+    total, _, _ = timed(step, steps, 5)
+    ms = total / steps
+    del d
+    return {"workload": f"adjoint_2e{log2n}", "value": world * n / (ms * 1e-3) / 1e9, "unit": UNIT,
+            "ms_per_step": ms, "steps": steps, "bytes_per_sample": 56,
+            "hbm": {"algorithmic_bytes": 56 * n, "achieved_gbs": 56 * n / (ms * 1e-3) / 1e9,
+                    "frac": 56 * n / (ms * 1e-3) / 1e9 / peak},
+            "kernels": "backward_pipe_kernel (vector path), backward_scalar_kernel for a ragged tail"}
 
 
 def albedo(vndf, dev, rank, world, timed):

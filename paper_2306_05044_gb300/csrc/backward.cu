@@ -125,6 +125,102 @@ __global__ void __launch_bounds__(kBwdBlock) backward_scalar_kernel(BwdArgs a, i
   }
 }
 
+// The generic adjoint over full 4-sample groups with 16-byte aligned streams: each
+// thread's next group is staged in shared memory with cp.async while the current
+// one is computed (per-thread copies, no barrier).  The optional adjoint inputs
+// g_wm and g_pdf are staged only when given (warp-uniform flags); slot k of the
+// layout is stream k in the order wi xyz, alpha_x, [alpha_y], [u1, u2], [g_wm xyz],
+// [g_pdf].  Same per-sample function, so the same bits as backward_vec4_kernel.
+template <bool PHILOX, bool ISO>
+__host__ __device__ constexpr int bwd_fixed_streams() { return 4 + (ISO ? 0 : 1) + (PHILOX ? 0 : 2); }
+
+template <bool PHILOX, bool ISO>
+__device__ __forceinline__ void bwd_stage(const BwdArgs& a, int64_t e, float4* slot, bool has_g, bool has_p) {
+  int k = 0;
+  cp_async16(slot + (k++) * kBwdBlock, a.wx + e);
+  cp_async16(slot + (k++) * kBwdBlock, a.wy + e);
+  cp_async16(slot + (k++) * kBwdBlock, a.wz + e);
+  cp_async16(slot + (k++) * kBwdBlock, a.ax + e);
+  if constexpr (!ISO) cp_async16(slot + (k++) * kBwdBlock, a.ay + e);
+  if constexpr (!PHILOX) {
+    cp_async16(slot + (k++) * kBwdBlock, a.u1 + e);
+    cp_async16(slot + (k++) * kBwdBlock, a.u2 + e);
+  }
+  if (has_g) {
+    cp_async16(slot + (k++) * kBwdBlock, a.gmx + e);
+    cp_async16(slot + (k++) * kBwdBlock, a.gmy + e);
+    cp_async16(slot + (k++) * kBwdBlock, a.gmz + e);
+  }
+  if (has_p) cp_async16(slot + k * kBwdBlock, a.gp + e);
+}
+
+template <bool PHILOX, bool ISO>
+__global__ void __launch_bounds__(kBwdBlock, VNDF_BWD_MIN_BLOCKS) backward_pipe_kernel(BwdArgs a, int64_t n4) {
+  constexpr int kFixed = bwd_fixed_streams<PHILOX, ISO>();
+  const bool has_g = a.gmx != nullptr, has_p = a.gp != nullptr;
+  const int ns = kFixed + (has_g ? 3 : 0) + (has_p ? 1 : 0);
+  extern __shared__ float4 smem_b[];  // [2][ns][kBwdBlock]
+  const int64_t stride = int64_t(gridDim.x) * kBwdBlock;
+  const int64_t q0 = int64_t(blockIdx.x) * kBwdBlock + threadIdx.x;
+  float4* mine = smem_b + threadIdx.x;
+  if (q0 < n4) bwd_stage<PHILOX, ISO>(a, 4 * q0, mine, has_g, has_p);
+  cp_async_commit();
+  int slot = 0;
+  for (int64_t q = q0; q < n4; q += stride) {
+    if (q + stride < n4) bwd_stage<PHILOX, ISO>(a, 4 * (q + stride), mine + (slot ^ 1) * ns * kBwdBlock, has_g, has_p);
+    cp_async_commit();
+    cp_async_wait<1>();
+    const float4* cur = mine + slot * ns * kBwdBlock;
+    slot ^= 1;
+    const int64_t e = 4 * q;
+    float X[4], Y[4], Z[4], AX[4], AY[4], U1[4], U2[4];
+    float GX[4] = {0.f, 0.f, 0.f, 0.f}, GY[4] = {0.f, 0.f, 0.f, 0.f}, GZ[4] = {0.f, 0.f, 0.f, 0.f};
+    float GP[4] = {0.f, 0.f, 0.f, 0.f};
+    int k = 0;
+    *reinterpret_cast<float4*>(X) = cur[(k++) * kBwdBlock];
+    *reinterpret_cast<float4*>(Y) = cur[(k++) * kBwdBlock];
+    *reinterpret_cast<float4*>(Z) = cur[(k++) * kBwdBlock];
+    *reinterpret_cast<float4*>(AX) = cur[(k++) * kBwdBlock];
+    if constexpr (ISO) {
+      *reinterpret_cast<float4*>(AY) = *reinterpret_cast<float4*>(AX);
+    } else {
+      *reinterpret_cast<float4*>(AY) = cur[(k++) * kBwdBlock];
+    }
+    if constexpr (PHILOX) {
+      uniforms4(a.rng, uint64_t(e), U1, U2);
+    } else {
+      *reinterpret_cast<float4*>(U1) = cur[(k++) * kBwdBlock];
+      *reinterpret_cast<float4*>(U2) = cur[(k++) * kBwdBlock];
+    }
+    if (has_g) {
+      *reinterpret_cast<float4*>(GX) = cur[(k++) * kBwdBlock];
+      *reinterpret_cast<float4*>(GY) = cur[(k++) * kBwdBlock];
+      *reinterpret_cast<float4*>(GZ) = cur[(k++) * kBwdBlock];
+    }
+    if (has_p) *reinterpret_cast<float4*>(GP) = cur[k * kBwdBlock];
+    float OWX[4], OWY[4], OWZ[4], OAX[4], OAY[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float mx, my, mz, pdf;
+      const Grad5 g = cap_backward_one(X[j], Y[j], Z[j], AX[j], AY[j], U1[j], U2[j], GX[j], GY[j], GZ[j], GP[j],
+                                       0.f, mx, my, mz, pdf);
+      OWX[j] = g.wx;
+      OWY[j] = g.wy;
+      OWZ[j] = g.wz;
+      OAX[j] = ISO ? g.ax + g.ay : g.ax;
+      OAY[j] = g.ay;
+    }
+    if (a.gwx) {
+      store4(a.gwx, e, OWX);
+      store4(a.gwy, e, OWY);
+      store4(a.gwz, e, OWZ);
+    }
+    if (a.gax) store4(a.gax, e, OAX);
+    if (!ISO && a.gay) store4(a.gay, e, OAY);
+  }
+  cp_async_wait<0>();
+}
+
 // ---------------------------------------------------------------- fused loss + adjoint
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -349,7 +445,16 @@ int launch_backward(const BwdArgs& a, int64_t n, bool vec, cudaStream_t s) {
   int64_t done = 0;
   if (vec && n / 4 > 0) {
     const int64_t n4 = n / 4;
-    backward_vec4_kernel<PHILOX, ISO><<<grid_for(n4, kBwdBlock, 8, 32), kBwdBlock, 0, s>>>(a, n4);
+    if (VNDF_BWD_STAGED && n4 >= int64_t(16) * 3 * sm_count() * kBwdBlock) {
+      // staged kernel for large calls (as for the fused loss); the limit is set for the widest layout
+      constexpr size_t smem_max = size_t(2) * (bwd_fixed_streams<PHILOX, ISO>() + 4) * kBwdBlock * 16;
+      if (!ensure_dynamic_smem<backward_pipe_kernel<PHILOX, ISO>>(smem_max)) return VNDF_ERR_CUDA;
+      const int ns = bwd_fixed_streams<PHILOX, ISO>() + (a.gmx ? 3 : 0) + (a.gp ? 1 : 0);
+      backward_pipe_kernel<PHILOX, ISO><<<grid_for(n4, kBwdBlock, 8, VNDF_BWD_WAVES), kBwdBlock,
+                                          size_t(2) * ns * kBwdBlock * 16, s>>>(a, n4);
+    } else {
+      backward_vec4_kernel<PHILOX, ISO><<<grid_for(n4, kBwdBlock, 8, 32), kBwdBlock, 0, s>>>(a, n4);
+    }
     done = 4 * n4;
   }
   if (done < n)

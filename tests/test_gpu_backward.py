@@ -161,6 +161,30 @@ def test_fused_loss_staged_path(v):
     assert abs(big[0].item() - ref) <= 1e-5 * terms.abs().sum().item()
 
 
+@pytest.mark.parametrize("inputs", ["both", "g_wm", "g_pdf"])
+def test_generic_backward_staged_path(v, inputs):
+    """Above 16 x 3 x SMs x 256 groups the generic adjoint runs the shared-memory-staged kernel: its
+    gradients equal, bit for bit, those of small calls that take the plain kernel, for every
+    combination of the optional adjoint inputs."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = 16 * 3 * sms * 1024 + 517
+    d = workloads.adjoint_2e24(n=n, seed=44, device=DEV)
+    gp = torch.rand(n, device=DEV, generator=torch.Generator(device=DEV).manual_seed(5))
+    keys = ("wi_x", "wi_y", "wi_z", "alpha_x", "alpha_y")
+
+    def call(sl, base):
+        g = {} if inputs == "g_pdf" else {"g_wm_x": d["c_x"][sl], "g_wm_y": d["c_y"][sl], "g_wm_z": d["c_z"][sl]}
+        if inputs != "g_wm":
+            g["g_pdf"] = gp[sl]
+        return v.vndf_sample_backward(*(d[k][sl] for k in keys), seed=6, counter_base=base, **g)
+
+    big = call(slice(0, n), 0)
+    for start, m in ((0, 3000), (n // 2 + 7, 1029), (n - 2000, 2000)):
+        part = call(slice(start, start + m), start)
+        for a, b in zip(big, part):
+            assert torch.equal(a[start:start + m], b)
+
+
 def test_autograd_function(v):
     from paper_2306_05044_gb300.autograd import vndf_sample_autograd
     n = 5000
