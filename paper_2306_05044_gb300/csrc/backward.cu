@@ -431,11 +431,12 @@ __global__ void __launch_bounds__(kBwdBlock, VNDF_BWD_MIN_BLOCKS) loss_backward_
 }
 
 // One block: thread t sums partials t, t + 1024, ... in order, then a fixed tree.
+// The unrolled loop keeps 32 loads per thread in flight; the adds stay in order.
 __global__ void __launch_bounds__(1024) sum_partials_kernel(const float* partials, int64_t m, float* out) {
   __shared__ float smem[32];
   float v = 0.f;
-#pragma unroll 8
-  for (int64_t j = threadIdx.x; j < m; j += 1024) v += partials[j];  // loads overlap; adds stay in order
+#pragma unroll 32
+  for (int64_t j = threadIdx.x; j < m; j += 1024) v += partials[j];
   const float s = block_sum<1024>(v, smem);
   if (threadIdx.x == 0) *out = s;
 }

@@ -136,10 +136,9 @@ __global__ void __launch_bounds__(kFitBlock) fit_kernel(FitArgs a) {
 __global__ void __launch_bounds__(1024) fit_finish_kernel(FitArgs a) {
   __shared__ float sm[32];
   float v = 0.f;
-  const int32_t per = (a.nt + 1023) / 1024;
-  const int32_t t0 = min(a.nt, int32_t(threadIdx.x) * per), t1 = min(a.nt, t0 + per);
+  // thread t sums texels t, t + 1024, ... in order (coalesced loads, 16 in flight), then a fixed tree
 #pragma unroll 16
-  for (int32_t t = t0; t < t1; ++t) v += a.texel_loss[t];  // loads overlap; adds stay in order
+  for (int32_t t = threadIdx.x; t < a.nt; t += 1024) v += a.texel_loss[t];
   v = warp_sum_fit(v);
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
   __syncthreads();
