@@ -61,14 +61,42 @@ def _worker(rank, world, port, out_dir):
         padded[: q1 - q0] = torch.from_numpy(e)
         parts = [torch.empty_like(padded) for _ in range(world)]
         dist.all_gather(parts, padded)
+        # fitting: texels split, stream base = first texel; the loss shares are summed over ranks
+        from oracle import fit as ofit
+        m = workloads.roughness_map(res=FIT_RES, seed=5)
+        t0, t1 = sharding.texel_shard(rank, world, FIT_RES * FIT_RES)
+        st, wi_t, tg = _fit_inputs(m, t0, t1)
+        losses = []
+        for step in (1, 2):
+            st, loss, _ = ofit.fit_step(st, wi_t, tg, FIT_SAMPLES, step, seed=7, stream_base=t0,
+                                        n_total=FIT_RES * FIT_RES)
+            losses.append(sharding.sum_over_ranks(loss))
+        ax_parts = [torch.zeros(FIT_RES * FIT_RES, dtype=torch.float64) for _ in range(world)]
+        ax_local = torch.zeros(FIT_RES * FIT_RES, dtype=torch.float64)
+        ax_local[: t1 - t0] = torch.from_numpy(st["ax"])
+        dist.all_gather(ax_parts, ax_local)
+        tcounts = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
+        dist.all_gather(tcounts, torch.tensor([t1 - t0]))
         # timing reduction
         t_max = sharding.max_over_ranks(1.0 + rank)
         if rank == 0:
             torch.save({"samples": torch.cat(gathered, dim=1),
                         "albedo": torch.cat([p[: int(c.item())] for p, c in zip(parts, counts)]),
-                        "t_max": t_max}, os.path.join(out_dir, "result.pt"))
+                        "fit_ax": torch.cat([p[: int(c.item())] for p, c in zip(ax_parts, tcounts)]),
+                        "fit_losses": losses, "t_max": t_max}, os.path.join(out_dir, "result.pt"))
     finally:
         dist.destroy_process_group()
+
+
+FIT_RES, FIT_SAMPLES = 3, 16
+
+
+def _fit_inputs(m, t0, t1):
+    st = {"ax": m["alpha_x"].numpy()[t0:t1].astype(np.float64), "ay": m["alpha_y"].numpy()[t0:t1].astype(np.float64)}
+    st.update({k: np.zeros(t1 - t0) for k in ("mx", "my", "vx", "vy")})
+    wi = np.stack([m[k].numpy()[t0:t1] for k in ("wi_x", "wi_y", "wi_z")]).astype(np.float64)
+    tg = np.stack([m[k].numpy()[t0:t1] for k in ("target_x", "target_y", "target_z")]).astype(np.float64)
+    return st, wi, tg
 
 
 def test_shards_concatenate_to_single_run(tmp_path):
@@ -88,6 +116,13 @@ def test_shards_concatenate_to_single_run(tmp_path):
     a = g["alpha_x"].numpy()
     e = microfacet.albedo_estimate(wi_q, a, a, g["n_samples"].numpy(), 0.04, seed=3)
     np.testing.assert_array_equal(res["albedo"].numpy(), e)
+    from oracle import fit as ofit
+    m = workloads.roughness_map(res=FIT_RES, seed=5)
+    st, wi_t, tg = _fit_inputs(m, 0, FIT_RES * FIT_RES)
+    for step in (1, 2):
+        st, loss, _ = ofit.fit_step(st, wi_t, tg, FIT_SAMPLES, step, seed=7)
+        assert abs(res["fit_losses"][step - 1] / loss - 1) < 1e-12
+    np.testing.assert_array_equal(res["fit_ax"].numpy(), st["ax"])
     assert res["t_max"] == 2.0
 
 
