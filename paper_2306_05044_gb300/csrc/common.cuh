@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "vndf.h"
@@ -25,17 +26,18 @@ inline bool all_aligned16(P... p) {
   return (... && (p == nullptr || aligned(p, 16)));
 }
 
-// Multiprocessor count of the current device (cached per device).
+// Multiprocessor count of the current device (cached per device; several host
+// threads may ask at once, and all of them store the same value).
 inline int sm_count() {
-  static int cache[64] = {0};
+  static std::atomic<int> cache[64];  // zero-initialised (static storage)
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
-  if (cache[dev] == 0) {
-    int v = 0;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v == 0) {
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
-    cache[dev] = v;
+    cache[dev].store(v, std::memory_order_relaxed);
   }
-  return cache[dev];
+  return v;
 }
 
 // Grid for a grid-stride loop over `work` items with `block` threads per CTA:
