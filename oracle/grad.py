@@ -19,16 +19,17 @@ H_CS = 1e-30
 INPUT_NAMES = ("wi_x", "wi_y", "wi_z", "alpha_x", "alpha_y")
 
 
-def _forward(u1, u2, wi, ax, ay, method="cap"):
-    wm = sample_vndf(u1, u2, wi, ax, ay, method)
-    pdf = vndf_pdf(wm, wi, ax, ay)
+def _forward(u1, u2, wi, ax, ay, method="cap", extended=False):
+    wm = sample_vndf(u1, u2, wi, ax, ay, method, extended)
+    pdf = vndf_pdf(wm, wi, ax, ay, extended)
     return np.concatenate([wm, pdf[None]], axis=0)  # (4, N): wm_x, wm_y, wm_z, pdf
 
 
-def jacobian_complex_step(u1, u2, wi, ax, ay, method="cap"):
+def jacobian_complex_step(u1, u2, wi, ax, ay, method="cap", extended=False):
     """d(wm_x, wm_y, wm_z, pdf)/d(input) for each input in INPUT_NAMES.
 
-    Returns an array of shape (5, 4, N): [input, output, sample].
+    Returns an array of shape (5, 4, N): [input, output, sample].  extended=True differentiates
+    the sampler and density on the extended domain (incident directions below the horizon).
     """
     base = [np.asarray(wi[0], np.float64), np.asarray(wi[1], np.float64),
             np.asarray(wi[2], np.float64), np.asarray(ax, np.float64), np.asarray(ay, np.float64)]
@@ -36,12 +37,12 @@ def jacobian_complex_step(u1, u2, wi, ax, ay, method="cap"):
     for k in range(5):
         args = [b.astype(np.complex128) for b in base]
         args[k] = args[k] + 1j * H_CS
-        f = _forward(u1, u2, args[:3], args[3], args[4], method)
+        f = _forward(u1, u2, args[:3], args[3], args[4], method, extended)
         out.append(np.imag(f) / H_CS)
     return np.stack(out)
 
 
-def jacobian_central_difference(u1, u2, wi, ax, ay, rel_step=1e-6, method="cap"):
+def jacobian_central_difference(u1, u2, wi, ax, ay, rel_step=1e-6, method="cap", extended=False):
     """Same Jacobian by central differences, step rel_step * max(1, |x|)."""
     base = [np.asarray(wi[0], np.float64), np.asarray(wi[1], np.float64),
             np.asarray(wi[2], np.float64), np.asarray(ax, np.float64), np.asarray(ay, np.float64)]
@@ -52,8 +53,8 @@ def jacobian_central_difference(u1, u2, wi, ax, ay, rel_step=1e-6, method="cap")
         minus = [b.copy() for b in base]
         plus[k] = plus[k] + step
         minus[k] = minus[k] - step
-        fp = _forward(u1, u2, plus[:3], plus[3], plus[4], method)
-        fm = _forward(u1, u2, minus[:3], minus[3], minus[4], method)
+        fp = _forward(u1, u2, plus[:3], plus[3], plus[4], method, extended)
+        fm = _forward(u1, u2, minus[:3], minus[3], minus[4], method, extended)
         out.append((fp - fm) / (2.0 * step))
     return np.stack(out)
 
@@ -67,12 +68,12 @@ def u_jacobian_complex_step(u1, u2, wi, ax, ay, extended=False):
     return d1, d2
 
 
-def vjp(u1, u2, wi, ax, ay, g_wm=None, g_pdf=None, isotropic=False):
+def vjp(u1, u2, wi, ax, ay, g_wm=None, g_pdf=None, isotropic=False, extended=False):
     """Vector-Jacobian product: (g_wi (3, N), g_alpha_x (N,), g_alpha_y (N,) or None).
 
     g_wm: (3, N) adjoint of wm (None = zero); g_pdf: (N,) adjoint of pdf (None = zero).
     With isotropic=True, alpha_y is alpha_x and the single alpha gradient is
-    returned as g_alpha_x (g_alpha_y is None).
+    returned as g_alpha_x (g_alpha_y is None).  extended=True: on the extended domain.
     """
     n = np.asarray(u1).shape[0]
     g = np.zeros((4, n))
@@ -80,7 +81,7 @@ def vjp(u1, u2, wi, ax, ay, g_wm=None, g_pdf=None, isotropic=False):
         g[:3] = np.asarray(g_wm, np.float64)
     if g_pdf is not None:
         g[3] = np.asarray(g_pdf, np.float64)
-    jac = jacobian_complex_step(u1, u2, wi, ax, ay)
+    jac = jacobian_complex_step(u1, u2, wi, ax, ay, extended=extended)
     grads = (jac * g[None]).sum(axis=1)  # (5, N)
     if isotropic:
         return grads[:3], grads[3] + grads[4], None

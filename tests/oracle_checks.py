@@ -471,3 +471,17 @@ def hemisphere_sampler_errors(n=20000, seed=28):
     ref, ref_pdf = vndf.sample_vndf_with_pdf(u1, u2, wi, one, one, extended=True)
     unit = np.abs(np.sqrt(vndf.dot(wm, wm)) - 1.0).max()
     return np.abs(wm - ref).max(), np.abs(pdf / ref_pdf - 1.0).max(), unit
+
+
+def extended_gradient_errors(n=400, seed=32):
+    """Below the horizon: complex step vs central differences (relative to the largest entry) and the
+    degree-0 homogeneity g_wi . wi = 0 of every output."""
+    u1, u2, wi, ax, ay = random_batch_extended(n, seed, alpha_lo=0.1, cos_lo=-0.7)
+    u2 = np.clip(u2, 1e-3, 1 - 1e-3)
+    jc = grad.jacobian_complex_step(u1, u2, wi, ax, ay, extended=True)
+    jf = grad.jacobian_central_difference(u1, u2, wi, ax, ay, extended=True)
+    scale = np.abs(jc).max(axis=0, keepdims=True) + 1e-12
+    e_fd = (np.abs(jc - jf) / scale).max()
+    e_hom = np.abs((jc[:3] * wi[:, None, :]).sum(axis=0)).max() / np.abs(jc).max()
+    below = (wi[2] < 0).mean()
+    return e_fd, e_hom, below

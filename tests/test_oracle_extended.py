@@ -128,3 +128,12 @@ def test_fp64_oracle_loses_digits_at_tiny_one_plus_zi():
     wm, pd = vndf.sample_vndf_with_pdf(np.array([0.3]), np.array([0.7]), wi.reshape(3, 1), np.ones(1), np.ones(1),
                                        extended=True)
     assert abs(pd[0] / p - 1) > 1e-7 and np.abs(wm[:, 0] - m).max() > 1e-7  # FP64: ~1e-6 off here
+
+
+def test_gradients_below_horizon():
+    """The complex-step derivative of the extended sampler and density against central differences, and
+    the degree-0 homogeneity in wi that every output has."""
+    e_fd, e_hom, below = oc.extended_gradient_errors()
+    assert below > 0.3
+    assert e_fd < 1e-6, e_fd
+    assert e_hom < 1e-12, e_hom
