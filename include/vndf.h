@@ -72,7 +72,8 @@ extern "C" {
  * reading of it.  Domain: alpha_x, alpha_y > 0, all finite, and
  * 1 + i.z >= 2^-40 (i at least about 1.4e-6 rad from straight down); outside
  * it the usual fallback.  For wi.z > 0 results equal VNDF_METHOD_SPHERICAL_CAP
- * bit for bit.  Accepted by vndf_sample only. */
+ * bit for bit.  Accepted by vndf_sample; its density at a given normal is
+ * vndf_pdf_extended and its adjoint vndf_sample_backward_extended. */
 #define VNDF_METHOD_SPHERICAL_CAP_EXTENDED 2
 
 /* Version of this ABI; bumped on any incompatible change. */
@@ -244,6 +245,26 @@ int vndf_sample_backward(int64_t n,
                          float *g_wi_x, float *g_wi_y, float *g_wi_z,
                          float *g_alpha_x, float *g_alpha_y,
                          void *cuda_stream);
+
+/*
+ * vndf_sample_backward_extended -- vndf_sample_backward for
+ * VNDF_METHOD_SPHERICAL_CAP_EXTENDED (incident directions below the horizon
+ * too; the extension is a reading of Sec. 3.2-3.3 and Eq. 4, see that method):
+ * the same vector-Jacobian product of (wm, pdf), with the pdf of
+ * vndf_pdf_extended, on the extended domain.  Same arguments, layout and
+ * errors as vndf_sample_backward; samples outside the extended domain get
+ * zero gradients.
+ */
+int vndf_sample_backward_extended(int64_t n,
+                                  const float *wi_x, const float *wi_y, const float *wi_z,
+                                  const float *alpha_x, const float *alpha_y,
+                                  const float *u1, const float *u2,
+                                  uint64_t seed, uint64_t counter_base, uint32_t stream_id,
+                                  const float *g_wm_x, const float *g_wm_y, const float *g_wm_z,
+                                  const float *g_pdf,
+                                  float *g_wi_x, float *g_wi_y, float *g_wi_z,
+                                  float *g_alpha_x, float *g_alpha_y,
+                                  void *cuda_stream);
 
 /* Device workspace (bytes) that vndf_sample_loss_backward needs for n samples:
  * one float per 128-sample group.  0 for n <= 0. */

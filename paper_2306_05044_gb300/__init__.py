@@ -44,6 +44,8 @@ SIGNATURES = {
                                               _P, _P, _P, _P, _P, _P]),
     "vndf_sample_backward": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _U64, _U64, _U32,
                                             _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "vndf_sample_backward_extended": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _U64, _U64, _U32,
+                                            _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "vndf_loss_workspace_bytes": (_SZ, [_I64]),
     "vndf_sample_loss_backward": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _U64, _U64, _U32,
                                                  _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
@@ -248,8 +250,9 @@ def vndf_sample_hemisphere(wi_x, wi_y, wi_z, u1=None, u2=None, seed=0, counter_b
 
 def vndf_sample_backward(wi_x, wi_y, wi_z, alpha_x, alpha_y=None, u1=None, u2=None, seed=0, counter_base=0,
                          stream_id=0, g_wm_x=None, g_wm_y=None, g_wm_z=None, g_pdf=None, want_wi=True,
-                         want_alpha=True, n=None, stream=None):
-    """Gradients of (wm, pdf) w.r.t. (wi, alpha) for fixed u; see vndf_sample_backward in include/vndf.h.
+                         want_alpha=True, n=None, stream=None, extended=False):
+    """Gradients of (wm, pdf) w.r.t. (wi, alpha) for fixed u; see vndf_sample_backward (and, with
+    extended=True, vndf_sample_backward_extended) in include/vndf.h.
 
     Returns (g_wi_x, g_wi_y, g_wi_z, g_alpha_x, g_alpha_y); entries not requested are None.
     With alpha_y=None (isotropic) g_alpha_x holds d/d alpha and g_alpha_y is None.
@@ -258,15 +261,21 @@ def vndf_sample_backward(wi_x, wi_y, wi_z, alpha_x, alpha_y=None, u1=None, u2=No
     g_wi = [_out(None, n, wi_x) for _ in range(3)] if want_wi else [None, None, None]
     g_ax = _out(None, n, wi_x) if want_alpha else None
     g_ay = _out(None, n, wi_x) if (want_alpha and alpha_y is not None) else None
-    st = load().vndf_sample_backward(
+    name = "vndf_sample_backward_extended" if extended else "vndf_sample_backward"
+    st = getattr(load(), name)(
         n, _ptr(wi_x, "wi_x"), _ptr(wi_y, "wi_y"), _ptr(wi_z, "wi_z"), _ptr(alpha_x, "alpha_x"),
         _ptr(alpha_y, "alpha_y"), _ptr(u1, "u1"), _ptr(u2, "u2"), int(seed) & (2**64 - 1),
         int(counter_base) & (2**64 - 1), int(stream_id) & 0xFFFFFFFF, _ptr(g_wm_x, "g_wm_x"),
         _ptr(g_wm_y, "g_wm_y"), _ptr(g_wm_z, "g_wm_z"), _ptr(g_pdf, "g_pdf"), _ptr(g_wi[0], "g_wi_x"),
         _ptr(g_wi[1], "g_wi_y"), _ptr(g_wi[2], "g_wi_z"), _ptr(g_ax, "g_alpha_x"), _ptr(g_ay, "g_alpha_y"),
         _stream(stream, wi_x.device))
-    _check("vndf_sample_backward", st)
+    _check(name, st)
     return g_wi[0], g_wi[1], g_wi[2], g_ax, g_ay
+
+
+def vndf_sample_backward_extended(*args, **kwargs):
+    """vndf_sample_backward on the extended domain (wi below the horizon too); see include/vndf.h."""
+    return vndf_sample_backward(*args, extended=True, **kwargs)
 
 
 def vndf_loss_workspace_bytes(n):

@@ -46,7 +46,7 @@ __device__ __forceinline__ void store4(float* p, int64_t e, const float (&d)[4])
   st_stream(p + e, *reinterpret_cast<const float4*>(d));
 }
 
-template <bool PHILOX, bool ISO>
+template <bool PHILOX, bool ISO, bool EXT>
 __global__ void __launch_bounds__(kBwdBlock, 3) backward_vec4_kernel(BwdArgs a, int64_t n4) {
   const int64_t stride = int64_t(gridDim.x) * kBwdBlock;
   for (int64_t q = int64_t(blockIdx.x) * kBwdBlock + threadIdx.x; q < n4; q += stride) {
@@ -80,8 +80,8 @@ __global__ void __launch_bounds__(kBwdBlock, 3) backward_vec4_kernel(BwdArgs a, 
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       float mx, my, mz, pdf;
-      const Grad5 g = cap_backward_one(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], GX[k], GY[k], GZ[k], GP[k],
-                                       0.f, mx, my, mz, pdf);
+      const Grad5 g = cap_backward_one<true, EXT>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], GX[k], GY[k],
+                                                  GZ[k], GP[k], 0.f, mx, my, mz, pdf);
       OWX[k] = g.wx;
       OWY[k] = g.wy;
       OWZ[k] = g.wz;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kBwdBlock, 3) backward_vec4_kernel(BwdArgs a, 
   }
 }
 
-template <bool PHILOX, bool ISO>
+template <bool PHILOX, bool ISO, bool EXT>
 __global__ void __launch_bounds__(kBwdBlock) backward_scalar_kernel(BwdArgs a, int64_t begin, int64_t n) {
   const int64_t stride = int64_t(gridDim.x) * kBwdBlock;
   for (int64_t e = begin + int64_t(blockIdx.x) * kBwdBlock + threadIdx.x; e < n; e += stride) {
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kBwdBlock) backward_scalar_kernel(BwdArgs a, i
     }
     const float gx = a.gmx ? a.gmx[e] : 0.f, gy = a.gmx ? a.gmy[e] : 0.f, gz = a.gmx ? a.gmz[e] : 0.f;
     float mx, my, mz, pdf;
-    const Grad5 g = cap_backward_one(a.wx[e], a.wy[e], a.wz[e], ax, ay, u1, u2, gx, gy, gz,
+    const Grad5 g = cap_backward_one<true, EXT>(a.wx[e], a.wy[e], a.wz[e], ax, ay, u1, u2, gx, gy, gz,
                                      a.gp ? a.gp[e] : 0.f, 0.f, mx, my, mz, pdf);
     if (a.gwx) {
       a.gwx[e] = g.wx;
@@ -154,7 +154,7 @@ __device__ __forceinline__ void bwd_stage(const BwdArgs& a, int64_t e, float4* s
   if (has_p) cp_async16(slot + k * kBwdBlock, a.gp + e);
 }
 
-template <bool PHILOX, bool ISO>
+template <bool PHILOX, bool ISO, bool EXT>
 __global__ void __launch_bounds__(kBwdBlock, VNDF_BWD_MIN_BLOCKS) backward_pipe_kernel(BwdArgs a, int64_t n4) {
   constexpr int kFixed = bwd_fixed_streams<PHILOX, ISO>();
   const bool has_g = a.gmx != nullptr, has_p = a.gp != nullptr;
@@ -202,8 +202,8 @@ __global__ void __launch_bounds__(kBwdBlock, VNDF_BWD_MIN_BLOCKS) backward_pipe_
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       float mx, my, mz, pdf;
-      const Grad5 g = cap_backward_one(X[j], Y[j], Z[j], AX[j], AY[j], U1[j], U2[j], GX[j], GY[j], GZ[j], GP[j],
-                                       0.f, mx, my, mz, pdf);
+      const Grad5 g = cap_backward_one<true, EXT>(X[j], Y[j], Z[j], AX[j], AY[j], U1[j], U2[j], GX[j], GY[j],
+                                                  GZ[j], GP[j], 0.f, mx, my, mz, pdf);
       OWX[j] = g.wx;
       OWY[j] = g.wy;
       OWZ[j] = g.wz;
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(1024) sum_partials_kernel(const float* partial
   if (threadIdx.x == 0) *out = s;
 }
 
-template <bool PHILOX, bool ISO>
+template <bool PHILOX, bool ISO, bool EXT>
 int launch_backward(const BwdArgs& a, int64_t n, bool vec, cudaStream_t s) {
   int64_t done = 0;
   if (vec && n / 4 > 0) {
@@ -449,17 +449,18 @@ int launch_backward(const BwdArgs& a, int64_t n, bool vec, cudaStream_t s) {
     if (VNDF_BWD_STAGED && n4 >= int64_t(16) * 3 * sm_count() * kBwdBlock) {
       // staged kernel for large calls (as for the fused loss); the limit is set for the widest layout
       constexpr size_t smem_max = size_t(2) * (bwd_fixed_streams<PHILOX, ISO>() + 4) * kBwdBlock * 16;
-      if (!ensure_dynamic_smem<backward_pipe_kernel<PHILOX, ISO>>(smem_max)) return VNDF_ERR_CUDA;
+      if (!ensure_dynamic_smem<backward_pipe_kernel<PHILOX, ISO, EXT>>(smem_max)) return VNDF_ERR_CUDA;
       const int ns = bwd_fixed_streams<PHILOX, ISO>() + (a.gmx ? 3 : 0) + (a.gp ? 1 : 0);
-      backward_pipe_kernel<PHILOX, ISO><<<grid_for(n4, kBwdBlock, 8, VNDF_BWD_WAVES), kBwdBlock,
-                                          size_t(2) * ns * kBwdBlock * 16, s>>>(a, n4);
+      backward_pipe_kernel<PHILOX, ISO, EXT><<<grid_for(n4, kBwdBlock, 8, VNDF_BWD_WAVES), kBwdBlock,
+                                               size_t(2) * ns * kBwdBlock * 16, s>>>(a, n4);
     } else {
-      backward_vec4_kernel<PHILOX, ISO><<<grid_for(n4, kBwdBlock, 8, 32), kBwdBlock, 0, s>>>(a, n4);
+      backward_vec4_kernel<PHILOX, ISO, EXT><<<grid_for(n4, kBwdBlock, 8, 32), kBwdBlock, 0, s>>>(a, n4);
     }
     done = 4 * n4;
   }
   if (done < n)
-    backward_scalar_kernel<PHILOX, ISO><<<grid_for(n - done, kBwdBlock, 8, 32), kBwdBlock, 0, s>>>(a, done, n);
+    backward_scalar_kernel<PHILOX, ISO, EXT>
+        <<<grid_for(n - done, kBwdBlock, 8, 32), kBwdBlock, 0, s>>>(a, done, n);
   return launch_status();
 }
 
@@ -494,12 +495,13 @@ int launch_loss(const BwdArgs& a, int64_t n, bool vec, float* partials, float* l
 
 using namespace vndf;
 
-extern "C" int vndf_sample_backward(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z,
-                                    const float* alpha_x, const float* alpha_y, const float* u1, const float* u2,
-                                    uint64_t seed, uint64_t counter_base, uint32_t stream_id, const float* g_wm_x,
-                                    const float* g_wm_y, const float* g_wm_z, const float* g_pdf, float* g_wi_x,
-                                    float* g_wi_y, float* g_wi_z, float* g_alpha_x, float* g_alpha_y,
-                                    void* cuda_stream) {
+namespace vndf {
+template <bool EXT>
+int backward_entry(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z, const float* alpha_x,
+                   const float* alpha_y, const float* u1, const float* u2, uint64_t seed, uint64_t counter_base,
+                   uint32_t stream_id, const float* g_wm_x, const float* g_wm_y, const float* g_wm_z,
+                   const float* g_pdf, float* g_wi_x, float* g_wi_y, float* g_wi_z, float* g_alpha_x,
+                   float* g_alpha_y, void* cuda_stream) {
   if (n < 0 || n >= kMaxN) return VNDF_ERR_SIZE;
   if (n == 0) return VNDF_OK;
   if (!wi_x || !wi_y || !wi_z || !alpha_x) return VNDF_ERR_NULL;
@@ -519,8 +521,30 @@ extern "C" int vndf_sample_backward(int64_t n, const float* wi_x, const float* w
                                  g_wi_x, g_wi_y, g_wi_z, g_alpha_x, g_alpha_y);
   const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   if (u1)
-    return alpha_y ? launch_backward<false, false>(a, n, vec, s) : launch_backward<false, true>(a, n, vec, s);
-  return alpha_y ? launch_backward<true, false>(a, n, vec, s) : launch_backward<true, true>(a, n, vec, s);
+    return alpha_y ? launch_backward<false, false, EXT>(a, n, vec, s)
+                   : launch_backward<false, true, EXT>(a, n, vec, s);
+  return alpha_y ? launch_backward<true, false, EXT>(a, n, vec, s) : launch_backward<true, true, EXT>(a, n, vec, s);
+}
+}  // namespace vndf
+
+extern "C" int vndf_sample_backward(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z,
+                                    const float* alpha_x, const float* alpha_y, const float* u1, const float* u2,
+                                    uint64_t seed, uint64_t counter_base, uint32_t stream_id, const float* g_wm_x,
+                                    const float* g_wm_y, const float* g_wm_z, const float* g_pdf, float* g_wi_x,
+                                    float* g_wi_y, float* g_wi_z, float* g_alpha_x, float* g_alpha_y,
+                                    void* cuda_stream) {
+  return backward_entry<false>(n, wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, seed, counter_base, stream_id, g_wm_x,
+                               g_wm_y, g_wm_z, g_pdf, g_wi_x, g_wi_y, g_wi_z, g_alpha_x, g_alpha_y, cuda_stream);
+}
+
+extern "C" int vndf_sample_backward_extended(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z,
+                                             const float* alpha_x, const float* alpha_y, const float* u1,
+                                             const float* u2, uint64_t seed, uint64_t counter_base,
+                                             uint32_t stream_id, const float* g_wm_x, const float* g_wm_y,
+                                             const float* g_wm_z, const float* g_pdf, float* g_wi_x, float* g_wi_y,
+                                             float* g_wi_z, float* g_alpha_x, float* g_alpha_y, void* cuda_stream) {
+  return backward_entry<true>(n, wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, seed, counter_base, stream_id, g_wm_x,
+                              g_wm_y, g_wm_z, g_pdf, g_wi_x, g_wi_y, g_wi_z, g_alpha_x, g_alpha_y, cuda_stream);
 }
 
 extern "C" size_t vndf_loss_workspace_bytes(int64_t n) {

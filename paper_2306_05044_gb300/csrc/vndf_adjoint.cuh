@@ -31,20 +31,27 @@ struct Grad5 {
 // Adjoint of (wm, pdf) for one sample.  gmx, gmy, gmz: adjoint of wm; gpdf:
 // adjoint of pdf; glog: adjoint of log(pdf).  Also returns the forward values.
 // With PDF_TERMS = false the pdf adjoints are taken as zero at compile time and
-// the returned pdf is not computed (0).
-template <bool PDF_TERMS = true>
+// the returned pdf is not computed (0).  With EXT, the extended domain of
+// kMethodCapExt (incident directions below the horizon): a = 1 + i.z is then
+// formed as (i.x^2 + i.y^2) / (1 - i.z) when i.z < 0, and da / di.z = 1 either way.
+template <bool PDF_TERMS = true, bool EXT = false>
 __device__ __forceinline__ Grad5 cap_backward_one(float wx, float wy, float wz, float ax, float ay, float u1,
                                                   float u2, float gmx, float gmy, float gmz, float gpdf,
                                                   float glog, float& mx, float& my, float& mz, float& pdf) {
-  const bool ok = in_domain(wx, wy, wz, ax, ay);
+  bool ok = EXT ? in_domain_ext_inputs(wx, wy, wz, ax, ay) : in_domain(wx, wy, wz, ax, ay);
   // ---- forward (as in sample_one<cap>)
   const float sx = ax * wx, sy = ay * wy;
   const float l2 = fmaf(sx, sx, fmaf(sy, sy, wz * wz));
   const float r = rsqrtf(l2);
   const float ix = sx * r, iy = sy * r, iz = wz * r;
-  const float a = 1.f + iz;
-  const float om = 1.f - u2;
   const float rho2 = fmaf(ix, ix, iy * iy);
+  const float a_up = __fadd_rn(1.f, iz);
+  float a = a_up;
+  if constexpr (EXT) {
+    if (iz < 0.f) a = __fdividef(rho2, 1.f - iz);
+    ok &= a >= kMinCapA;
+  }
+  const float om = 1.f - u2;
   const float S = fmaf(2.f * a, om, u2 * rho2);
   // st = sqrt(u2 S) and d st / dS = u2 / (2 st) from one rsqrt; both are 0 at u2 = 0
   const float q = u2 * S;

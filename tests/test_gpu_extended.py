@@ -12,7 +12,7 @@ import torch
 
 import parity
 import workloads
-from oracle import philox, vndf as ovndf
+from oracle import grad, philox, vndf as ovndf
 
 pytestmark = pytest.mark.gpu
 
@@ -198,3 +198,74 @@ def test_full_size_sphere_stream_sampled(v):
     print("full size sphere sampled", st)
     del d, out
     torch.cuda.empty_cache()
+
+
+def _sphere_adjoint_inputs(n, seed):
+    """The sphere workload with roughness kept >= 1e-2 (where FP32 gradients have a useful condition)."""
+    d = workloads.sphere_stream(n=n, seed=seed, device=DEV)
+    for k in ("alpha_x", "alpha_y"):
+        d[k] = torch.clamp(d[k], min=1e-2).contiguous()
+    return d
+
+
+@pytest.mark.parametrize("iso", [False, True])
+def test_backward_extended_matches_complex_step(v, iso):
+    """vndf_sample_backward_extended against the oracle's complex-step vector-Jacobian product on the
+    extended domain (about half the samples below the horizon)."""
+    n = (1 << 13) + 3
+    d = _sphere_adjoint_inputs(n, 51)
+    ay = None if iso else d["alpha_y"]
+    g = torch.randn(4, n, device=DEV, generator=torch.Generator(device=DEV).manual_seed(3))
+    got = v.vndf_sample_backward_extended(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], ay, seed=12,
+                                          g_wm_x=g[0].contiguous(), g_wm_y=g[1].contiguous(),
+                                          g_wm_z=g[2].contiguous(), g_pdf=g[3].contiguous())
+    u1, u2 = philox.sample_uniforms(12, 0, 0, n)
+    wi = np.stack([d[k].cpu().numpy().astype(np.float64) for k in ("wi_x", "wi_y", "wi_z")])
+    ax = d["alpha_x"].cpu().numpy().astype(np.float64)
+    ayn = ax if iso else d["alpha_y"].cpu().numpy().astype(np.float64)
+    gn = g.cpu().numpy().astype(np.float64)
+    keep = parity.one_plus_zi(wi, ax, ayn) >= 1e-6  # where the FP64 oracle is itself accurate
+    rwi, rax, ray = grad.vjp(u1, u2, wi, ax, ayn, gn[:3], gn[3], isotropic=iso, extended=True)
+    ref = np.concatenate([rwi, rax[None]] + ([] if iso else [ray[None]]))
+    outs = [got[0], got[1], got[2], got[3]] + ([] if iso else [got[4]])
+    mine = np.stack([t.cpu().numpy().astype(np.float64) for t in outs])
+    scale = np.abs(ref).max(axis=0)
+    e = (np.abs(mine - ref).max(axis=0) / np.maximum(scale, 1e-30))[keep]
+    print(f"extended adjoint iso={iso}: median {np.median(e):.2e} p99.9 {np.quantile(e, 0.999):.2e} "
+          f"max {e.max():.2e} below-horizon {(wi[2] < 0).mean():.2f}")
+    assert (wi[2][keep] < 0).mean() > 0.3
+    assert np.median(e) < 1e-5
+    assert np.quantile(e, 0.999) < 1e-3
+
+
+def test_backward_extended_equals_upper_above_horizon(v):
+    """Above the horizon the extended adjoint is the upper-hemisphere adjoint bit for bit; below it the
+    upper one returns zero gradients."""
+    n = 20001
+    d = _sphere_adjoint_inputs(n, 52)
+    keys = ("wi_x", "wi_y", "wi_z", "alpha_x", "alpha_y")
+    gpdf = torch.rand(n, device=DEV, generator=torch.Generator(device=DEV).manual_seed(4))
+    a = v.vndf_sample_backward(*(d[k] for k in keys), seed=3, g_pdf=gpdf)
+    b = v.vndf_sample_backward_extended(*(d[k] for k in keys), seed=3, g_pdf=gpdf)
+    up = d["wi_z"] > 0
+    for x, y in zip(a, b):
+        assert torch.equal(x[up], y[up])
+        assert torch.all(x[~up] == 0)
+    assert torch.any(b[2][~up] != 0)
+
+
+def test_autograd_extended(v):
+    """The autograd wrapper with extended=True reaches the extended adjoint."""
+    from paper_2306_05044_gb300.autograd import vndf_sample_autograd
+    n = 4099
+    d = _sphere_adjoint_inputs(n, 53)
+    keys = ("wi_x", "wi_y", "wi_z", "alpha_x", "alpha_y")
+    leaves = {k: d[k].clone().requires_grad_(True) for k in keys}
+    wm_x, wm_y, wm_z, pdf = vndf_sample_autograd(*(leaves[k] for k in keys), seed=5, extended=True)
+    c = torch.randn(3, n, device=DEV, generator=torch.Generator(device=DEV).manual_seed(6))
+    (c[0] * wm_x + c[1] * wm_y + c[2] * wm_z + pdf).sum().backward()
+    ref = v.vndf_sample_backward_extended(*(d[k] for k in keys), seed=5, g_wm_x=c[0].contiguous(),
+                                          g_wm_y=c[1].contiguous(), g_wm_z=c[2].contiguous(),
+                                          g_pdf=torch.ones(n, device=DEV))
+    for k, r in zip(keys, ref):
+        assert torch.equal(leaves[k].grad, r)
