@@ -115,11 +115,14 @@ __device__ __forceinline__ Grad5 cap_backward_one(float wx, float wy, float wz, 
   g_iy = fmaf(2.f * iy, g_rho2, g_iy);
   // a = 1 + iz
   const float g_iz = g_a;
-  // i = s / |s|
-  const float idot = fmaf(g_ix, ix, fmaf(g_iy, iy, g_iz * iz));
+  // i = s / |s|: g_s = (g_i - i (i . g_i)) / |s|.  Its z part is written as
+  // g_iz (1 - i.z^2) - i.z (i.x g_ix + i.y g_iy) with 1 - i.z^2 = i.x^2 + i.y^2:
+  // near straight down, g_iz grows like 1 / (1 + i.z) and the plain form cancels.
+  const float gxy = fmaf(g_ix, ix, g_iy * iy);
+  const float idot = fmaf(g_iz, iz, gxy);
   const float g_sx = fmaf(-ix, idot, g_ix) * r;
   const float g_sy = fmaf(-iy, idot, g_iy) * r;
-  const float g_sz = fmaf(-iz, idot, g_iz) * r;
+  const float g_sz = fmaf(g_iz, rho2, -iz * gxy) * r;
   // s = (ax wx, ay wy, wz)
   Grad5 g;
   g.wx = ax * g_sx;
