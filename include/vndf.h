@@ -444,9 +444,9 @@ int vndf_microbench(int64_t lanes, int32_t samples_per_lane, int method, int pre
  * benchmark (Sec. 4, "CPU Synthetic Benchmark", which calls the sampler in a
  * loop).  An explicit host entry point, not a fallback of vndf_sample: all
  * pointers are HOST memory, uniforms are explicit, and the arithmetic is FP32
- * with the same rounding-aware formulas as the GPU kernels (both methods),
- * vectorised by the compiler and split over `threads` host threads (0 = all
- * hardware threads).  Results do not depend on the thread count.  It has no
+ * with the same rounding-aware formulas as the GPU kernels, vectorised by the
+ * compiler and split over `threads` host threads (0 = all hardware threads).
+ * method is any VNDF_METHOD_* (the extended cap method as in vndf_sample).  Results do not depend on the thread count.  It has no
  * double-float path, so, like the prior sampler, about 1e-5 of samples lie
  * beyond 4e-6 rad of an FP64 evaluation.
  * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, METHOD).

@@ -1,5 +1,6 @@
 // Host (CPU) implementation of both hemisphere samplers wrapped in the GGX
-// VNDF routine, for the paper's CPU benchmark (Sec. 4, "CPU Synthetic
+// VNDF routine (the cap sampler also on the extended domain), for the paper's
+// CPU benchmark (Sec. 4, "CPU Synthetic
 // Benchmark": the sampler called in a loop, median time over 100 runs).
 // It is an explicit entry point for host callers, never a fallback of the GPU
 // entry points.  Plain portable C++17: FP32 arithmetic written branch-free so
@@ -50,8 +51,11 @@ __attribute__((always_inline)) inline void sincospi_taylor_host(float x, float& 
 template <int METHOD>
 __attribute__((always_inline)) inline void sample_host(float wx, float wy, float wz, float ax, float ay, float u1, float u2, float& mx, float& my,
                         float& mz, float& pdf) {
-  const bool ok = (wz > 0.f) & (ax > 0.f) & (ay > 0.f) & std::isfinite(wx) & std::isfinite(wy) &
-                  std::isfinite(wz) & std::isfinite(ax) & std::isfinite(ay);
+  constexpr bool kExt = METHOD == VNDF_METHOD_SPHERICAL_CAP_EXTENDED;
+  constexpr bool kCap = METHOD != VNDF_METHOD_POLAR_DISK;
+  // the upper domain needs wi.z > 0; the extended one 1 + z_i' >= 2^-40, tested once a is formed
+  bool ok = (kExt | (wz > 0.f)) & (ax > 0.f) & (ay > 0.f) & std::isfinite(wx) & std::isfinite(wy) &
+            std::isfinite(wz) & std::isfinite(ax) & std::isfinite(ay);
   // keep the arithmetic finite on out-of-domain lanes (their results are replaced below)
   wz = ok ? wz : 1.f;
   ax = ok ? ax : 1.f;
@@ -63,20 +67,25 @@ __attribute__((always_inline)) inline void sample_host(float wx, float wy, float
   const float l2 = std::fma(sx, sx, std::fma(sy, sy, wz * wz));
   const float rl = 1.f / std::sqrt(l2);
   const float ix = sx * rl, iy = sy * rl, iz = wz * rl;
-  const float a = 1.f + iz;
+  const float rho2 = std::fma(ix, ix, iy * iy);  // 1 - i.z^2
+  // a = 1 + i.z; below the horizon rho2 / (1 - i.z), which does not cancel
+  float a = 1.f + iz;
+  if constexpr (kExt) {
+    a = iz < 0.f ? rho2 / (1.f - iz) : a;
+    ok &= a >= 0x1p-40f;
+  }
   float sp, cp;
   sincospi_taylor_host(2.f * u1, sp, cp);
   float hx, hy, hz;
-  if constexpr (METHOD == VNDF_METHOD_SPHERICAL_CAP) {
+  if constexpr (kCap) {
     // Sec. 3.3: c on the cap z in (-i.z, 1], h = c + i
-    const float rho2 = std::fma(ix, ix, iy * iy);
     const float st = std::sqrt(u2 * std::fma(2.f * a, 1.f - u2, u2 * rho2));
     hx = std::fma(st, cp, ix);
     hy = std::fma(st, sp, iy);
     hz = (1.f - u2) * a;
   } else {
     // Heitz 2018 cross-section sampler (Sec. 2 step (2))
-    const float tmp = std::fma(ix, ix, iy * iy);
+    const float tmp = rho2;
     const bool pole = !(tmp > 0.f);
     const float rt = 1.f / std::sqrt(pole ? 1.f : tmp);
     const float w1x = pole ? 1.f : -iy * rt, w1y = pole ? 0.f : ix * rt;
@@ -105,7 +114,7 @@ __attribute__((always_inline)) inline void sample_host(float wx, float wy, float
   my = ok ? vy * rv : 0.f;
   mz = ok ? vz * rv : 1.f;
   float p;
-  if constexpr (METHOD == VNDF_METHOD_SPHERICAL_CAP) {
+  if constexpr (kCap) {
     const float hh = std::fma(hx, hx, std::fma(hy, hy, hz * hz));
     p = vv * nv / (kPiF * ax * ay * a * hh);
   } else {
@@ -140,13 +149,18 @@ extern "C" int vndf_cpu_sample(int64_t n, const float* wi_x, const float* wi_y, 
                                const float* alpha_x, const float* alpha_y, const float* u1, const float* u2,
                                int method, float* wm_x, float* wm_y, float* wm_z, float* pdf, int threads) {
   if (n < 0 || n >= (int64_t(1) << 62)) return VNDF_ERR_SIZE;
-  if (method != VNDF_METHOD_SPHERICAL_CAP && method != VNDF_METHOD_POLAR_DISK) return VNDF_ERR_METHOD;
+  if (method != VNDF_METHOD_SPHERICAL_CAP && method != VNDF_METHOD_POLAR_DISK &&
+      method != VNDF_METHOD_SPHERICAL_CAP_EXTENDED)
+    return VNDF_ERR_METHOD;
   if (n == 0) return VNDF_OK;
   if (!wi_x || !wi_y || !wi_z || !alpha_x || !u1 || !u2 || !wm_x || !wm_y || !wm_z) return VNDF_ERR_NULL;
   const HostArgs h{wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, wm_x, wm_y, wm_z, pdf};
   auto body = [&](int64_t i0, int64_t i1) {
     if (method == VNDF_METHOD_SPHERICAL_CAP)
       pdf ? run_range<VNDF_METHOD_SPHERICAL_CAP, true>(h, i0, i1) : run_range<VNDF_METHOD_SPHERICAL_CAP, false>(h, i0, i1);
+    else if (method == VNDF_METHOD_SPHERICAL_CAP_EXTENDED)
+      pdf ? run_range<VNDF_METHOD_SPHERICAL_CAP_EXTENDED, true>(h, i0, i1)
+          : run_range<VNDF_METHOD_SPHERICAL_CAP_EXTENDED, false>(h, i0, i1);
     else
       pdf ? run_range<VNDF_METHOD_POLAR_DISK, true>(h, i0, i1) : run_range<VNDF_METHOD_POLAR_DISK, false>(h, i0, i1);
   };

@@ -1,0 +1,126 @@
+"""Writes cap_samples_mp50.txt: stored expected samples of the spherical-cap sampler.
+
+Every expected value comes from the oracle alone: the 50-digit evaluation of
+Sec. 2 steps (1)-(3) with the Sec. 3.3 cap sampler and the density of Eq. 1
+(``oracle.vndf_mp.sample_with_pdf``), and, for inputs outside the sampler's
+domain, the fallback the oracle defines (``oracle.vndf.in_domain``; normal
+(0, 0, 1), density 0).  Nothing here calls the CUDA library.
+
+The inputs are fixed float32 values chosen to reach the places where a
+plausible mistake shows: normal incidence, grazing and below-horizon incident
+directions, roughness from 1e-6 to 1.5, strong anisotropy, unnormalised wi,
+and uniforms at the ends of [0, 1) (the cap's top at u2 = 0, its rim as
+u2 -> 1, phi -> 2 pi as u1 -> 1).
+
+Run from the repository root:  python tests/golden/make_golden.py
+"""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from oracle import vndf, vndf_mp  # noqa: E402
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "cap_samples_mp50.txt")
+ONE_M = 1.0 - 2.0 ** -24  # largest float32 uniform below 1
+TINY_U = 2.0 ** -24
+
+# kind, wi (x, y, z), alpha (x, y), u (1, 2), what the row exercises
+CASES = [
+    ("cap", (0.0, 0.0, 1.0), (1.0, 1.0), (0.0, 0.0), "alpha = 1 at normal incidence, cap top: wm = (0, 0, 1), pdf = 1/pi"),
+    ("cap", (0.0, 0.0, 1.0), (0.5, 0.5), (0.25, 0.5), "normal incidence, isotropic"),
+    ("cap", (0.6, 0.0, 0.8), (0.3, 0.3), (0.125, 0.75), "oblique, isotropic"),
+    ("cap", (0.3, -0.4, 0.8660254), (0.05, 0.8), (0.7, 0.2), "anisotropic"),
+    ("cap", (1.0, 0.0, 1e-3), (0.2, 0.2), (0.5, 0.5), "grazing wi.z = 1e-3"),
+    ("cap", (0.6, 0.8, 1e-5), (0.5, 0.05), (0.9, 0.99), "grazing wi.z = 1e-5, anisotropic, near the rim"),
+    ("cap", (0.5, 0.5, 0.70710678), (1e-4, 1e-4), (0.9, 0.1), "alpha = 1e-4"),
+    ("cap", (0.8, 0.0, 0.6), (1.0, 1.0), (0.3, ONE_M), "alpha = 1, u2 at its largest (the rim)"),
+    ("cap", (0.0, 0.99, 0.1), (1e-3, 1.0), (0.6, 0.4), "alpha_x / alpha_y = 1e-3"),
+    ("cap", (-0.2, 0.5, 0.8), (1.5, 0.7), (0.05, 0.95), "alpha above 1"),
+    ("cap", (3.0, -4.0, 12.0), (0.4, 0.4), (0.33, 0.66), "unnormalised wi, length 13"),
+    ("cap", (0.1, 0.2, 0.97), (0.6, 0.3), (ONE_M, TINY_U), "u1 at its largest, u2 at its smallest non-zero"),
+    ("cap", (-0.7, -0.1, 0.3), (0.02, 0.02), (0.37, 0.81), "small alpha, wi in the third quadrant"),
+    ("cap", (0.5, 0.5, 0.0), (0.5, 0.5), (0.5, 0.5), "outside the domain: wi.z = 0"),
+    ("cap", (0.6, 0.0, -0.8), (0.3, 0.3), (0.4, 0.6), "outside the domain: below the horizon"),
+    ("cap", (0.0, 0.0, 1.0), (0.0, 0.5), (0.5, 0.5), "outside the domain: alpha_x = 0"),
+    ("cap_extended", (0.6, 0.0, -0.8), (0.3, 0.3), (0.4, 0.6), "below the horizon, 1 + z_i' = 0.024"),
+    ("cap_extended", (0.0, 0.8, -0.6), (0.01, 0.01), (0.2, 0.3), "below the horizon, 1 + z_i' = 9e-5"),
+    ("cap_extended", (1.0, 0.0, -0.1), (1e-3, 1e-3), (0.75, 0.5), "below the horizon, 1 + z_i' = 5e-5"),
+    ("cap_extended", (0.8660254, 0.0, -0.5), (1e-6, 1e-6), (0.1, 0.9), "below the horizon, 1 + z_i' = 1.5e-12"),
+    ("cap_extended", (0.5, 0.5, -0.5), (1.0, 1.0), (0.5, 0.25), "below the horizon, alpha = 1"),
+    ("cap_extended", (0.3, 0.9, -0.3), (0.02, 0.5), (0.8, 0.05), "below the horizon, anisotropic"),
+    ("cap_extended", (0.6, 0.0, 0.8), (0.3, 0.3), (0.125, 0.75), "above the horizon: same as the cap row"),
+    ("cap_extended", (0.0, 0.0, -1.0), (0.5, 0.5), (0.5, 0.5), "outside the domain: straight down (1 + z_i' = 0)"),
+    ("hemisphere", (0.0, 0.0, 1.0), (1.0, 1.0), (0.25, 0.5), "normal incidence"),
+    ("hemisphere", (0.6, 0.0, 0.8), (1.0, 1.0), (0.5, 0.5), "oblique"),
+    ("hemisphere", (0.8, 0.0, -0.6), (1.0, 1.0), (0.3, 0.7), "below the horizon"),
+    ("hemisphere", (1e-5, 0.0, -1.0), (1.0, 1.0), (0.6, 0.4), "nearly straight down, 1 + z_i = 5e-11"),
+    ("hemisphere", (0.0, 0.0, -1.0), (1.0, 1.0), (0.5, 0.5), "outside the domain: straight down"),
+]
+
+
+def f32(x):
+    return float(np.float32(x))
+
+
+def rows():
+    out = []
+    for kind, wi, al, u, note in CASES:
+        wi = tuple(f32(t) for t in wi)
+        ax, ay = f32(al[0]), f32(al[1])
+        u1, u2 = f32(u[0]), f32(u[1])
+        w = np.array(wi, np.float64).reshape(3, 1)
+        ok = bool(vndf.in_domain(w, np.array([ax]), np.array([ay]), kind != "cap")[0])
+        if ok:
+            wm, pdf = vndf_mp.sample_with_pdf(u1, u2, wi, ax, ay)
+            a = vndf_mp.one_plus_zi(wi, ax, ay)
+        else:
+            wm, pdf, a = (0.0, 0.0, 1.0), 0.0, float("nan")
+        out.append((kind, wi, ax, ay, u1, u2, wm, pdf, a, note))
+    return out
+
+
+def render(rs):
+    lines = [
+        "# Spherical-cap VNDF samples at 50 significant digits (Dupuy & Benyoub, HPG 2023).",
+        "# Sec. 2 steps (1)-(3) with the Sec. 3.3 cap sampler; pdf = Eq. 1 at the sample.",
+        "# kind = cap (upper domain, wi.z > 0), cap_extended (1 + z_i' >= 2^-40), or hemisphere",
+        "# (Sec. 3.3 on its own: wm = h / |h|, the GGX sampler at alpha = 1).  Outside the domain",
+        "# the expected output is wm = (0, 0, 1), pdf = 0.",
+        "# Inputs are float32 values written as exact hexadecimal floats; outputs are the",
+        "# 50-digit results rounded to float64.  one_plus_zi = 1 + z_i' (nan outside the domain).",
+        "# Written by tests/golden/make_golden.py from oracle/ only.",
+        "# kind wi_x wi_y wi_z alpha_x alpha_y u1 u2 | wm_x wm_y wm_z pdf one_plus_zi | note",
+    ]
+    for kind, wi, ax, ay, u1, u2, wm, pdf, a, note in rs:
+        ins = " ".join(float.hex(t) for t in (*wi, ax, ay, u1, u2))
+        outs = " ".join(repr(float(t)) for t in (*wm, pdf, a))
+        lines.append(f"{kind} {ins} | {outs} | {note}")
+    return "\n".join(lines) + "\n"
+
+
+def load(path=OUT):
+    """Parsed rows: dicts with kind, wi (3,), alpha_x, alpha_y, u1, u2, wm (3,), pdf, one_plus_zi, note."""
+    res = []
+    with open(path) as fh:
+        for line in fh:
+            if not line.strip() or line.startswith("#"):
+                continue
+            ins, outs, note = (s.strip() for s in line.split("|", 2))
+            f = ins.split()
+            x = [float.fromhex(t) for t in f[1:]]
+            y = [float(t) for t in outs.split()]
+            res.append({"kind": f[0], "wi": np.array(x[0:3]), "alpha_x": x[3], "alpha_y": x[4],
+                        "u1": x[5], "u2": x[6], "wm": np.array(y[0:3]), "pdf": y[3],
+                        "one_plus_zi": y[4], "note": note})
+    return res
+
+
+if __name__ == "__main__":
+    with open(OUT, "w") as fh:
+        fh.write(render(rows()))
+    print(f"wrote {OUT}")

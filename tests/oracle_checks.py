@@ -485,3 +485,60 @@ def extended_gradient_errors(n=400, seed=32):
     e_hom = np.abs((jc[:3] * wi[:, None, :]).sum(axis=0)).max() / np.abs(jc).max()
     below = (wi[2] < 0).mean()
     return e_fd, e_hom, below
+
+
+# ----------------------------------------------------------------------------
+# Stored 50-digit samples (tests/golden/cap_samples_mp50.txt)
+# ----------------------------------------------------------------------------
+
+def golden_rows():
+    import os
+    import sys
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    if here not in sys.path:
+        sys.path.insert(0, here)
+    import make_golden
+    return make_golden.load()
+
+
+def golden_oracle_sample(r):
+    """The FP64 oracle's (wm, pdf) for one stored row."""
+    wi = r["wi"].reshape(3, 1)
+    ax, ay = np.array([r["alpha_x"]]), np.array([r["alpha_y"]])
+    u1, u2 = np.array([r["u1"]]), np.array([r["u2"]])
+    if r["kind"] == "hemisphere":
+        wm, pdf = vndf.sample_hemisphere(u1, u2, wi)
+    else:
+        wm, pdf = vndf.sample_vndf_with_pdf(u1, u2, wi, ax, ay, "cap", r["kind"] == "cap_extended")
+    return wm[:, 0], float(pdf[0])
+
+
+def golden_row_error(r):
+    """(angle, pdf relative error, bound) of the FP64 oracle against one stored row.
+
+    The bound is FP64 rounding amplified by 1 / (1 + z_i') where the cap bottom
+    -z_i' is subtracted (Sec. 3.3), and by 1 / sin(theta) where sqrt(1 - z^2) is
+    formed from z as the paper writes it (1 - z = u2 (1 + z_i'), so
+    1 - z^2 = u2 a (2 - u2 a) with a = 1 + z_i').  The pdf is held to 4x the bound.
+    Out-of-domain rows give (0, 0, 1) exactly or an infinite error.
+    """
+    wm, pdf = golden_oracle_sample(r)
+    a = r["one_plus_zi"]
+    if math.isnan(a):
+        exact = tuple(wm) == (0.0, 0.0, 1.0) and pdf == 0.0
+        return (0.0, 0.0, 1.0) if exact else (math.inf, math.inf, 1.0)
+    eps = 2.0 ** -52
+    s = r["u2"] * a * (2.0 - r["u2"] * a)
+    tol = 64 * eps * max(1.0, 1.0 / a) + 8 * eps / max(math.sqrt(s), 2.0 ** -26)
+    cr = np.cross(wm, r["wm"])
+    ang = math.atan2(float(np.linalg.norm(cr)), float(wm @ r["wm"]))
+    return ang, abs(pdf / r["pdf"] - 1.0), tol
+
+
+def golden_excess():
+    """Largest error / bound over the stored rows (<= 1 when the oracle agrees)."""
+    worst = 0.0
+    for r in golden_rows():
+        ang, rel, tol = golden_row_error(r)
+        worst = max(worst, ang / tol, rel / (4 * tol))
+    return worst

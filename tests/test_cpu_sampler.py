@@ -37,6 +37,25 @@ def test_cpu_cap_matches_oracle(v):
     assert st["tail_angle_frac"] < 1e-4
 
 
+def test_cpu_cap_extended_matches_oracle(v):
+    n = (1 << 17) + 5
+    d = {k: t.numpy() for k, t in workloads.sphere_stream(n=n, seed=15).items()}
+    u1, u2 = philox.sample_uniforms(5, 0, 0, n)
+    wx, wy, wz, pdf = v.vndf_cpu_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], u1, u2,
+                                        method="cap_extended")
+    wi = np.stack([d["wi_x"], d["wi_y"], d["wi_z"]])
+    wm = np.stack([wx, wy, wz])
+    st = parity.compare_cap(wm, pdf, u1, u2, wi, d["alpha_x"], d["alpha_y"], strict=False, extended=True)
+    print("cpu cap extended", st)
+    assert st["tail_angle_frac"] < 1e-3
+    assert (wz > 0).all()
+    # above the horizon the extended method is the upper-domain method, bit for bit
+    up = wi[2] > 0
+    ref = v.vndf_cpu_sample(*(d[k][up] for k in ("wi_x", "wi_y", "wi_z", "alpha_x", "alpha_y")), u1[up], u2[up])
+    for a, b in zip((wx, wy, wz, pdf), ref):
+        assert np.array_equal(a[up], b)
+
+
 def test_cpu_prior_matches_oracle(v):
     n = 1 << 16
     d = _inputs(n, seed=13)
@@ -76,3 +95,27 @@ def test_cpu_domain_fallback_and_errors(v):
     np.testing.assert_array_equal(pdf, np.zeros(3, np.float32))
     with pytest.raises(v.VndfError):
         v.vndf_cpu_sample(x, x, z, a, a, u, u, method=5)
+
+
+@pytest.mark.parametrize("kind", ["cap", "cap_extended"])
+def test_cpu_sampler_on_stored_samples(v, kind):
+    """The host sampler on the stored 50-digit rows (tests/golden), held to the
+    condition-scaled bound (it has no double-float path); exact fallback outside the domain."""
+    import oracle_checks as oc
+    rows = [r for r in oc.golden_rows() if r["kind"] == kind]
+    wi = np.stack([r["wi"] for r in rows], axis=1).astype(np.float32)
+    col = {k: np.array([r[k] for r in rows], np.float32) for k in ("alpha_x", "alpha_y", "u1", "u2")}
+    wx, wy, wz, pdf = v.vndf_cpu_sample(wi[0], wi[1], wi[2], col["alpha_x"], col["alpha_y"], col["u1"], col["u2"],
+                                        method=kind)
+    for k, r in enumerate(rows):
+        g = np.array([wx[k], wy[k], wz[k]], np.float64)
+        if np.isnan(r["one_plus_zi"]):
+            assert tuple(g) == (0.0, 0.0, 1.0) and pdf[k] == 0.0
+            continue
+        kap, kap_h = parity.conditioning(np.array([r["u1"]]), np.array([r["u2"]]), r["wi"].reshape(3, 1),
+                                         np.array([r["alpha_x"]]), np.array([r["alpha_y"]]))
+        ang = float(parity.angle_between(g.reshape(3, 1), r["wm"].reshape(3, 1))[0])
+        assert ang <= max(parity.ANGLE_TOL, parity.K_ULP * float(kap[0]) * parity.EPS32), (r["note"], ang)
+        rel = abs(float(pdf[k]) / r["pdf"] - 1.0)
+        assert rel <= max(parity.PDF_TOL, parity.K_ULP * float(3 * kap[0] + 2 * kap_h[0]) * parity.EPS32), \
+            (r["note"], rel)

@@ -1,0 +1,99 @@
+"""The stored 50-digit cap samples (tests/golden/cap_samples_mp50.txt) against the FP64 oracle.
+
+The fixture is written by tests/golden/make_golden.py from oracle/ only.  These
+checks pin the FP64 oracle's sampler (Sec. 2 steps (1)-(3), Sec. 3.3) and its
+definition-based density (Eq. 1 through D and G1 of App. A) to an evaluation
+in 50 digits, on inputs at the edges of the domain:
+* where 1 + z_i' is not tiny, FP64 agrees to within its rounding bound,
+* where it is, FP64 loses digits in proportion to 1 / (1 + z_i') (Sec. 3.3
+  subtracts z_i' from the cap bottom), and the error stays inside that bound,
+* the density written out from its definition (D, G1, wi.wm) at the stored
+  normal equals the stored density, which the sampler's fused form produced,
+* the closed forms the paper's own reasoning gives: wm = (0, 0, 1) and
+  pdf = 1/pi at alpha = 1, normal incidence, u2 = 0; the hemisphere rows obey
+  Eq. 2 with D_std = 1/pi and sigma_std = (1 + z_i)/2 (Eqs. 3-4).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle_checks as oc
+from oracle import vndf
+
+ROWS = oc.golden_rows()
+import make_golden  # noqa: E402  (on the path once golden_rows has run)
+
+
+def test_fixture_shape():
+    kinds = {r["kind"] for r in ROWS}
+    assert kinds == {"cap", "cap_extended", "hemisphere"}
+    assert len(ROWS) == len(make_golden.CASES)
+    for r in ROWS:
+        for t in (*r["wi"], r["alpha_x"], r["alpha_y"], r["u1"], r["u2"]):
+            assert float(np.float32(t)) == t  # inputs are exact float32 values
+        assert 0.0 <= r["u1"] < 1.0 and 0.0 <= r["u2"] < 1.0
+        if math.isnan(r["one_plus_zi"]):
+            assert tuple(r["wm"]) == (0.0, 0.0, 1.0) and r["pdf"] == 0.0
+        else:
+            assert abs(np.linalg.norm(r["wm"]) - 1.0) < 1e-15 and r["pdf"] > 0.0
+
+
+def test_fixture_is_what_the_script_writes():
+    pytest.importorskip("mpmath")
+    with open(make_golden.OUT) as fh:
+        assert fh.read() == make_golden.render(make_golden.rows())
+
+
+@pytest.mark.parametrize("k", range(len(ROWS)))
+def test_fp64_oracle_matches_50_digits(k):
+    ang, rel, tol = oc.golden_row_error(ROWS[k])
+    assert ang <= tol, (ROWS[k]["note"], ang, tol)
+    assert rel <= 4 * tol, (ROWS[k]["note"], rel, tol)
+
+
+@pytest.mark.parametrize("k", [k for k, r in enumerate(ROWS) if r["kind"] != "hemisphere"
+                               and not math.isnan(r["one_plus_zi"])])
+def test_density_definition_at_stored_normal(k):
+    """Eq. 1 through D and G1 (App. A) at the stored wm reproduces the stored fused density."""
+    r = ROWS[k]
+    wi = r["wi"].reshape(3, 1)
+    ax, ay = np.array([r["alpha_x"]]), np.array([r["alpha_y"]])
+    p = float(vndf.vndf_pdf(r["wm"].reshape(3, 1), wi, ax, ay, r["kind"] == "cap_extended")[0])
+    # the density's sensitivity to wm: D varies on the angular scale of alpha, and wi.wm
+    # cancels near the visibility boundary; both are resolved by the 17-digit normal except
+    # at the smallest roughness
+    wu = wi[:, 0] / np.linalg.norm(wi)
+    cos_iv = float(wu @ r["wm"])
+    tol = 1e-12 / min(r["alpha_x"], r["alpha_y"]) ** 2 + 1e-14 / max(abs(cos_iv), 1e-300)
+    assert abs(p / r["pdf"] - 1.0) <= max(tol, 1e-12), (r["note"], p, r["pdf"])
+
+
+def test_closed_form_at_normal_incidence():
+    r = ROWS[0]
+    assert r["u2"] == 0.0 and r["alpha_x"] == r["alpha_y"] == 1.0
+    assert tuple(r["wm"]) == (0.0, 0.0, 1.0)
+    assert abs(r["pdf"] * math.pi - 1.0) < 1e-15
+
+
+def test_extended_rows_above_horizon_equal_cap_rows():
+    ext = [r for r in ROWS if r["kind"] == "cap_extended" and r["wi"][2] > 0]
+    assert ext
+    for r in ext:
+        same = [c for c in ROWS if c["kind"] == "cap" and np.array_equal(c["wi"], r["wi"])
+                and c["alpha_x"] == r["alpha_x"] and c["u1"] == r["u1"] and c["u2"] == r["u2"]]
+        assert same and np.array_equal(same[0]["wm"], r["wm"]) and same[0]["pdf"] == r["pdf"]
+
+
+def test_hemisphere_rows_follow_eq2():
+    """Hemisphere rows: pdf = max(0, wi.wm) / (pi (1 + z_i) / 2) with z_i the unit wi's height (Eqs. 2-4)."""
+    for r in ROWS:
+        if r["kind"] != "hemisphere" or math.isnan(r["one_plus_zi"]):
+            continue
+        wu = r["wi"] / np.linalg.norm(r["wi"])
+        a = r["one_plus_zi"]
+        expect = max(0.0, float(wu @ r["wm"])) / (math.pi * a / 2.0)
+        # wi.wm carries the 17-digit rounding of wm, relative to its own size
+        tol = 1e-15 * (np.abs(wu) @ np.abs(r["wm"])) / max(float(wu @ r["wm"]), 1e-300)
+        assert abs(expect / r["pdf"] - 1.0) <= max(tol, 1e-14), (r["note"], expect, r["pdf"])
+        assert r["wm"][2] > 0.0

@@ -1,0 +1,127 @@
+"""The CUDA samplers on the stored 50-digit samples (tests/golden/cap_samples_mp50.txt).
+
+Each stored row fixes float32 inputs and explicit uniforms; the kernels run on
+them through the C ABI (vndf_sample with the upper-domain and extended cap
+methods, vndf_sample_hemisphere) and are compared with the stored values, which
+the oracle alone wrote.  This needs no arbitrary-precision library on the GPU
+host.  Bounds: 4e-6 rad and 1e-5 relative on every row inside the accuracy
+contract (the double-float rescue keeps those there); rows outside it (roughness
+below 1e-3, or wi.z below 1e-4 on the upper domain) are held to the
+condition-scaled bound of tests/parity.py.  Out-of-domain rows must give
+wm = (0, 0, 1) and pdf = 0 exactly.  An extended-method row above the horizon
+must equal the upper-domain method's output bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle_checks as oc
+import parity
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+ROWS = oc.golden_rows()
+
+
+@pytest.fixture(scope="module")
+def v():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2306_05044_gb300 as lib
+    return lib
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=DEV)
+
+
+def _columns(rows):
+    wi = np.stack([r["wi"] for r in rows], axis=1)
+    cols = {k: np.array([r[k] for r in rows]) for k in ("alpha_x", "alpha_y", "u1", "u2")}
+    return wi, cols
+
+
+def run_kind(v, kind, rows):
+    wi, c = _columns(rows)
+    wx, wy, wz = (_dev(wi[i]) for i in range(3))
+    u1, u2 = _dev(c["u1"]), _dev(c["u2"])
+    if kind == "hemisphere":
+        out = v.vndf_sample_hemisphere(wx, wy, wz, u1=u1, u2=u2)
+    else:
+        out = v.vndf_sample(wx, wy, wz, _dev(c["alpha_x"]), _dev(c["alpha_y"]), u1=u1, u2=u2, method=kind)
+    torch.cuda.synchronize()
+    wm = np.stack([t.cpu().numpy().astype(np.float64) for t in out[:3]])
+    return wm, out[3].cpu().numpy().astype(np.float64)
+
+
+def check_rows(kind, rows, wm, pdf, strict_fn):
+    for k, r in enumerate(rows):
+        g, p = wm[:, k], pdf[k]
+        if math.isnan(r["one_plus_zi"]):
+            assert tuple(g) == (0.0, 0.0, 1.0) and p == 0.0, (kind, r["note"], g, p)
+            continue
+        ang = float(parity.angle_between(g.reshape(3, 1), r["wm"].reshape(3, 1))[0])
+        rel = abs(p / r["pdf"] - 1.0)
+        if strict_fn(r):
+            abound, pbound = parity.ANGLE_TOL, parity.PDF_TOL
+        else:
+            a1, a2 = np.array([r["alpha_x"]]), np.array([r["alpha_y"]])
+            kap, kap_h = parity.conditioning(np.array([r["u1"]]), np.array([r["u2"]]),
+                                             r["wi"].reshape(3, 1), a1, a2)
+            abound = max(parity.ANGLE_TOL, parity.K_ULP * float(kap[0]) * parity.EPS32)
+            pbound = max(parity.PDF_TOL, parity.K_ULP * float(3 * kap[0] + 2 * kap_h[0]) * parity.EPS32)
+        assert ang <= abound, (kind, r["note"], ang, abound)
+        assert rel <= pbound, (kind, r["note"], rel, pbound)
+        assert abs(np.linalg.norm(g) - 1.0) <= 2.0 ** -21
+
+
+def _strict(extended):
+    def f(r):
+        ok = min(r["alpha_x"], r["alpha_y"]) >= 1e-3
+        if not extended:
+            ok &= r["wi"][2] / np.linalg.norm(r["wi"]) >= 1e-4
+        return ok
+    return f
+
+
+@pytest.mark.parametrize("kind", ["cap", "cap_extended", "hemisphere"])
+def test_gpu_matches_stored_samples(v, kind):
+    rows = [r for r in ROWS if r["kind"] == kind]
+    wm, pdf = run_kind(v, kind, rows)
+    check_rows(kind, rows, wm, pdf, _strict(kind != "cap"))
+
+
+def test_gpu_stored_rows_in_a_large_batch(v):
+    """The same rows scattered through a batch that spans many CTAs and a ragged tail
+    (other lanes hold a repeated ordinary input), so that each row meets the kernels'
+    vectorised, pipelined and tail code paths rather than a tiny launch."""
+    rows = [r for r in ROWS if r["kind"] == "cap_extended"]
+    n = (1 << 20) + 7
+    rng = np.random.default_rng(5)
+    pos = np.sort(rng.choice(n, size=len(rows), replace=False))
+    pos[-1] = n - 1  # one row in the last, partial, group
+    fill = ROWS[2]
+    wi = np.repeat(fill["wi"].reshape(3, 1), n, axis=1)
+    cols = {k: np.full(n, fill[k]) for k in ("alpha_x", "alpha_y", "u1", "u2")}
+    for p, r in zip(pos, rows):
+        wi[:, p] = r["wi"]
+        for k in cols:
+            cols[k][p] = r[k]
+    out = v.vndf_sample(*(_dev(wi[i]) for i in range(3)), _dev(cols["alpha_x"]), _dev(cols["alpha_y"]),
+                        u1=_dev(cols["u1"]), u2=_dev(cols["u2"]), method="cap_extended")
+    torch.cuda.synchronize()
+    wm = np.stack([t.cpu().numpy().astype(np.float64) for t in out[:3]])
+    pdf = out[3].cpu().numpy().astype(np.float64)
+    check_rows("cap_extended", rows, wm[:, pos], pdf[pos], _strict(True))
+
+
+def test_extended_equals_upper_above_horizon_bitwise(v):
+    up = [r for r in ROWS if r["kind"] == "cap" and not math.isnan(r["one_plus_zi"])]
+    wm_u, p_u = run_kind(v, "cap", up)
+    wm_e, p_e = run_kind(v, "cap_extended", up)
+    assert np.array_equal(wm_u, wm_e) and np.array_equal(p_u, p_e)

@@ -242,7 +242,10 @@ def _detectors():
         a, b = oc.extended_alpha_one_errors(n=2000)
         return a > 1e-13 or b > 1e-12
 
-    return dict(extended_normalisation=extended_normalisation, extended_cov=extended_cov,
+    def golden_mp50():
+        return oc.golden_excess() > 1.0
+
+    return dict(golden_mp50=golden_mp50, extended_normalisation=extended_normalisation, extended_cov=extended_cov,
                 extended_alpha_one=extended_alpha_one, reflection=reflection, reflected_density=reflected_density, philox_vs_curand=philox_vs_curand, pair_words=pair_words, invariants=invariants,
                 mirror=mirror, cov=cov, alpha_one=alpha_one, symmetry=symmetry,
                 normalisation=normalisation, eq1=eq1, brute_force=brute_force, prior=prior,
