@@ -13,6 +13,9 @@ Steps (Dupuy & Benyoub, HPG 2023):
   sqrt(1 - z^2) sin phi, z), h = c + i
 * Sec. 2 step (3): v = (ax hx, ay hy, hz), wm = v / |v|
 * Eqs. 1-4 at the sample: pdf = |v|^3 / (pi ax ay (1 + i.z) |h|^2)
+* the density of a given normal (``pdf_of_normal``): max(0, wi.wm) D(wm) / sigma(wi)
+  with the GGX D of App. A and the projected area sigma(wi) = (|M^-1 wi| + wi.z) / 2
+  of unit wi (Eq. 4 carried through the stretch; G1(wi) / wi.z = 1 / sigma(wi))
 """
 import mpmath
 
@@ -46,3 +49,20 @@ def one_plus_zi(wi, ax, ay):
         sx, sy = mpmath.mpf(float(ax)) * mpmath.mpf(float(wi[0])), mpmath.mpf(float(ay)) * mpmath.mpf(float(wi[1]))
         wz = mpmath.mpf(float(wi[2]))
         return float(1 + wz / mpmath.sqrt(sx * sx + sy * sy + wz * wz))
+
+
+def pdf_of_normal(wm, wi, ax, ay):
+    """Density of the given normal wm (3 floats) for direction wi (any length), 50 digits."""
+    with mpmath.workdps(DIGITS):
+        ax, ay = mpmath.mpf(float(ax)), mpmath.mpf(float(ay))
+        wx, wy, wz = (mpmath.mpf(float(t)) for t in wi)
+        n = mpmath.sqrt(wx * wx + wy * wy + wz * wz)
+        wx, wy, wz = wx / n, wy / n, wz / n
+        mx, my, mz = (mpmath.mpf(float(t)) for t in wm)
+        if mz <= 0:
+            return 0.0
+        s = mpmath.sqrt((ax * wx) ** 2 + (ay * wy) ** 2 + wz * wz)
+        sigma = (s + wz) / 2
+        q = (mx / ax) ** 2 + (my / ay) ** 2 + mz * mz
+        d = max(wx * mx + wy * my + wz * mz, mpmath.mpf(0))
+        return float(d / (mpmath.pi * ax * ay * q * q * sigma))

@@ -23,7 +23,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompil
               "--expt-relaxed-constexpr", "-Xptxas", "-O3"]
 
 
-HOST_FLAGS = ["-O3", "-std=c++17", "-fPIC", "-fopenmp-simd", "-fno-math-errno", "-fno-trapping-math", "-pthread"]
+HOST_FLAGS = ["-O3", "-std=c++17", "-fPIC", "-fopenmp-simd", "-fno-math-errno", "-fno-trapping-math", "-ffp-contract=off", "-pthread"]
 
 
 def _cxx():

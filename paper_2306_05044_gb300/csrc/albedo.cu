@@ -153,7 +153,7 @@ __device__ __forceinline__ float albedo_weight(const QueryConst& c, float f0, fl
   const float po = fmaf(sx, sx, sy * sy);
   const float lo = sqrt_fast(fmaf(oz, oz, po));
   const float num = c.A * oz;
-  const float g = __fdividef(num, fmaf(c.uz * po, __fdividef(1.f, lo + oz), num));
+  const float g = num * rcp_fast(fmaf(c.uz * po, rcp_fast(lo + oz), num));
   const float t = 1.f - d;
   const float t2 = t * t;
   const float fr = fmaf(1.f - f0, t2 * t2 * t, f0);

@@ -11,7 +11,10 @@
 // fused multiply-add (every AArch64 core) the loop vectorises; on the x86-64
 // baseline, which has none, std::fma is a library call and the loop stays
 // scalar, with the same results.  -fno-trapping-math lets the compiler compute
-// both sides of the domain selects.
+// both sides of the domain selects; -ffp-contract=off keeps the compiler from
+// fusing a product and a sum that the source writes apart (every fused
+// multiply-add here is an explicit std::fma), so the results are the same on
+// both ISAs and the extended method equals the upper one above the horizon.
 #include <cmath>
 #include <cstdint>
 #include <thread>
@@ -116,7 +119,9 @@ __attribute__((always_inline)) inline void sample_host(float wx, float wy, float
   float p;
   if constexpr (kCap) {
     const float hh = std::fma(hx, hx, std::fma(hy, hy, hz * hz));
-    p = vv * nv / (kPiF * ax * ay * a * hh);
+    // (|v|^2 / |h|^2) |v| / (pi ax ay a): every factor stays in FP32 range (|v|^3 would
+    // underflow for tiny roughness on the extended domain's smallest cap heights)
+    p = (vv / hh) * nv / (kPiF * ax * ay * a);
   } else {
     const float hi = std::fmax(std::fma(hx, ix, std::fma(hy, iy, hz * iz)), 0.f);
     p = 2.f * hi * vv * nv / (kPiF * ax * ay * a);

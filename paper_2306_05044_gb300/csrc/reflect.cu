@@ -97,14 +97,14 @@ __device__ __forceinline__ Reflected reflect_one(float wx, float wy, float wz, f
   r.oy = fmaf(2.f * d, my, -uy);
   r.oz = fmaf(2.f * d, mz, -uz);
   // PDF = |wi| |v|^4 / (2 pi ax ay L a |h|^4)
-  r.pdf = __fdividef(vv * vv, 2.f * kPi * ax * ay * L * a * hh * hh * rw);
+  r.pdf = vv * vv * rcp_fast(2.f * kPi * ax * ay * L * a * hh * hh * rw);
   // weight = F G2 / G1(wi) with G2 / G1 = (L_u + z_u) z_o / ((L_u + z_u) z_o + z_u P_o / (L_o + z_o))
   const float A = fmaf(L, rw, uz);                   // |M^-1 wi_unit| + wi_unit.z
   const float px = ax * r.ox, py = ay * r.oy;
   const float po = fmaf(px, px, py * py);
   const float lo = sqrt_fast(fmaf(r.oz, r.oz, po));
   const float num = A * r.oz;
-  const float g = __fdividef(num, fmaf(uz * po, __fdividef(1.f, lo + r.oz), num));
+  const float g = num * rcp_fast(fmaf(uz * po, rcp_fast(lo + r.oz), num));
   const float t = 1.f - d;
   const float t2 = t * t;
   const float fr = fmaf(1.f - f0, t2 * t2 * t, f0);

@@ -48,7 +48,7 @@ __device__ __forceinline__ Grad5 cap_backward_one(float wx, float wy, float wz, 
   const float a_up = __fadd_rn(1.f, iz);
   float a = a_up;
   if constexpr (EXT) {
-    if (iz < 0.f) a = __fdividef(rho2, 1.f - iz);
+    if (iz < 0.f) a = rho2 * rcp_fast(1.f - iz);
     ok &= a >= kMinCapA;
   }
   const float om = 1.f - u2;
@@ -68,17 +68,19 @@ __device__ __forceinline__ Grad5 cap_backward_one(float wx, float wy, float wz, 
   my = vy * rv;
   mz = vz * rv;
   const float hh = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
-  // one reciprocal of the pdf denominator gives 1/hh, 1/a, 1/ax and 1/ay
+  // two reciprocals, of a |h|^2 and of pi ax ay, give 1/hh, 1/a, 1/ax, 1/ay and the pdf
+  // (|v|^2 / (a |h|^2)) (|v| / (pi ax ay)), each factor within the FP32 range where the
+  // full product a |h|^2 ax ay, or |v|^3, would not be (tiny roughness together with the
+  // extended domain's smallest a)
   float rhh = 0.f, ra = 0.f, rax = 0.f, ray = 0.f, glp = 0.f;
   pdf = 0.f;
   if constexpr (PDF_TERMS) {
-    const float rden = __fdividef(1.f, kPi * ax * ay * a * hh);
-    pdf = vv * vv * rv * rden;
-    const float p_ = kPi * rden;
-    const float q1 = ax * ay * p_;
-    const float q2 = a * hh * p_;
-    rhh = q1 * a;
-    ra = q1 * hh;
+    const float rah = rcp_fast(a * hh);
+    const float rxy = rcp_fast(kPi * ax * ay);
+    pdf = (vv * rah) * ((vv * rv) * rxy);
+    rhh = a * rah;
+    ra = hh * rah;
+    const float q2 = kPi * rxy;
     rax = ay * q2;
     ray = ax * q2;
     glp = fmaf(gpdf, pdf, glog);  // adjoint of log pdf

@@ -63,6 +63,15 @@ __device__ __forceinline__ float sqrt_fast(float x) {
   return r;
 }
 
+// Reciprocal by the PTX rcp.approx.ftz.f32 instruction (documented maximum error
+// 1 ulp; subnormal inputs and results flush to zero): one MUFU instruction with
+// no subnormal fix-up, for operands that the callers keep in the normal range.
+__device__ __forceinline__ float rcp_fast(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // sin(pi x) and cos(pi x) for finite x (used with x = 2 u1, the azimuth in
 // half turns).  Reduction: j = rint(2x), r = x - j/2 in [-1/4, 1/4]; for
 // x in [0, 2] the subtraction is exact (Sterbenz).  sin(pi r) and cos(pi r)
@@ -143,7 +152,7 @@ __device__ __forceinline__ void cap_half_vector(const Stretched& i, float u1, fl
   // both variants then round a the same way and agree bit for bit above the horizon
   const float a_up = __fadd_rn(1.f, i.z);
   if constexpr (EXT)
-    a = i.z >= 0.f ? a_up : __fdividef(rho2, 1.f - i.z);  // 1 - i.z in [1, 2]
+    a = i.z >= 0.f ? a_up : rho2 * rcp_fast(1.f - i.z);  // 1 - i.z in [1, 2]
   else
     a = a_up;
   const float sin2 = u2 * fmaf(2.f * a, 1.f - u2, u2 * rho2);  // (1 - z)(1 + z)
@@ -187,10 +196,10 @@ __device__ __forceinline__ void polar_disk_normal(const Stretched& i, float u1, 
   const float q = sqrt_fast(fmaf(u2 * sp, sp, om));  // sqrt(1 - t1^2)
   const float a = 1.f + i.z;
   const float s = 0.5f * a;
-  const float oms = __fdividef(0.5f * tmp, a);     // 1 - s
+  const float oms = 0.5f * tmp * rcp_fast(a);      // 1 - s
   const bool pos = t2o >= 0.f;
   const float big = pos ? q + t2o : q - t2o;        // no cancellation either way
-  const float small = __fdividef(om, big);          // the other one of q -/+ t2o
+  const float small = om * rcp_fast(big);           // the other one of q -/+ t2o
   const float qm = pos ? small : big;               // q - t2o
   const float qp = pos ? big : small;               // q + t2o
   const float t2 = fmaf(oms, q, s * t2o);
@@ -218,13 +227,17 @@ __device__ __forceinline__ void finish_sample(const Stretched& i, float ax, floa
   my = vy * rv;
   mz = vz * rv;
   if constexpr (PDF) {
-    const float v3 = vv * vv * rv;  // |v|^3
+    const float nv = vv * rv;  // |v|
     if constexpr (is_cap<METHOD>()) {
+      // |v|^3 / (pi ax ay a |h|^2) as (|v|^2 / |h|^2) |v| / (pi ax ay a): |v|^2 / |h|^2 lies
+      // between min(ax, ay, 1)^2 and max(ax, ay, 1)^2, so no factor leaves the FP32 range,
+      // whereas |v|^3 underflows once |v| < 2e-13 (tiny roughness together with the
+      // extended domain's smallest cap heights a)
       const float hh = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
-      pdf = __fdividef(v3, kPi * ax * ay * a * hh);
+      pdf = (vv * rcp_fast(hh)) * nv * rcp_fast(kPi * ax * ay * a);
     } else {
       const float hi = fmaxf(fmaf(hx, i.x, fmaf(hy, i.y, hz * i.z)), 0.f);
-      pdf = __fdividef(2.f * hi * v3, kPi * ax * ay * a);
+      pdf = 2.f * hi * vv * nv * rcp_fast(kPi * ax * ay * a);
     }
   }
 }
@@ -300,10 +313,11 @@ __device__ __forceinline__ float pdf_of_normal(float wx, float wy, float wz, flo
     if (wz < 0.f) lw = fmaf(sx, sx, sy * sy) / (l - wz);
     ok &= lw >= kMinCapA * l;  // a = 1 + i.z = lw / l
   }
-  const float qx = __fdividef(mx, ax), qy = __fdividef(my, ay);
+  const float qx = mx * rcp_fast(ax), qy = my * rcp_fast(ay);
   const float q = fmaf(qx, qx, fmaf(qy, qy, mz * mz));
   const float d = fmaxf(fmaf(wx, mx, fmaf(wy, my, wz * mz)), 0.f);
-  const float p = __fdividef(2.f * d, kPi * ax * ay * lw * q * q);
+  // (ax q)(ay q) rather than ax ay q^2: q grows like 1 / alpha^2 away from the peak
+  const float p = 2.f * d * rcp_fast(kPi * lw * (ax * q) * (ay * q));
   return ok ? p : 0.f;
 }
 

@@ -8,7 +8,7 @@ domain, the fallback the oracle defines (``oracle.vndf.in_domain``; normal
 
 The inputs are fixed float32 values chosen to reach the places where a
 plausible mistake shows: normal incidence, grazing and below-horizon incident
-directions, roughness from 1e-6 to 1.5, strong anisotropy, unnormalised wi,
+directions, roughness from 1e-7 to 1.5, strong anisotropy, unnormalised wi,
 and uniforms at the ends of [0, 1) (the cap's top at u2 = 0, its rim as
 u2 -> 1, phi -> 2 pi as u1 -> 1).
 
@@ -44,6 +44,7 @@ CASES = [
     ("cap", (3.0, -4.0, 12.0), (0.4, 0.4), (0.33, 0.66), "unnormalised wi, length 13"),
     ("cap", (0.1, 0.2, 0.97), (0.6, 0.3), (ONE_M, TINY_U), "u1 at its largest, u2 at its smallest non-zero"),
     ("cap", (-0.7, -0.1, 0.3), (0.02, 0.02), (0.37, 0.81), "small alpha, wi in the third quadrant"),
+    ("cap", (0.3, 0.4, 0.8660254), (1e-7, 1e-7), (0.2, 0.6), "alpha = 1e-7"),
     ("cap", (0.5, 0.5, 0.0), (0.5, 0.5), (0.5, 0.5), "outside the domain: wi.z = 0"),
     ("cap", (0.6, 0.0, -0.8), (0.3, 0.3), (0.4, 0.6), "outside the domain: below the horizon"),
     ("cap", (0.0, 0.0, 1.0), (0.0, 0.5), (0.5, 0.5), "outside the domain: alpha_x = 0"),
@@ -51,6 +52,8 @@ CASES = [
     ("cap_extended", (0.0, 0.8, -0.6), (0.01, 0.01), (0.2, 0.3), "below the horizon, 1 + z_i' = 9e-5"),
     ("cap_extended", (1.0, 0.0, -0.1), (1e-3, 1e-3), (0.75, 0.5), "below the horizon, 1 + z_i' = 5e-5"),
     ("cap_extended", (0.8660254, 0.0, -0.5), (1e-6, 1e-6), (0.1, 0.9), "below the horizon, 1 + z_i' = 1.5e-12"),
+    ("cap_extended", (0.8660254, 0.0, -0.5), (1e-6, 1e-6), (0.3, ONE_M), "below the horizon, 1 + z_i' = 1.5e-12, the rim"),
+    ("cap_extended", (1.0, 0.0, -0.05), (1e-7, 1e-7), (0.7, 0.3), "below the horizon, alpha = 1e-7, 1 + z_i' = 2e-12"),
     ("cap_extended", (0.5, 0.5, -0.5), (1.0, 1.0), (0.5, 0.25), "below the horizon, alpha = 1"),
     ("cap_extended", (0.3, 0.9, -0.3), (0.02, 0.5), (0.8, 0.05), "below the horizon, anisotropic"),
     ("cap_extended", (0.6, 0.0, 0.8), (0.3, 0.3), (0.125, 0.75), "above the horizon: same as the cap row"),
@@ -78,9 +81,10 @@ def rows():
         if ok:
             wm, pdf = vndf_mp.sample_with_pdf(u1, u2, wi, ax, ay)
             a = vndf_mp.one_plus_zi(wi, ax, ay)
+            p32 = vndf_mp.pdf_of_normal(tuple(f32(t) for t in wm), wi, ax, ay)
         else:
-            wm, pdf, a = (0.0, 0.0, 1.0), 0.0, float("nan")
-        out.append((kind, wi, ax, ay, u1, u2, wm, pdf, a, note))
+            wm, pdf, a, p32 = (0.0, 0.0, 1.0), 0.0, float("nan"), 0.0
+        out.append((kind, wi, ax, ay, u1, u2, wm, pdf, a, p32, note))
     return out
 
 
@@ -93,18 +97,21 @@ def render(rs):
         "# the expected output is wm = (0, 0, 1), pdf = 0.",
         "# Inputs are float32 values written as exact hexadecimal floats; outputs are the",
         "# 50-digit results rounded to float64.  one_plus_zi = 1 + z_i' (nan outside the domain).",
+        "# pdf_wm32 = the density of the normal wm rounded to float32 (Eq. 1 through the App. A",
+        "# forms of D and G1, G1(wi)/wi.z = 1/sigma(wi)), for checking density-of-a-normal entries.",
         "# Written by tests/golden/make_golden.py from oracle/ only.",
-        "# kind wi_x wi_y wi_z alpha_x alpha_y u1 u2 | wm_x wm_y wm_z pdf one_plus_zi | note",
+        "# kind wi_x wi_y wi_z alpha_x alpha_y u1 u2 | wm_x wm_y wm_z pdf one_plus_zi pdf_wm32 | note",
     ]
-    for kind, wi, ax, ay, u1, u2, wm, pdf, a, note in rs:
+    for kind, wi, ax, ay, u1, u2, wm, pdf, a, p32, note in rs:
         ins = " ".join(float.hex(t) for t in (*wi, ax, ay, u1, u2))
-        outs = " ".join(repr(float(t)) for t in (*wm, pdf, a))
+        outs = " ".join(repr(float(t)) for t in (*wm, pdf, a, p32))
         lines.append(f"{kind} {ins} | {outs} | {note}")
     return "\n".join(lines) + "\n"
 
 
 def load(path=OUT):
-    """Parsed rows: dicts with kind, wi (3,), alpha_x, alpha_y, u1, u2, wm (3,), pdf, one_plus_zi, note."""
+    """Parsed rows: dicts with kind, wi (3,), alpha_x, alpha_y, u1, u2, wm (3,), pdf, one_plus_zi,
+    pdf_wm32, note."""
     res = []
     with open(path) as fh:
         for line in fh:
@@ -116,7 +123,7 @@ def load(path=OUT):
             y = [float(t) for t in outs.split()]
             res.append({"kind": f[0], "wi": np.array(x[0:3]), "alpha_x": x[3], "alpha_y": x[4],
                         "u1": x[5], "u2": x[6], "wm": np.array(y[0:3]), "pdf": y[3],
-                        "one_plus_zi": y[4], "note": note})
+                        "one_plus_zi": y[4], "pdf_wm32": y[5], "note": note})
     return res
 
 

@@ -502,14 +502,22 @@ def golden_rows():
 
 
 def golden_oracle_sample(r):
-    """The FP64 oracle's (wm, pdf) for one stored row."""
+    """The FP64 oracle's (wm, pdf) for one stored row.
+
+    For the GGX rows the density is the oracle's Eq. 1 at its own hemisphere
+    sample (vndf_pdf_at_cap_sample), which does not cancel; the definition form
+    through wi.wm does cancel next to the visibility boundary (the cap's rim as
+    u2 -> 1) and is pinned at the stored normal by a test of its own."""
     wi = r["wi"].reshape(3, 1)
     ax, ay = np.array([r["alpha_x"]]), np.array([r["alpha_y"]])
     u1, u2 = np.array([r["u1"]]), np.array([r["u2"]])
     if r["kind"] == "hemisphere":
         wm, pdf = vndf.sample_hemisphere(u1, u2, wi)
     else:
-        wm, pdf = vndf.sample_vndf_with_pdf(u1, u2, wi, ax, ay, "cap", r["kind"] == "cap_extended")
+        ext = r["kind"] == "cap_extended"
+        wm = vndf.sample_vndf(u1, u2, wi, ax, ay, "cap", ext)
+        ok = vndf.in_domain(wi, ax, ay, ext)
+        pdf = np.where(ok, vndf.vndf_pdf_at_cap_sample(u1, u2, wi, ax, ay, ext), 0.0) if ok.all() else np.zeros(1)
     return wm[:, 0], float(pdf[0])
 
 

@@ -97,3 +97,34 @@ def test_hemisphere_rows_follow_eq2():
         tol = 1e-15 * (np.abs(wu) @ np.abs(r["wm"])) / max(float(wu @ r["wm"]), 1e-300)
         assert abs(expect / r["pdf"] - 1.0) <= max(tol, 1e-14), (r["note"], expect, r["pdf"])
         assert r["wm"][2] > 0.0
+
+
+def _kd(r, wm):
+    wu = r["wi"] / np.linalg.norm(r["wi"])
+    return float(np.abs(wu * wm).sum() / abs(wu @ wm))
+
+
+@pytest.mark.parametrize("k", [k for k, r in enumerate(ROWS) if not math.isnan(r["one_plus_zi"])])
+def test_density_of_normal_forms_agree_at_50_digits(k):
+    """The 50-digit density of the float32-rounded normal (max(0, wi.wm) D / sigma, App. A and
+    Eq. 4) against the 50-digit fused density at the exact sample (Sec. 3.3 and Eq. 1): two
+    different formulas, apart only by the density's change over the float32 rounding of wm
+    (relative 2^-24 times 4 / alpha for D, plus wi.wm's amplification of the rounding)."""
+    r = ROWS[k]
+    amin = min(r["alpha_x"], r["alpha_y"], 1.0)
+    wm32 = r["wm"].astype(np.float32).astype(np.float64)
+    bound = 8 * 2.0 ** -24 * (4.0 / amin + _kd(r, wm32))
+    assert abs(r["pdf_wm32"] / r["pdf"] - 1.0) <= bound, (r["note"], r["pdf_wm32"], r["pdf"])
+
+
+@pytest.mark.parametrize("k", [k for k, r in enumerate(ROWS) if not math.isnan(r["one_plus_zi"])])
+def test_fp64_density_of_normal_matches_50_digits(k):
+    """The FP64 oracle's vndf_pdf at the float32 normal against the stored 50-digit value; its
+    G1 / sigma forms 1 + z_i' by cancellation, so the bound grows like 1 / (1 + z_i')."""
+    r = ROWS[k]
+    wm32 = r["wm"].astype(np.float32).astype(np.float64)
+    ext = r["kind"] != "cap"
+    p = float(vndf.vndf_pdf(wm32.reshape(3, 1), r["wi"].reshape(3, 1), np.array([r["alpha_x"]]),
+                            np.array([r["alpha_y"]]), ext)[0])
+    bound = 64 * 2.0 ** -52 * max(1.0, 1.0 / r["one_plus_zi"]) * _kd(r, wm32)
+    assert abs(p / r["pdf_wm32"] - 1.0) <= bound, (r["note"], p, r["pdf_wm32"])

@@ -125,3 +125,23 @@ def test_extended_equals_upper_above_horizon_bitwise(v):
     wm_u, p_u = run_kind(v, "cap", up)
     wm_e, p_e = run_kind(v, "cap_extended", up)
     assert np.array_equal(wm_u, wm_e) and np.array_equal(p_u, p_e)
+
+
+@pytest.mark.parametrize("kind", ["cap", "cap_extended", "hemisphere"])
+def test_pdf_entry_at_stored_normals(v, kind):
+    """vndf_pdf (vndf_pdf_extended for the extended and the hemisphere rows, the latter at
+    alpha = 1) at the stored normals rounded to float32, against the stored 50-digit density of
+    that float32 normal; the bound widens only where wi.wm cancels."""
+    rows = [r for r in ROWS if r["kind"] == kind and not math.isnan(r["one_plus_zi"])]
+    wi, c = _columns(rows)
+    wm = np.stack([r["wm"] for r in rows], axis=1).astype(np.float32)
+    p = v.vndf_pdf(*(_dev(wi[i]) for i in range(3)), _dev(c["alpha_x"]), _dev(c["alpha_y"]),
+                   *(_dev(wm[i]) for i in range(3)), extended=kind != "cap")
+    ref = np.array([r["pdf_wm32"] for r in rows])
+    rel = np.abs(p.cpu().numpy().astype(np.float64) / ref - 1.0)
+    wm64 = wm.astype(np.float64)
+    wu = wi / np.linalg.norm(wi, axis=0)
+    kd = np.abs(wu * wm64).sum(0) / np.abs((wu * wm64).sum(0))
+    bound = np.maximum(parity.PDF_TOL, parity.K_ULP * (kd + 8.0) * parity.EPS32)
+    bad = np.flatnonzero(~(rel <= bound))
+    assert bad.size == 0, [(rows[k]["note"], rel[k], bound[k]) for k in bad]
