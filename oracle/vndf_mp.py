@@ -13,6 +13,10 @@ Steps (Dupuy & Benyoub, HPG 2023):
   sqrt(1 - z^2) sin phi, z), h = c + i
 * Sec. 2 step (3): v = (ax hx, ay hy, hz), wm = v / |v|
 * Eqs. 1-4 at the sample: pdf = |v|^3 / (pi ax ay (1 + i.z) |h|^2)
+* derivatives of (wm, pdf) with respect to (wi, ax, ay) at fixed u (``jacobian``): central
+  differences of the same steps at 50 digits with step 1e-20, written with the exact identities
+  1 - z = u2 (1 + i.z) (so 1 - z^2 = u2 a (2 - u2 a), a = 1 + i.z) and h.z = (1 - u2) a, so that no
+  rounding at 1e-50 is divided by the step
 * the density of a given normal (``pdf_of_normal``): max(0, wi.wm) D(wm) / sigma(wi)
   with the GGX D of App. A and the projected area sigma(wi) = (|M^-1 wi| + wi.z) / 2
   of unit wi (Eq. 4 carried through the stretch; G1(wi) / wi.z = 1 / sigma(wi))
@@ -66,3 +70,39 @@ def pdf_of_normal(wm, wi, ax, ay):
         q = (mx / ax) ** 2 + (my / ay) ** 2 + mz * mz
         d = max(wx * mx + wy * my + wz * mz, mpmath.mpf(0))
         return float(d / (mpmath.pi * ax * ay * q * q * sigma))
+
+
+def _forward(u1, u2, wx, wy, wz, ax, ay):
+    """(wm_x, wm_y, wm_z, pdf) as mpf from mpf inputs: the steps of sample_with_pdf."""
+    sx, sy = ax * wx, ay * wy
+    el = mpmath.sqrt(sx * sx + sy * sy + wz * wz)
+    ix, iy, iz = sx / el, sy / el, wz / el
+    a = 1 + iz
+    phi = 2 * mpmath.pi * u1
+    st = mpmath.sqrt(u2 * a * (2 - u2 * a))
+    hx = st * mpmath.cos(phi) + ix
+    hy = st * mpmath.sin(phi) + iy
+    hz = (1 - u2) * a
+    vx, vy, vz = ax * hx, ay * hy, hz
+    vn = mpmath.sqrt(vx * vx + vy * vy + vz * vz)
+    hh = hx * hx + hy * hy + hz * hz
+    return vx / vn, vy / vn, vz / vn, vn ** 3 / (mpmath.pi * ax * ay * a * hh)
+
+
+def jacobian(u1, u2, wi, ax, ay):
+    """d(wm_x, wm_y, wm_z, pdf)/d(wi_x, wi_y, wi_z, alpha_x, alpha_y) at fixed u: a 5 x 4 list of
+    floats [input][output], by central differences at 50 digits (truncation ~ 1e-40, rounding
+    ~ 1e-30 relative)."""
+    with mpmath.workdps(DIGITS):
+        u1, u2 = mpmath.mpf(float(u1)), mpmath.mpf(float(u2))
+        x = [mpmath.mpf(float(t)) for t in (*wi, ax, ay)]
+        out = []
+        for k in range(5):
+            step = mpmath.mpf("1e-20") * max(1, abs(x[k]))
+            xp, xm = list(x), list(x)
+            xp[k] += step
+            xm[k] -= step
+            fp = _forward(u1, u2, *xp)
+            fm = _forward(u1, u2, *xm)
+            out.append([float((p - m) / (2 * step)) for p, m in zip(fp, fm)])
+        return out

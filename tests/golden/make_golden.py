@@ -1,10 +1,13 @@
-"""Writes cap_samples_mp50.txt: stored expected samples of the spherical-cap sampler.
+"""Writes cap_samples_mp50.txt and cap_jacobians_mp50.txt: stored expected samples of the
+spherical-cap sampler and their derivatives.
 
 Every expected value comes from the oracle alone: the 50-digit evaluation of
 Sec. 2 steps (1)-(3) with the Sec. 3.3 cap sampler and the density of Eq. 1
 (``oracle.vndf_mp.sample_with_pdf``), and, for inputs outside the sampler's
 domain, the fallback the oracle defines (``oracle.vndf.in_domain``; normal
-(0, 0, 1), density 0).  Nothing here calls the CUDA library.
+(0, 0, 1), density 0); the derivatives of each in-domain sample with respect to
+(wi, alpha) at fixed u come from ``oracle.vndf_mp.jacobian``.  Nothing here calls
+the CUDA library.
 
 The inputs are fixed float32 values chosen to reach the places where a
 plausible mistake shows: normal incidence, grazing and below-horizon incident
@@ -26,6 +29,9 @@ if ROOT not in sys.path:
 from oracle import vndf, vndf_mp  # noqa: E402
 
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "cap_samples_mp50.txt")
+OUT_JAC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "cap_jacobians_mp50.txt")
+JAC_INPUTS = ("wi_x", "wi_y", "wi_z", "alpha_x", "alpha_y")
+JAC_OUTPUTS = ("wm_x", "wm_y", "wm_z", "pdf")
 ONE_M = 1.0 - 2.0 ** -24  # largest float32 uniform below 1
 TINY_U = 2.0 ** -24
 
@@ -127,7 +133,48 @@ def load(path=OUT):
     return res
 
 
+def jacobian_rows(rs):
+    """(row index, 5 x 4 Jacobian) for every in-domain GGX row (cap and cap_extended)."""
+    out = []
+    for k, (kind, wi, ax, ay, u1, u2, wm, pdf, a, p32, note) in enumerate(rs):
+        if kind == "hemisphere" or a != a:
+            continue
+        out.append((k, vndf_mp.jacobian(u1, u2, wi, ax, ay)))
+    return out
+
+
+def render_jacobians(rs):
+    lines = [
+        "# Derivatives of the spherical-cap sample (wm) and its density (pdf) with respect to the inputs",
+        "# (wi, alpha_x, alpha_y), with the uniforms held fixed: the reparameterised gradients that an",
+        "# adjoint of Sec. 2 steps (1)-(3), Sec. 3.3 and Eq. 1 computes.  50-digit central differences",
+        "# (oracle/vndf_mp.py: jacobian), rounded to float64.",
+        "# row = index of the sample's row in cap_samples_mp50.txt (its non-comment lines, from 0).",
+        "# The 20 numbers are J[input][output], inputs " + " ".join(JAC_INPUTS) + ",",
+        "# outputs " + " ".join(JAC_OUTPUTS) + " (input-major).",
+        "# Written by tests/golden/make_golden.py from oracle/ only.",
+    ]
+    for k, jac in jacobian_rows(rs):
+        lines.append(f"{k} | " + " ".join(repr(float(v)) for row in jac for v in row))
+    return "\n".join(lines) + "\n"
+
+
+def load_jacobians(path=OUT_JAC):
+    """{row index: 5 x 4 array [input][output]}."""
+    res = {}
+    with open(path) as fh:
+        for line in fh:
+            if not line.strip() or line.startswith("#"):
+                continue
+            k, vals = line.split("|", 1)
+            res[int(k)] = np.array([float(t) for t in vals.split()]).reshape(5, 4)
+    return res
+
+
 if __name__ == "__main__":
+    rs = rows()
     with open(OUT, "w") as fh:
-        fh.write(render(rows()))
-    print(f"wrote {OUT}")
+        fh.write(render(rs))
+    with open(OUT_JAC, "w") as fh:
+        fh.write(render_jacobians(rs))
+    print(f"wrote {OUT} and {OUT_JAC}")

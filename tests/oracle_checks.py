@@ -501,6 +501,13 @@ def golden_rows():
     return make_golden.load()
 
 
+def golden_jacobians():
+    """{row index: 5 x 4 stored 50-digit Jacobian [input][output]} (tests/golden/cap_jacobians_mp50.txt)."""
+    golden_rows()  # puts tests/golden on the path
+    import make_golden
+    return make_golden.load_jacobians()
+
+
 def golden_oracle_sample(r):
     """The FP64 oracle's (wm, pdf) for one stored row.
 

@@ -128,3 +128,64 @@ def test_fp64_density_of_normal_matches_50_digits(k):
                             np.array([r["alpha_y"]]), ext)[0])
     bound = 64 * 2.0 ** -52 * max(1.0, 1.0 / r["one_plus_zi"]) * _kd(r, wm32)
     assert abs(p / r["pdf_wm32"] - 1.0) <= bound, (r["note"], p, r["pdf_wm32"])
+
+
+JACS = make_golden.load_jacobians()
+
+
+def _jacobian_amplification(r):
+    """FP64 rounding amplification of the oracle's derivatives at one row: 1 / (1 + z_i') (the cap
+    bottom -z_i' subtracted), 1 / (1 - u2) and 1 / sqrt(u2 a) (the cap height and sin(theta) formed
+    as the paper writes them), |wi| / |wi.z| (grazing incidence)."""
+    a, u2 = r["one_plus_zi"], r["u2"]
+    amp = max(1.0, 1.0 / a) * max(1.0, 1.0 / (1.0 - u2), 1.0 / math.sqrt(u2 * a) if u2 > 0 else 1.0)
+    return amp * max(1.0, float(np.linalg.norm(r["wi"])) / abs(r["wi"][2]))
+
+
+def test_jacobian_fixture_is_what_the_script_writes():
+    pytest.importorskip("mpmath")
+    with open(make_golden.OUT_JAC) as fh:
+        assert fh.read() == make_golden.render_jacobians(make_golden.rows())
+
+
+def test_jacobian_fixture_covers_every_ggx_row():
+    want = {k for k, r in enumerate(ROWS) if r["kind"] != "hemisphere" and not math.isnan(r["one_plus_zi"])}
+    assert set(JACS) == want
+
+
+def test_jacobian_closed_forms_at_normal_incidence():
+    """alpha = 1, wi = z, u2 = 0 (cap top): h = i + z, so wm = normalize(wx, wy, 1 + wz) and
+    d wm_x / d wi_x = d wm_y / d wi_y = 1/2; the density there is D = 1 / (pi ax ay), so
+    d pdf / d alpha_x = d pdf / d alpha_y = -1 / pi."""
+    J = JACS[0]
+    assert abs(J[0, 0] - 0.5) < 1e-15 and abs(J[1, 1] - 0.5) < 1e-15
+    assert abs(J[3, 3] + 1 / math.pi) < 1e-15 and abs(J[4, 3] + 1 / math.pi) < 1e-15
+
+
+def test_jacobian_scale_invariance_in_wi():
+    """The sampler and its density are invariant to the length of wi (Sec. 2 normalises it):
+    J^T wi = 0 for every output."""
+    for k, J in JACS.items():
+        wi = ROWS[k]["wi"]
+        for j in range(4):
+            col = J[:3, j]
+            assert abs(col @ wi) <= 1e-9 * max(np.abs(col).max() * np.linalg.norm(wi), 1e-300), (k, j)
+
+
+@pytest.mark.parametrize("k", [k for k in sorted(JACS)
+                               if 64 * 2.0 ** -52 * _jacobian_amplification(ROWS[k]) <= 1e-3])
+def test_fp64_complex_step_matches_50_digit_jacobian(k):
+    """The FP64 oracle's complex-step derivatives (oracle/grad.py) against the stored 50-digit ones,
+    column by column, within 64 ulp times the row's rounding amplification.  Rows where that bound
+    exceeds 1e-3 (1 + z_i' near 1e-12) are beyond FP64 and left out; there the stored values are
+    the reference."""
+    from oracle import grad
+    r = ROWS[k]
+    tol = 64 * 2.0 ** -52 * _jacobian_amplification(r)
+    Jc = grad.jacobian_complex_step(np.array([r["u1"]]), np.array([r["u2"]]), r["wi"].reshape(3, 1),
+                                    np.array([r["alpha_x"]]), np.array([r["alpha_y"]]), "cap",
+                                    r["kind"] == "cap_extended")[:, :, 0]
+    J = JACS[k]
+    for j in range(4):
+        err = np.linalg.norm(Jc[:, j] - J[:, j])
+        assert err <= tol * max(np.linalg.norm(J[:, j]), 1e-300), (r["note"], j, err)
