@@ -17,6 +17,10 @@ Steps (Dupuy & Benyoub, HPG 2023):
   differences of the same steps at 50 digits with step 1e-20, written with the exact identities
   1 - z = u2 (1 + i.z) (so 1 - z^2 = u2 a (2 - u2 a), a = 1 + i.z) and h.z = (1 - u2) a, so that no
   rounding at 1e-50 is divided by the step
+* reflection sampling (``reflection``, App. A): wo = 2 (wi.wm) wm - wi (Eq. reflect) for unit wi,
+  the density of wo, pdf(wm) / (4 wi.wm), and the estimator weight F(wi.wm) G2 / G1(wi) with
+  Schlick's F = f0 + (1 - f0)(1 - wi.wm)^5 and the height-correlated G2 = Gi Go / (Gi + Go - Gi Go),
+  G1(w) = 2 w.z / (w.z + |M^-1 w|) (unit w above the surface); weight 0 when wo.z <= 0
 * the density of a given normal (``pdf_of_normal``): max(0, wi.wm) D(wm) / sigma(wi)
   with the GGX D of App. A and the projected area sigma(wi) = (|M^-1 wi| + wi.z) / 2
   of unit wi (Eq. 4 carried through the stretch; G1(wi) / wi.z = 1 / sigma(wi))
@@ -106,3 +110,27 @@ def jacobian(u1, u2, wi, ax, ay):
             fm = _forward(u1, u2, *xm)
             out.append([float((p - m) / (2 * step)) for p, m in zip(fp, fm)])
         return out
+
+
+def reflection(u1, u2, wi, ax, ay, f0):
+    """(wo (3 floats), pdf of wo, weight) for one upper-domain sample, at 50 digits."""
+    with mpmath.workdps(DIGITS):
+        u1, u2, ax, ay, f0 = (mpmath.mpf(float(t)) for t in (u1, u2, ax, ay, f0))
+        w = [mpmath.mpf(float(t)) for t in wi]
+        mx, my, mz, pdf_m = _forward(u1, u2, *w, ax, ay)
+        n = mpmath.sqrt(w[0] ** 2 + w[1] ** 2 + w[2] ** 2)
+        ux, uy, uz = w[0] / n, w[1] / n, w[2] / n
+        d = ux * mx + uy * my + uz * mz
+        ox, oy, oz = 2 * d * mx - ux, 2 * d * my - uy, 2 * d * mz - uz
+        pdf_o = pdf_m / (4 * d)
+
+        def g1(x, y, z):
+            return 2 * z / (z + mpmath.sqrt((ax * x) ** 2 + (ay * y) ** 2 + z * z))
+
+        if oz <= 0:
+            weight = mpmath.mpf(0)
+        else:
+            gi, go = g1(ux, uy, uz), g1(ox, oy, oz)
+            fr = f0 + (1 - f0) * (1 - d) ** 5
+            weight = fr * go / (gi + go - gi * go)
+        return (float(ox), float(oy), float(oz)), float(pdf_o), float(weight)

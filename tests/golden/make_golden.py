@@ -1,12 +1,14 @@
-"""Writes cap_samples_mp50.txt and cap_jacobians_mp50.txt: stored expected samples of the
-spherical-cap sampler and their derivatives.
+"""Writes cap_samples_mp50.txt, cap_jacobians_mp50.txt and reflection_mp50.txt: stored
+expected samples of the spherical-cap sampler, their derivatives, and reflection sampling
+through them.
 
 Every expected value comes from the oracle alone: the 50-digit evaluation of
 Sec. 2 steps (1)-(3) with the Sec. 3.3 cap sampler and the density of Eq. 1
 (``oracle.vndf_mp.sample_with_pdf``), and, for inputs outside the sampler's
 domain, the fallback the oracle defines (``oracle.vndf.in_domain``; normal
 (0, 0, 1), density 0); the derivatives of each in-domain sample with respect to
-(wi, alpha) at fixed u come from ``oracle.vndf_mp.jacobian``.  Nothing here calls
+(wi, alpha) at fixed u come from ``oracle.vndf_mp.jacobian``, the reflected
+directions, their densities and estimator weights from ``oracle.vndf_mp.reflection``.  Nothing here calls
 the CUDA library.
 
 The inputs are fixed float32 values chosen to reach the places where a
@@ -30,6 +32,8 @@ from oracle import vndf, vndf_mp  # noqa: E402
 
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "cap_samples_mp50.txt")
 OUT_JAC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "cap_jacobians_mp50.txt")
+OUT_REFL = os.path.join(os.path.dirname(os.path.abspath(__file__)), "reflection_mp50.txt")
+REFL_F0 = 0.04
 JAC_INPUTS = ("wi_x", "wi_y", "wi_z", "alpha_x", "alpha_y")
 JAC_OUTPUTS = ("wm_x", "wm_y", "wm_z", "pdf")
 ONE_M = 1.0 - 2.0 ** -24  # largest float32 uniform below 1
@@ -159,6 +163,48 @@ def render_jacobians(rs):
     return "\n".join(lines) + "\n"
 
 
+def reflection_rows(rs):
+    """(row index, wo, pdf, weight) for every upper-domain cap row; out-of-domain rows give the
+    fallback (0, 0, 1), 0, 0."""
+    out = []
+    for k, (kind, wi, ax, ay, u1, u2, wm, pdf, a, p32, note) in enumerate(rs):
+        if kind != "cap":
+            continue
+        if a != a:
+            out.append((k, (0.0, 0.0, 1.0), 0.0, 0.0))
+        else:
+            out.append((k, *vndf_mp.reflection(u1, u2, wi, ax, ay, REFL_F0)))
+    return out
+
+
+def render_reflection(rs):
+    lines = [
+        "# Reflection sampling through the spherical-cap sampler (App. A), 50 digits, rounded to float64:",
+        "# for each upper-domain row of cap_samples_mp50.txt (its sample wm), wo = 2 (wi.wm) wm - wi with",
+        "# unit wi (Eq. reflect), the density of wo, pdf(wm) / (4 wi.wm), and the estimator weight",
+        "# F(wi.wm) G2 / G1(wi) (Schlick's F with f0 = %r, height-correlated G2; 0 when wo.z <= 0)." % REFL_F0,
+        "# Outside the domain: wo = (0, 0, 1), pdf = 0, weight = 0.",
+        "# row | wo_x wo_y wo_z pdf weight",
+        "# Written by tests/golden/make_golden.py from oracle/ only.",
+    ]
+    for k, wo, p, w in reflection_rows(rs):
+        lines.append(f"{k} | " + " ".join(repr(float(t)) for t in (*wo, p, w)))
+    return "\n".join(lines) + "\n"
+
+
+def load_reflection(path=OUT_REFL):
+    """{row index: (wo (3,), pdf, weight)}."""
+    res = {}
+    with open(path) as fh:
+        for line in fh:
+            if not line.strip() or line.startswith("#"):
+                continue
+            k, vals = line.split("|", 1)
+            v = [float(t) for t in vals.split()]
+            res[int(k)] = (np.array(v[:3]), v[3], v[4])
+    return res
+
+
 def load_jacobians(path=OUT_JAC):
     """{row index: 5 x 4 array [input][output]}."""
     res = {}
@@ -177,4 +223,6 @@ if __name__ == "__main__":
         fh.write(render(rs))
     with open(OUT_JAC, "w") as fh:
         fh.write(render_jacobians(rs))
-    print(f"wrote {OUT} and {OUT_JAC}")
+    with open(OUT_REFL, "w") as fh:
+        fh.write(render_reflection(rs))
+    print(f"wrote {OUT}, {OUT_JAC} and {OUT_REFL}")

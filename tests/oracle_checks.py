@@ -508,6 +508,13 @@ def golden_jacobians():
     return make_golden.load_jacobians()
 
 
+def golden_reflection():
+    """{row index: (wo (3,), pdf, weight)} stored at 50 digits (tests/golden/reflection_mp50.txt)."""
+    golden_rows()
+    import make_golden
+    return make_golden.load_reflection()
+
+
 def golden_oracle_sample(r):
     """The FP64 oracle's (wm, pdf) for one stored row.
 

@@ -189,3 +189,55 @@ def test_fp64_complex_step_matches_50_digit_jacobian(k):
     for j in range(4):
         err = np.linalg.norm(Jc[:, j] - J[:, j])
         assert err <= tol * max(np.linalg.norm(J[:, j]), 1e-300), (r["note"], j, err)
+
+
+REFL = make_golden.load_reflection()
+
+
+def test_reflection_fixture_is_what_the_script_writes():
+    pytest.importorskip("mpmath")
+    with open(make_golden.OUT_REFL) as fh:
+        assert fh.read() == make_golden.render_reflection(make_golden.rows())
+
+
+def test_reflection_closed_form_at_normal_incidence():
+    """alpha = 1, wi = z, wm = z: wo = z, its density pdf(wm) / 4 = 1 / (4 pi), and the weight is
+    F(1) G2 / G1 = f0 (G1 = G2 = 1 at normal incidence and exit)."""
+    wo, p, w = REFL[0]
+    assert tuple(wo) == (0.0, 0.0, 1.0)
+    assert abs(p * 4 * math.pi - 1.0) < 1e-15 and abs(w - make_golden.REFL_F0) < 1e-17
+
+
+def test_reflection_rows_are_consistent():
+    """|wo| = 1, wo.z <= 0 exactly where the weight is 0, and 0 <= weight <= 1 (energy)."""
+    for k, (wo, p, w) in REFL.items():
+        if math.isnan(ROWS[k]["one_plus_zi"]):
+            continue
+        assert abs(np.linalg.norm(wo) - 1.0) < 1e-15
+        assert (wo[2] <= 0) == (w == 0.0)
+        assert 0.0 <= w <= 1.0 and p > 0.0
+
+
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")  # out-of-domain lanes divide by zero before the select
+@pytest.mark.parametrize("k", sorted(REFL))
+def test_fp64_reflection_matches_50_digits(k):
+    """The FP64 oracle's sample_reflection (oracle/microfacet.py: reflect, bsdf_pdf through G1 and D,
+    estimator_weight through the BRDF of Eq. microfacet) against the stored 50-digit values, which
+    take the density as pdf(wm) / (4 wi.wm) and the weight as F G2 / G1: different routes.  The
+    oracle's weight divides D at the recomputed half vector normalize(wi + wo) by D at wm; D varies
+    on the angular scale of alpha, so that ratio carries the rounding times 1 / alpha."""
+    from oracle import microfacet
+    r = ROWS[k]
+    wo_ref, p_ref, w_ref = REFL[k]
+    wo, p, w = microfacet.sample_reflection(np.array([r["u1"]]), np.array([r["u2"]]), r["wi"].reshape(3, 1),
+                                            np.array([r["alpha_x"]]), np.array([r["alpha_y"]]), make_golden.REFL_F0)
+    wo, p, w = wo[:, 0], float(p[0]), float(w[0])
+    if math.isnan(r["one_plus_zi"]):
+        assert tuple(wo) == (0.0, 0.0, 1.0) and p == 0.0 and w == 0.0
+        return
+    tol = 64 * 2.0 ** -52 * _jacobian_amplification(r)
+    ang = math.atan2(float(np.linalg.norm(np.cross(wo, wo_ref))), float(wo @ wo_ref))
+    assert ang <= 2 * tol, (r["note"], ang)
+    assert abs(p / p_ref - 1.0) <= 4 * tol, (r["note"], p, p_ref)
+    wtol = 4 * tol * max(1.0, 1.0 / min(r["alpha_x"], r["alpha_y"]))
+    assert abs(w - w_ref) <= wtol * max(w_ref, 1e-300) or (w == 0.0 and w_ref == 0.0), (r["note"], w, w_ref)
