@@ -334,8 +334,10 @@ size_t vndf_albedo_workspace_bytes(int32_t n_queries, int32_t max_samples_per_qu
  *   config             NULL (use the configuration vndf_albedo_autotune picked
  *                      on this device, else a default) or three int32 on the
  *                      host: warps per CTA (1-16), 256-sample groups per work
- *                      item (1-256; each warp takes whole items in turn), CTAs
- *                      per SM (1-32).
+ *                      item (1-256; each warp takes a contiguous run of whole
+ *                      items, the runs of all warps within one item of each
+ *                      other), CTAs per SM (1-32; capped at the number an SM
+ *                      holds at once, so that every CTA starts immediately).
  * The summation order is fixed by the data (256-sample groups, then groups in
  * order), so E is bit-identical for every config, every split of the queries
  * into calls, and every replay of a captured CUDA graph.

@@ -16,10 +16,12 @@
 //   the data, not of the launch, so E is bit-identical for every launch shape.
 // * An item is `groups_per_item` consecutive groups of one query.  A one-block
 //   prologue computes per-query item counts and their exclusive scan; each warp
-//   of the persistent kernel then takes items w, w + W, w + 2W, ... (W = warps
-//   in the grid) on its own, with no block barrier, writes one partial per
-//   group, and the warp that completes a query's last item sums the query's
-//   group partials (fixed lane-strided order + butterfly) into E_q.
+//   of the persistent kernel (only as many CTAs as the SMs hold at once) then
+//   takes a contiguous run of about total / W items (W = warps in the grid) on
+//   its own, with no block barrier, and writes one partial per group.  When it
+//   leaves a query it adds the number of that query's items it did to the
+//   query's counter; the warp whose addition completes the query sums the
+//   query's group partials (fixed lane-strided order + butterfly) into E_q.
 // * Nothing waits on anything: completion is detected with an atomic counter
 //   per query (fence, then atomicAdd), so no warp ever spins.  The one barrier
 //   is at CTA start, after the item offsets are copied into shared memory.
@@ -51,7 +53,7 @@ struct AlbedoArgs {
   float f0;
   Rng rng;  // rng.stream is the stream id of query 0
   float* E;
-  int32_t* ctl;     // [0] next item, [1] total items, [2 .. 2+nq] item offsets, then done[nq]
+  int32_t* ctl;     // [0] reserved (0), [1] total items, [2 .. 2+nq] item offsets, then done[nq]
   float* partials;  // nq * gmax group sums
 };
 
@@ -167,6 +169,17 @@ __device__ __forceinline__ float warp_tree(float v) {
 }
 
 // ---------------------------------------------------------------- persistent kernel
+// The item's query: the last q with offsets[q] <= item (every lane runs the same search).
+__device__ __forceinline__ int32_t item_query(const int32_t* offsets, int32_t nq, int32_t item) {
+  int32_t lo = 0, hi = nq - 1;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if (offsets[mid] <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 __global__ void __launch_bounds__(512) albedo_kernel(AlbedoArgs a) {
   extern __shared__ int32_t s_offsets[];
   const int lane = threadIdx.x & 31;
@@ -179,23 +192,51 @@ __global__ void __launch_bounds__(512) albedo_kernel(AlbedoArgs a) {
   }
   int32_t* done = a.ctl + 3 + a.nq;
   const int32_t total = a.ctl[1];
-  for (int64_t item = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); item < total;
-       item += warps) {
-    // the query of this item: last q with offsets[q] <= item (same search in every lane)
-    int32_t lo = 0, hi = a.nq - 1;
-    while (lo < hi) {
-      const int32_t mid = (lo + hi + 1) >> 1;
-      if (offsets[mid] <= int32_t(item)) lo = mid;
-      else hi = mid - 1;
+  // Each warp takes a contiguous run of items, the runs differing in length by at most one
+  // item: the warps finish together, and the query changes only at the run's query
+  // boundaries, so its search, its per-query constants and its completion count are paid
+  // once per query and run, not per item.
+  const int64_t w = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int32_t it0 = int32_t(w * total / warps), it1 = int32_t((w + 1) * total / warps);
+  if (it0 >= it1) return;
+  int32_t q = item_query(offsets, a.nq, it0);
+  int32_t n = a.ns[q];
+  int32_t groups = (n + kGroupSamples - 1) / kGroupSamples;
+  QueryConst c = query_const(a, q);
+  Rng r = a.rng;
+  r.stream = a.rng.stream + uint32_t(q);
+  int32_t mine = 0;  // items of query q done by this warp since the last count
+  // Adds this warp's items of query q to its completion count; the warp whose addition
+  // completes the query sums the query's group partials (fixed order) into E_q.
+  auto finish = [&]() {
+    int32_t last = 0;
+    if (lane == 0) {
+      __threadfence();
+      const int32_t items_q = offsets[q + 1] - offsets[q];
+      last = atomicAdd(done + q, mine) + mine == items_q;
     }
-    const int32_t q = lo;
-    const int32_t n = a.ns[q];
-    const int32_t groups = (n + kGroupSamples - 1) / kGroupSamples;
-    const int32_t k = int32_t(item) - offsets[q];
+    if (__shfl_sync(0xffffffffu, last, 0)) {
+      __threadfence();
+      float sum = 0.f;
+      for (int32_t g = lane; g < groups; g += 32) sum += __ldcg(a.partials + size_t(q) * a.gmax + g);
+      sum = warp_tree(sum);
+      if (lane == 0) a.E[q] = sum / float(n);
+    }
+    mine = 0;
+  };
+  for (int32_t item = it0; item < it1; ++item) {
+    if (offsets[q + 1] <= item) {  // next query with items (queries without items are skipped)
+      finish();
+      do {
+        ++q;
+      } while (offsets[q + 1] <= item);
+      n = a.ns[q];
+      groups = (n + kGroupSamples - 1) / kGroupSamples;
+      c = query_const(a, q);
+      r.stream = a.rng.stream + uint32_t(q);
+    }
+    const int32_t k = item - offsets[q];
     const int32_t g_end = min(groups, (k + 1) * a.groups_per_item);
-    const QueryConst c = query_const(a, q);
-    Rng r = a.rng;
-    r.stream = a.rng.stream + uint32_t(q);
     for (int32_t g = k * a.groups_per_item; g < g_end; ++g) {
       const int32_t j0 = g * kGroupSamples + lane * kLaneSamples;
       float acc = 0.f;
@@ -211,20 +252,9 @@ __global__ void __launch_bounds__(512) albedo_kernel(AlbedoArgs a) {
       acc = warp_tree(acc);
       if (lane == 0) a.partials[size_t(q) * a.gmax + g] = acc;
     }
-    int32_t last = 0;
-    if (lane == 0) {
-      __threadfence();
-      const int32_t items_q = offsets[q + 1] - offsets[q];
-      last = atomicAdd(done + q, 1) == items_q - 1;
-    }
-    if (__shfl_sync(0xffffffffu, last, 0)) {
-      __threadfence();
-      float sum = 0.f;
-      for (int32_t g = lane; g < groups; g += 32) sum += __ldcg(a.partials + size_t(q) * a.gmax + g);
-      sum = warp_tree(sum);
-      if (lane == 0) a.E[q] = sum / float(n);
-    }
+    ++mine;
   }
+  finish();
 }
 
 // ---------------------------------------------------------------- launch configuration
@@ -253,8 +283,16 @@ AlbedoConfig current_config() {
 int launch_albedo(AlbedoArgs a, const AlbedoConfig& c, cudaStream_t s) {
   a.groups_per_item = c.groups_per_item;
   albedo_prologue_kernel<<<1, 1024, 0, s>>>(a);
-  const unsigned grid = static_cast<unsigned>(sm_count() * c.ctas_per_sm);
   const size_t smem = a.nq + 1 <= kCachedOffsets ? size_t(a.nq + 1) * sizeof(int32_t) : 0;
+  // Every CTA must be resident from the start: the item runs are cut for the whole grid, and
+  // a CTA that waited for a free slot would finish its run after the others.
+  int resident = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, albedo_kernel, 32 * c.block_warps, smem) !=
+          cudaSuccess ||
+      resident < 1)
+    resident = 1;
+  const int ctas = c.ctas_per_sm < resident ? c.ctas_per_sm : resident;
+  const unsigned grid = static_cast<unsigned>(sm_count() * ctas);
   albedo_kernel<<<grid, 32 * c.block_warps, smem, s>>>(a);
   return launch_status();
 }
