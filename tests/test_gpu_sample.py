@@ -222,3 +222,61 @@ def test_full_size_anisotropic_stream_sampled(v):
     print("full size sampled", st)
     del d, out
     torch.cuda.empty_cache()
+
+
+@pytest.mark.slow
+def test_indices_beyond_int32(v):
+    """2^31 + 4101 samples in one call (77 GB of inputs and outputs): element indices past 2^31 and
+    Philox counters past 2^31 must be formed in 64 bits, and the n % 4 = 1 tail must run.  The
+    inputs tile a 2^20 + 3 block of the anisotropic workload (an odd period, so every residue mod 4
+    meets every input); outputs are checked at the int32 boundaries, the end and random windows
+    against the oracle with the same uniforms, and vndf_pdf is run over the same normals.
+    Only this library's kernels touch the full arrays: they are filled and read back through
+    slices, each a separate copy of at most 2^20 + 3 elements (torch's gather kernel asserts on
+    tensors of more than 2^31 elements)."""
+    n = (1 << 31) + 4101  # n % 4 = 1
+    free, _ = torch.cuda.mem_get_info()
+    if free < 100 * (1 << 30):
+        pytest.skip(f"needs about 86 GB of free device memory, {free / 2**30:.0f} GB free")
+    period = (1 << 20) + 3
+    blk = workloads.anisotropic_stream(n=period, seed=41, device=DEV)
+    d = {}
+    for k, t in blk.items():
+        x = torch.empty(n, dtype=torch.float32, device=DEV)
+        for s0 in range(0, n, period):
+            m = min(period, n - s0)
+            x[s0:s0 + m].copy_(t[:m])
+        d[k] = x
+    out = v.vndf_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], seed=9, counter_base=3)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(1)
+    L = 64
+    starts = np.unique(np.concatenate([[0, (1 << 30) - L // 2, (1 << 31) - L // 2, n - L],
+                                       rng.integers(0, n - L, 60)]))
+    idx = np.concatenate([s0 + np.arange(L) for s0 in starts])
+
+    assert starts.max() + L <= n
+
+    def gather(t):
+        return np.concatenate([t[int(s0):int(s0) + L].cpu().numpy() for s0 in starts])
+
+    blk_np = {k: t.cpu().numpy() for k, t in blk.items()}
+    wi = np.stack([blk_np[k][idx % period] for k in ("wi_x", "wi_y", "wi_z")])
+    ax, ay = blk_np["alpha_x"][idx % period], blk_np["alpha_y"][idx % period]
+    for k in ("wi_x", "alpha_y"):  # the tiled inputs themselves, at the same windows
+        assert np.array_equal(gather(d[k]), blk_np[k][idx % period])
+    wm = np.stack([gather(o) for o in out[:3]])
+    pdf = gather(out[3])
+    u1, u2 = philox.uniforms_at(9, 3, 0, idx)
+    st = parity.compare_cap(wm, pdf, u1, u2, wi, ax, ay)
+    print("beyond int32", st)
+    # the density entry over the same normals
+    p2 = v.vndf_pdf(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], out[0], out[1], out[2])
+    torch.cuda.synchronize()
+    p2s = gather(p2).astype(np.float64)
+    wi64, wm64 = wi.astype(np.float64), wm.astype(np.float64)
+    ref = ovndf.vndf_pdf(wm64, wi64, ax.astype(np.float64), ay.astype(np.float64))
+    kd = (np.abs(wi64 * wm64).sum(0) / np.abs(ovndf.dot(wi64, wm64))) / np.sqrt(ovndf.dot(wi64, wi64))
+    assert np.all(np.abs(p2s / ref - 1.0) <= np.maximum(1e-5, parity.K_ULP * (kd + 8.0) * parity.EPS32))
+    del d, out, p2
+    torch.cuda.empty_cache()
