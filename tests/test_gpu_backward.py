@@ -221,3 +221,81 @@ def test_full_size_fused_loss_sampled(v):
     got = np.stack([pick(t) for t in (gx, gy, gz, gax, gay)])
     _check_errors(_errors(got, ref), "full-size fused gradients")
     assert np.isfinite(loss.item())
+
+
+def _tiled(blk, n, period):
+    """Device copies of blk's arrays tiled to length n, written slice by slice (no torch kernel
+    runs over more than `period` elements)."""
+    out = {}
+    for k, t in blk.items():
+        x = torch.empty(n, dtype=torch.float32, device=DEV)
+        for s0 in range(0, n, period):
+            m = min(period, n - s0)
+            x[s0:s0 + m].copy_(t[:m])
+        out[k] = x
+    return out
+
+
+@pytest.mark.slow
+def test_adjoints_beyond_int32(v):
+    """The fused forward+loss+adjoint and the generic adjoint over one call of 2^31 + 4101 samples
+    (about 112 GB): 64-bit element indices, Philox counters and loss-partial indices past 2^31.
+    The inputs tile a 2^20 + 3 block.  The loss workspace is filled with NaN first, so a partial
+    that no warp wrote would show; every partial is finite, the loss equals their sum, the partials
+    of 128-sample groups at the 2^31 boundary, the end and random places equal the oracle's sums of
+    the same terms, and the gradients there match the oracle's complex-step products."""
+    n = (1 << 31) + 4101
+    free, _ = torch.cuda.mem_get_info()
+    if free < 130 * (1 << 30):
+        pytest.skip(f"needs about 120 GB of free device memory, {free / 2**30:.0f} GB free")
+    period = (1 << 20) + 3
+    blk = workloads.adjoint_2e24(n=period, seed=42, device=DEV)
+    d = _tiled(blk, n, period)
+    blk_np = {k: t.cpu().numpy().astype(np.float64) for k, t in blk.items()}
+    nbytes = v.vndf_loss_workspace_bytes(n)
+    ws = torch.full(((nbytes + 3) // 4,), float("nan"), dtype=torch.float32, device=DEV)
+    loss, gx, gy, gz, gax, gay = v.vndf_sample_loss_backward(
+        d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], d["c_x"], d["c_y"], d["c_z"], seed=5,
+        counter_base=7, workspace=ws.view(torch.uint8))
+    torch.cuda.synchronize()
+    groups = (n + 127) // 128
+    partials = ws[:groups].cpu().numpy().astype(np.float64)
+    assert np.isfinite(partials).all()
+    got = float(loss.item())
+    assert abs(got - partials.sum()) <= 1e-6 * np.abs(partials).sum()
+    rng = np.random.default_rng(2)
+    gsel = np.unique(np.concatenate([[0, (1 << 31) // 128 - 1, (1 << 31) // 128, groups - 1],
+                                     rng.integers(0, groups, 60)]))
+    idx = np.concatenate([np.arange(128 * g, min(128 * g + 128, n)) for g in gsel])
+
+    def gather(t):
+        return np.concatenate([t[128 * int(g):min(128 * int(g) + 128, n)].cpu().numpy() for g in gsel])
+
+    wi = np.stack([blk_np[k][idx % period] for k in ("wi_x", "wi_y", "wi_z")])
+    ax, ay = blk_np["alpha_x"][idx % period], blk_np["alpha_y"][idx % period]
+    c = np.stack([blk_np[k][idx % period] for k in ("c_x", "c_y", "c_z")])
+    u1, u2 = philox.uniforms_at(5, 7, 0, idx)
+    wm, pdf = ovndf.sample_vndf_with_pdf(u1, u2, wi, ax, ay)
+    terms = ovndf.dot(c, wm) + np.log(pdf)
+    # partials of the selected groups against the oracle's sums of the same 128 terms
+    bounds = np.cumsum([0] + [min(128 * int(g) + 128, n) - 128 * int(g) for g in gsel])
+    for j, g in enumerate(gsel):
+        t = terms[bounds[j]:bounds[j + 1]]
+        assert abs(partials[g] - t.sum()) <= 1e-5 * np.abs(t).sum(), (g, partials[g], t.sum())
+    rwi, rax, ray = grad.vjp(u1, u2, wi, ax, ay, c, 1.0 / pdf)
+    ref = np.concatenate([rwi, rax[None], ray[None]])
+    got_g = np.stack([gather(t).astype(np.float64) for t in (gx, gy, gz, gax, gay)])
+    _check_errors(_errors(got_g, ref), "fused gradients beyond int32")
+    del gx, gy, gz, gax, gay, ws
+    torch.cuda.empty_cache()
+    # the generic adjoint with g_wm = c and no density term, over the same inputs
+    gx, gy, gz, gax, gay = v.vndf_sample_backward(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"],
+                                                  seed=5, counter_base=7, g_wm_x=d["c_x"], g_wm_y=d["c_y"],
+                                                  g_wm_z=d["c_z"])
+    torch.cuda.synchronize()
+    rwi, rax, ray = grad.vjp(u1, u2, wi, ax, ay, c, np.zeros_like(pdf))
+    ref = np.concatenate([rwi, rax[None], ray[None]])
+    got_g = np.stack([gather(t).astype(np.float64) for t in (gx, gy, gz, gax, gay)])
+    _check_errors(_errors(got_g, ref), "generic gradients beyond int32")
+    del d, gx, gy, gz, gax, gay
+    torch.cuda.empty_cache()
