@@ -230,7 +230,8 @@ def test_indices_beyond_int32(v):
     Philox counters past 2^31 must be formed in 64 bits, and the n % 4 = 1 tail must run.  The
     inputs tile a 2^20 + 3 block of the anisotropic workload (an odd period, so every residue mod 4
     meets every input); outputs are checked at the int32 boundaries, the end and random windows
-    against the oracle with the same uniforms, and vndf_pdf is run over the same normals.
+    against the oracle with the same uniforms; vndf_pdf is run over the same normals, and reflection
+    sampling and the hemisphere sampler over the same inputs.
     Only this library's kernels touch the full arrays: they are filled and read back through
     slices, each a separate copy of at most 2^20 + 3 elements (torch's gather kernel asserts on
     tensors of more than 2^31 elements)."""
@@ -278,5 +279,31 @@ def test_indices_beyond_int32(v):
     ref = ovndf.vndf_pdf(wm64, wi64, ax.astype(np.float64), ay.astype(np.float64))
     kd = (np.abs(wi64 * wm64).sum(0) / np.abs(ovndf.dot(wi64, wm64))) / np.sqrt(ovndf.dot(wi64, wi64))
     assert np.all(np.abs(p2s / ref - 1.0) <= np.maximum(1e-5, parity.K_ULP * (kd + 8.0) * parity.EPS32))
-    del d, out, p2
+    del out, p2
+    torch.cuda.empty_cache()
+    # reflection sampling over the same inputs, with the bounds of test_gpu_reflection.py
+    from oracle import microfacet
+    from test_gpu_reflection import _weight_sensitivity
+    ax64, ay64 = ax.astype(np.float64), ay.astype(np.float64)
+    refl = v.vndf_sample_reflection(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], seed=9,
+                                    counter_base=3, f0=0.04)
+    torch.cuda.synchronize()
+    got = np.stack([gather(t) for t in refl[:3]]).astype(np.float64)
+    pg, wg = (gather(t).astype(np.float64) for t in refl[3:])
+    wb, pr, wr = microfacet.sample_reflection(u1, u2, wi64, ax64, ay64, 0.04)
+    assert parity.angle_between(got, wb).max() <= 2 * parity.ANGLE_TOL
+    assert np.abs(pg / pr - 1.0).max() <= parity.PDF_TOL
+    sens = _weight_sensitivity(u1, u2, wi64, ax64, ay64, 0.04)
+    assert np.all(np.abs(wg - wr) <= 1e-5 * np.abs(wr) + 1e-7 + sens * parity.ANGLE_TOL)
+    del refl
+    torch.cuda.empty_cache()
+    # the hemisphere sampler over the same directions
+    hemi = v.vndf_sample_hemisphere(d["wi_x"], d["wi_y"], d["wi_z"], seed=9, counter_base=3)
+    torch.cuda.synchronize()
+    hm = np.stack([gather(t) for t in hemi[:3]]).astype(np.float64)
+    hp = gather(hemi[3]).astype(np.float64)
+    href, hpref = ovndf.sample_hemisphere(u1, u2, wi64)
+    assert parity.angle_between(hm, href).max() <= parity.ANGLE_TOL
+    assert np.quantile(np.abs(hp / hpref - 1.0), 0.999) <= parity.PDF_TOL
+    del d, hemi
     torch.cuda.empty_cache()
