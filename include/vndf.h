@@ -267,7 +267,8 @@ int vndf_sample_backward_extended(int64_t n,
                                   void *cuda_stream);
 
 /* Device workspace (bytes) that vndf_sample_loss_backward needs for n samples:
- * one float per 128-sample group.  0 for n <= 0. */
+ * one float per 128-sample group, one per segment of 2048 groups, and a
+ * counter.  0 for n <= 0. */
 size_t vndf_loss_workspace_bytes(int64_t n);
 
 /*
@@ -281,8 +282,10 @@ size_t vndf_loss_workspace_bytes(int64_t n);
  *   c_x, c_y, c_z       per-sample weight vectors (device).
  *   g_wi_*, g_alpha_*   outputs as in vndf_sample_backward (NULL = skip).
  *   loss                output, one float (device).  It is summed per fixed
- *                       128-sample group and then over groups in index
- *                       order, so it is bit-reproducible for a given n.
+ *                       128-sample group, then per fixed segment of 2048
+ *                       groups, then over the segments, each level in an
+ *                       order that depends only on n, so it is
+ *                       bit-reproducible for a given n.
  *   workspace           device scratch of >= vndf_loss_workspace_bytes(n)
  *                       bytes, owned by the caller; its contents on entry are
  *                       ignored.  Concurrent calls need separate workspaces.

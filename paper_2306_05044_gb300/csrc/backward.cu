@@ -246,7 +246,9 @@ __device__ __forceinline__ float block_sum(float v, float* smem) {
 
 template <bool PHILOX, bool ISO, bool VEC>
 __global__ void __launch_bounds__(kBwdBlock, 3) loss_backward_kernel(BwdArgs a, int64_t n, int64_t ch0,
-                                                                  int64_t chunks, float* partials) {
+                                                                  int64_t chunks, float* partials,
+                                                                  unsigned* sum_counter) {
+  if (sum_counter && blockIdx.x == 0 && threadIdx.x == 0) *sum_counter = 0u;  // read by sum_partials_kernel
   for (int64_t ch = ch0 + blockIdx.x; ch < chunks; ch += gridDim.x) {
     const int64_t e = ch * kChunk + 4 * int64_t(threadIdx.x);
     float X[4], Y[4], Z[4], AX[4], AY[4], U1[4], U2[4], CX[4], CY[4], CZ[4];
@@ -366,8 +368,9 @@ __device__ __forceinline__ void loss_stage(const BwdArgs& a, int64_t e, float4* 
 // of loss_backward_kernel, so the loss does not depend on which kernel ran.
 template <bool PHILOX, bool ISO>
 __global__ void __launch_bounds__(kBwdBlock, VNDF_BWD_MIN_BLOCKS) loss_backward_pipe_kernel(BwdArgs a, int64_t chunks,
-                                                                       float* partials) {
+                                                                       float* partials, unsigned* sum_counter) {
   constexpr int NS = loss_streams_in<PHILOX, ISO>();
+  if (blockIdx.x == 0 && threadIdx.x == 0) *sum_counter = 0u;  // read by sum_partials_kernel
   extern __shared__ float4 smem_l[];  // [2][NS][kBwdBlock]
   float4* mine = smem_l + threadIdx.x;
   if (int64_t(blockIdx.x) < chunks)
@@ -430,15 +433,44 @@ __global__ void __launch_bounds__(kBwdBlock, VNDF_BWD_MIN_BLOCKS) loss_backward_
   cp_async_wait<0>();
 }
 
-// One block: thread t sums partials t, t + 1024, ... in order, then a fixed tree.
-// The unrolled loop keeps 32 loads per thread in flight; the adds stay in order.
-__global__ void __launch_bounds__(1024) sum_partials_kernel(const float* partials, int64_t m, float* out) {
+// The loss partials are summed in two fixed levels.  Segment b holds partials
+// [b * kSegPartials, (b + 1) * kSegPartials); a CTA adds a segment in a fixed order
+// (thread t takes t, t + kSumBlock, ... in turn, then a fixed tree) and stores the
+// segment sum; the CTA that finishes last (a counter that the loss kernel zeroed
+// before any CTA here started) adds the segment sums the same way.  The order
+// depends only on n, so the loss is bit-reproducible for a given n, and the work
+// is spread over many SMs instead of one.
+constexpr int kSegPartials = 2048;
+constexpr int kSumBlock = 256;
+
+__host__ __device__ inline int64_t loss_segments(int64_t groups) {
+  return (groups + kSegPartials - 1) / kSegPartials;
+}
+
+__global__ void __launch_bounds__(kSumBlock) sum_partials_kernel(const float* partials, int64_t m, float* seg,
+                                                                 int64_t nseg, unsigned* counter, float* out) {
   __shared__ float smem[32];
-  float v = 0.f;
-#pragma unroll 32
-  for (int64_t j = threadIdx.x; j < m; j += 1024) v += partials[j];
-  const float s = block_sum<1024>(v, smem);
-  if (threadIdx.x == 0) *out = s;
+  __shared__ bool last;
+  for (int64_t b = blockIdx.x; b < nseg; b += gridDim.x) {
+    const int64_t j0 = b * kSegPartials, j1 = j0 + kSegPartials < m ? j0 + kSegPartials : m;
+    float v = 0.f;
+#pragma unroll 8
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += kSumBlock) v += partials[j];
+    const float t = block_sum<kSumBlock>(v, smem);
+    if (threadIdx.x == 0) seg[b] = t;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) {  // uniform over the block
+    __threadfence();
+    float w = 0.f;
+    for (int64_t k = threadIdx.x; k < nseg; k += kSumBlock) w += __ldcg(seg + k);
+    const float t = block_sum<kSumBlock>(w, smem);
+    if (threadIdx.x == 0) *out = t;
+  }
 }
 
 template <bool PHILOX, bool ISO, bool EXT>
@@ -464,8 +496,22 @@ int launch_backward(const BwdArgs& a, int64_t n, bool vec, cudaStream_t s) {
   return launch_status();
 }
 
+// Loss workspace: the group partials, then the segment sums, then the counter.
+struct LossWorkspace {
+  float* partials;
+  float* seg;
+  unsigned* counter;
+};
+
+inline LossWorkspace loss_workspace(void* ws, int64_t n) {
+  const int64_t groups = (n + kGroup - 1) / kGroup;
+  float* p = static_cast<float*>(ws);
+  return LossWorkspace{p, p + groups, reinterpret_cast<unsigned*>(p + groups + loss_segments(groups))};
+}
+
 template <bool PHILOX, bool ISO>
-int launch_loss(const BwdArgs& a, int64_t n, bool vec, float* partials, float* loss, cudaStream_t s) {
+int launch_loss(const BwdArgs& a, int64_t n, bool vec, const LossWorkspace& w, float* loss, cudaStream_t s) {
+  float* partials = w.partials;
   const int64_t chunks = (n + kChunk - 1) / kChunk;
   const int64_t groups = (n + kGroup - 1) / kGroup;
   // the staged kernel pays off once every resident CTA gets many chunks (measured: slower at 2^22
@@ -477,17 +523,21 @@ int launch_loss(const BwdArgs& a, int64_t n, bool vec, float* partials, float* l
       constexpr size_t smem = size_t(2) * loss_streams_in<PHILOX, ISO>() * kBwdBlock * 16;
       if (!ensure_dynamic_smem<loss_backward_pipe_kernel<PHILOX, ISO>>(smem)) return VNDF_ERR_CUDA;
       loss_backward_pipe_kernel<PHILOX, ISO>
-          <<<grid_for(full * kBwdBlock, kBwdBlock, 8, VNDF_BWD_WAVES), kBwdBlock, smem, s>>>(a, full, partials);
+          <<<grid_for(full * kBwdBlock, kBwdBlock, 8, VNDF_BWD_WAVES), kBwdBlock, smem, s>>>(a, full, partials,
+                                                                                          w.counter);
     }
-    if (full < chunks) loss_backward_kernel<PHILOX, ISO, true><<<1, kBwdBlock, 0, s>>>(a, n, full, chunks, partials);
+    if (full < chunks)
+      loss_backward_kernel<PHILOX, ISO, true><<<1, kBwdBlock, 0, s>>>(a, n, full, chunks, partials, nullptr);
   } else {
     const unsigned grid = grid_for(chunks * kBwdBlock, kBwdBlock, 8, 16);
     if (vec)
-      loss_backward_kernel<PHILOX, ISO, true><<<grid, kBwdBlock, 0, s>>>(a, n, 0, chunks, partials);
+      loss_backward_kernel<PHILOX, ISO, true><<<grid, kBwdBlock, 0, s>>>(a, n, 0, chunks, partials, w.counter);
     else
-      loss_backward_kernel<PHILOX, ISO, false><<<grid, kBwdBlock, 0, s>>>(a, n, 0, chunks, partials);
+      loss_backward_kernel<PHILOX, ISO, false><<<grid, kBwdBlock, 0, s>>>(a, n, 0, chunks, partials, w.counter);
   }
-  sum_partials_kernel<<<1, 1024, 0, s>>>(partials, groups, loss);
+  const int64_t nseg = loss_segments(groups);
+  const unsigned sgrid = static_cast<unsigned>(nseg < 65535 ? nseg : 65535);
+  sum_partials_kernel<<<sgrid, kSumBlock, 0, s>>>(partials, groups, w.seg, nseg, w.counter, loss);
   return launch_status();
 }
 
@@ -549,7 +599,8 @@ extern "C" int vndf_sample_backward_extended(int64_t n, const float* wi_x, const
 
 extern "C" size_t vndf_loss_workspace_bytes(int64_t n) {
   if (n <= 0) return 0;
-  return size_t((n + kGroup - 1) / kGroup) * sizeof(float);
+  const int64_t groups = (n + kGroup - 1) / kGroup;
+  return size_t(groups + loss_segments(groups) + 1) * sizeof(float);
 }
 
 extern "C" int vndf_sample_loss_backward(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z,
@@ -577,10 +628,10 @@ extern "C" int vndf_sample_loss_backward(int64_t n, const float* wi_x, const flo
             make_rng(seed, counter_base, stream_id)};
   const bool vec = all_aligned16(wi_x, wi_y, wi_z, alpha_x, alpha_y, c_x, c_y, c_z, u1, u2, g_wi_x, g_wi_y,
                                  g_wi_z, g_alpha_x, g_alpha_y);
-  float* partials = static_cast<float*>(workspace);
+  const LossWorkspace w = loss_workspace(workspace, n);
   if (u1)
-    return alpha_y ? launch_loss<false, false>(a, n, vec, partials, loss, s)
-                   : launch_loss<false, true>(a, n, vec, partials, loss, s);
-  return alpha_y ? launch_loss<true, false>(a, n, vec, partials, loss, s)
-                 : launch_loss<true, true>(a, n, vec, partials, loss, s);
+    return alpha_y ? launch_loss<false, false>(a, n, vec, w, loss, s)
+                   : launch_loss<false, true>(a, n, vec, w, loss, s);
+  return alpha_y ? launch_loss<true, false>(a, n, vec, w, loss, s)
+                 : launch_loss<true, true>(a, n, vec, w, loss, s);
 }
