@@ -39,3 +39,13 @@ def test_hash_covers_every_listed_file():
         assert files, kernel
         for f in files:
             assert os.path.exists(os.path.join(ROOT, "paper_2306_05044_gb300", "csrc", f)), (kernel, f)
+
+
+def test_roofline_denominators(monkeypatch, tmp_path):
+    """The HBM peak and the maximum SM clock come from MEASURED_PEAKS.json, else the stated fallbacks."""
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.hbm_peak() == (bench.FALLBACK_HBM_GBS, "fallback")
+    assert bench.max_sm_clock_mhz() == 2070.0
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6787.6, "sm_max_mhz": 2032}')
+    assert bench.hbm_peak() == (6787.6, "measured")
+    assert bench.max_sm_clock_mhz() == 2032.0
