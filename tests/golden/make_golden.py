@@ -28,7 +28,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from oracle import vndf, vndf_mp  # noqa: E402
+from oracle import vndf  # noqa: E402  (oracle.vndf_mp, which needs mpmath, is imported where it is used)
 
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "cap_samples_mp50.txt")
 OUT_JAC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "cap_jacobians_mp50.txt")
@@ -81,6 +81,7 @@ def f32(x):
 
 
 def rows():
+    from oracle import vndf_mp
     out = []
     for kind, wi, al, u, note in CASES:
         wi = tuple(f32(t) for t in wi)
@@ -139,6 +140,7 @@ def load(path=OUT):
 
 def jacobian_rows(rs):
     """(row index, 5 x 4 Jacobian) for every in-domain GGX row (cap and cap_extended)."""
+    from oracle import vndf_mp
     out = []
     for k, (kind, wi, ax, ay, u1, u2, wm, pdf, a, p32, note) in enumerate(rs):
         if kind == "hemisphere" or a != a:
@@ -166,6 +168,7 @@ def render_jacobians(rs):
 def reflection_rows(rs):
     """(row index, wo, pdf, weight) for every upper-domain cap row; out-of-domain rows give the
     fallback (0, 0, 1), 0, 0."""
+    from oracle import vndf_mp
     out = []
     for k, (kind, wi, ax, ay, u1, u2, wm, pdf, a, p32, note) in enumerate(rs):
         if kind != "cap":

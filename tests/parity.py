@@ -137,8 +137,10 @@ def compare_cap(wm_gpu, pdf_gpu, u1, u2, wi, ax, ay, strict=True, extended=False
 def compare_cap_mp(wm_gpu, pdf_gpu, u1, u2, wi, ax, ay, limit=2000):
     """Extended-domain samples with 1 + z_i' < A_MP (the FP64 oracle's weak spot) against the
     50-digit reference (oracle.vndf_mp), at the flat limits.  Checks at most ``limit`` of them."""
-    import pytest
-    mp = pytest.importorskip("oracle.vndf_mp")
+    try:
+        from oracle import vndf_mp as mp
+    except ImportError:  # no mpmath here: the stored 50-digit rows of tests/golden cover these samples
+        return {"n_mp": 0, "mp_reference": "mpmath not installed"}
     wi = np.asarray(wi, np.float64)
     ax = np.asarray(ax, np.float64)
     ay = np.asarray(ay, np.float64)
