@@ -451,15 +451,24 @@ int vndf_microbench(int64_t lanes, int32_t samples_per_lane, int method, int pre
  * pointers are HOST memory, uniforms are explicit, and the arithmetic is FP32
  * with the same rounding-aware formulas as the GPU kernels, vectorised by the
  * compiler and split over `threads` host threads (0 = all hardware threads).
- * method is any VNDF_METHOD_* (the extended cap method as in vndf_sample).  Results do not depend on the thread count.  It has no
- * double-float path, so, like the prior sampler, about 1e-5 of samples lie
- * beyond 4e-6 rad of an FP64 evaluation.
+ *   method             any VNDF_METHOD_* (the extended cap method as in
+ *                      vndf_sample).
+ *   precise            cap methods only: nonzero recomputes the samples whose
+ *                      half vector is ill-conditioned (the condition test of
+ *                      vndf_sample) in double precision, so that every sample
+ *                      meets 4e-6 rad and 1e-5 relative (wi.z >= 1e-4, alpha
+ *                      >= 1e-3), as vndf_sample does; 0 runs the plain FP32
+ *                      sampler, the accuracy class of the prior sampler (about
+ *                      1e-5 of samples beyond 4e-6 rad), which the paper's
+ *                      benchmark times.  Ignored for the prior sampler.
+ *   threads            host threads (0 = all hardware threads).
+ * Results do not depend on the thread count.
  * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, METHOD).
  */
 int vndf_cpu_sample(int64_t n,
                     const float *wi_x, const float *wi_y, const float *wi_z,
                     const float *alpha_x, const float *alpha_y,
-                    const float *u1, const float *u2, int method,
+                    const float *u1, const float *u2, int method, int precise,
                     float *wm_x, float *wm_y, float *wm_z, float *pdf, int threads);
 
 /* Size of the fixed device scratch array behind vndf_albedo_batched_noalloc:

@@ -58,7 +58,8 @@ SIGNATURES = {
     "vndf_fit_step": (ctypes.c_int, [_I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _F, _F, _F, _F,
                                      _F, _F, _U64, _U64, _U32, _P, _P, _SZ, _P]),
     "vndf_microbench": (ctypes.c_int, [_I64, _I32, ctypes.c_int, ctypes.c_int, _U64, _P, _P]),
-    "vndf_cpu_sample": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int, _P, _P, _P, _P, ctypes.c_int]),
+    "vndf_cpu_sample": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
+                                       ctypes.c_int]),
     "vndf_albedo_batched_noalloc": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, _P, _I32, _F, _U64, _U64, _U32, _P,
                                                    _P, _P]),
 }
@@ -403,7 +404,7 @@ def vndf_microbench(lanes, samples_per_lane=64, method="cap", seed=1, sums=None,
 
 
 def vndf_cpu_sample(wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, method="cap", with_pdf=True, threads=0,
-                    out=None):
+                    out=None, precise=False):
     """Host-CPU sampler on numpy float32 arrays; see vndf_cpu_sample in include/vndf.h.
 
     ``out`` optionally gives preallocated contiguous float32 outputs (wm_x, wm_y, wm_z, pdf).
@@ -422,6 +423,7 @@ def vndf_cpu_sample(wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, method="cap", wi
                 raise ValueError("vndf_cpu_sample: outputs must be contiguous float32 arrays of the input size")
     p = lambda a: None if a is None else a.ctypes.data  # noqa: E731
     st = load().vndf_cpu_sample(n, *(p(a) for a in arrs), p(ay), p(us[0]), p(us[1]), _method(method),
-                                p(out[0]), p(out[1]), p(out[2]), p(out[3]) if with_pdf else None, int(threads))
+                                int(bool(precise)), p(out[0]), p(out[1]), p(out[2]), p(out[3]) if with_pdf else None,
+                                int(threads))
     _check("vndf_cpu_sample", st)
     return out[0], out[1], out[2], (out[3] if with_pdf else None)

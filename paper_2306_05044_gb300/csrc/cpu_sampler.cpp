@@ -51,9 +51,13 @@ __attribute__((always_inline)) inline void sincospi_taylor_host(float x, float& 
   c = ((k + 1) & 2) ? -b : b;
 }
 
-template <int METHOD>
+// Condition-number threshold of the cap sampler's half vector above which a sample is
+// recomputed in double precision (the GPU kernels use the same test and threshold).
+constexpr float kRescueKappa = 24.f;
+
+template <int METHOD, bool PRECISE = false>
 __attribute__((always_inline)) inline void sample_host(float wx, float wy, float wz, float ax, float ay, float u1, float u2, float& mx, float& my,
-                        float& mz, float& pdf) {
+                        float& mz, float& pdf, bool& bad) {
   constexpr bool kExt = METHOD == VNDF_METHOD_SPHERICAL_CAP_EXTENDED;
   constexpr bool kCap = METHOD != VNDF_METHOD_POLAR_DISK;
   // the upper domain needs wi.z > 0; the extended one 1 + z_i' >= 2^-40, tested once a is formed
@@ -127,6 +131,41 @@ __attribute__((always_inline)) inline void sample_host(float wx, float wy, float
     p = 2.f * hi * vv * nv / (kPiF * ax * ay * a);
   }
   pdf = ok ? p : 0.f;
+  bad = false;
+  if constexpr (PRECISE && kCap) {
+    // |c.x| + |i.x| etc. bound the rounding of h; compare it with |v| and |h|
+    const float sx = std::fabs(hx - ix) + std::fabs(ix), sy = std::fabs(hy - iy) + std::fabs(iy);
+    const float k2 = std::fma(ax * sx, ax * sx, std::fma(ay * sy, ay * sy, hz * hz));
+    const float kh2 = std::fma(sx, sx, std::fma(sy, sy, hz * hz));
+    const float hh2 = std::fma(hx, hx, std::fma(hy, hy, hz * hz));
+    constexpr float k = kRescueKappa * kRescueKappa;
+    bad = ok & ((k2 > k * vv) | (kh2 > k * hh2));
+  }
+}
+
+// One cap sample in double precision (Sec. 2 steps (1)-(3), Sec. 3.3, the fused density
+// of Eq. 1), for the samples sample_host flags; inputs are in the domain.
+template <bool EXT>
+void sample_host_double(float wx, float wy, float wz, float ax, float ay, float u1, float u2, float& mx, float& my,
+                        float& mz, float& pdf) {
+  constexpr double kPiD = 3.14159265358979323846;
+  const double axd = ax, ayd = ay, u1d = u1, u2d = u2;
+  const double sx = axd * wx, sy = ayd * wy, sz = wz;
+  const double l = std::sqrt(sx * sx + sy * sy + sz * sz);
+  const double ix = sx / l, iy = sy / l, iz = sz / l;
+  const double rho2 = ix * ix + iy * iy;
+  double a = 1.0 + iz;
+  if (EXT && iz < 0.0) a = rho2 / (1.0 - iz);
+  const double st = std::sqrt(u2d * (2.0 * a * (1.0 - u2d) + u2d * rho2));
+  const double phi = 2.0 * kPiD * u1d;
+  const double hx = st * std::cos(phi) + ix, hy = st * std::sin(phi) + iy, hz = (1.0 - u2d) * a;
+  const double vx = axd * hx, vy = ayd * hy, vz = hz;
+  const double vv = vx * vx + vy * vy + vz * vz, nv = std::sqrt(vv);
+  mx = static_cast<float>(vx / nv);
+  my = static_cast<float>(vy / nv);
+  mz = static_cast<float>(vz / nv);
+  const double hh = hx * hx + hy * hy + hz * hz;
+  pdf = static_cast<float>((vv / hh) * nv / (kPiD * axd * ayd * a));
 }
 
 struct HostArgs {
@@ -134,17 +173,46 @@ struct HostArgs {
   float *mx, *my, *mz, *pdf;
 };
 
-template <int METHOD, bool PDF>
+template <int METHOD, bool PDF, bool PRECISE>
 void run_range(const HostArgs& h, int64_t i0, int64_t i1) {
   const float* ay = h.ay ? h.ay : h.ax;
+  constexpr int64_t kBlock = 2048;  // samples per pass: the vector loop, then the flagged ones
+  unsigned char flag[kBlock];
+  for (int64_t b0 = i0; b0 < i1; b0 += kBlock) {
+    const int64_t b1 = b0 + kBlock < i1 ? b0 + kBlock : i1;
 #pragma omp simd
-  for (int64_t i = i0; i < i1; ++i) {
-    float mx, my, mz, p;
-    sample_host<METHOD>(h.wx[i], h.wy[i], h.wz[i], h.ax[i], ay[i], h.u1[i], h.u2[i], mx, my, mz, p);
-    h.mx[i] = mx;
-    h.my[i] = my;
-    h.mz[i] = mz;
-    if constexpr (PDF) h.pdf[i] = p;
+    for (int64_t i = b0; i < b1; ++i) {
+      float mx, my, mz, p;
+      bool bad;
+      sample_host<METHOD, PRECISE>(h.wx[i], h.wy[i], h.wz[i], h.ax[i], ay[i], h.u1[i], h.u2[i], mx, my, mz, p,
+                                   bad);
+      h.mx[i] = mx;
+      h.my[i] = my;
+      h.mz[i] = mz;
+      if constexpr (PDF) h.pdf[i] = p;
+      if constexpr (PRECISE) flag[i - b0] = bad;
+    }
+    if constexpr (PRECISE) {
+      for (int64_t i = b0; i < b1; ++i) {
+        if (!flag[i - b0]) continue;
+        float mx, my, mz, p;
+        sample_host_double<METHOD == VNDF_METHOD_SPHERICAL_CAP_EXTENDED>(h.wx[i], h.wy[i], h.wz[i], h.ax[i], ay[i],
+                                                                        h.u1[i], h.u2[i], mx, my, mz, p);
+        h.mx[i] = mx;
+        h.my[i] = my;
+        h.mz[i] = mz;
+        if constexpr (PDF) h.pdf[i] = p;
+      }
+    }
+  }
+}
+
+template <int METHOD>
+void run_method(const HostArgs& h, bool pdf, bool precise, int64_t i0, int64_t i1) {
+  if (precise) {
+    pdf ? run_range<METHOD, true, true>(h, i0, i1) : run_range<METHOD, false, true>(h, i0, i1);
+  } else {
+    pdf ? run_range<METHOD, true, false>(h, i0, i1) : run_range<METHOD, false, false>(h, i0, i1);
   }
 }
 
@@ -152,7 +220,8 @@ void run_range(const HostArgs& h, int64_t i0, int64_t i1) {
 
 extern "C" int vndf_cpu_sample(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z,
                                const float* alpha_x, const float* alpha_y, const float* u1, const float* u2,
-                               int method, float* wm_x, float* wm_y, float* wm_z, float* pdf, int threads) {
+                               int method, int precise, float* wm_x, float* wm_y, float* wm_z, float* pdf,
+                               int threads) {
   if (n < 0 || n >= (int64_t(1) << 62)) return VNDF_ERR_SIZE;
   if (method != VNDF_METHOD_SPHERICAL_CAP && method != VNDF_METHOD_POLAR_DISK &&
       method != VNDF_METHOD_SPHERICAL_CAP_EXTENDED)
@@ -160,14 +229,14 @@ extern "C" int vndf_cpu_sample(int64_t n, const float* wi_x, const float* wi_y, 
   if (n == 0) return VNDF_OK;
   if (!wi_x || !wi_y || !wi_z || !alpha_x || !u1 || !u2 || !wm_x || !wm_y || !wm_z) return VNDF_ERR_NULL;
   const HostArgs h{wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, wm_x, wm_y, wm_z, pdf};
+  const bool want_pdf = pdf != nullptr, strict = precise != 0;
   auto body = [&](int64_t i0, int64_t i1) {
     if (method == VNDF_METHOD_SPHERICAL_CAP)
-      pdf ? run_range<VNDF_METHOD_SPHERICAL_CAP, true>(h, i0, i1) : run_range<VNDF_METHOD_SPHERICAL_CAP, false>(h, i0, i1);
+      run_method<VNDF_METHOD_SPHERICAL_CAP>(h, want_pdf, strict, i0, i1);
     else if (method == VNDF_METHOD_SPHERICAL_CAP_EXTENDED)
-      pdf ? run_range<VNDF_METHOD_SPHERICAL_CAP_EXTENDED, true>(h, i0, i1)
-          : run_range<VNDF_METHOD_SPHERICAL_CAP_EXTENDED, false>(h, i0, i1);
+      run_method<VNDF_METHOD_SPHERICAL_CAP_EXTENDED>(h, want_pdf, strict, i0, i1);
     else
-      pdf ? run_range<VNDF_METHOD_POLAR_DISK, true>(h, i0, i1) : run_range<VNDF_METHOD_POLAR_DISK, false>(h, i0, i1);
+      run_method<VNDF_METHOD_POLAR_DISK>(h, want_pdf, false, i0, i1);  // the prior sampler has no such path
   };
   int t = threads > 0 ? threads : static_cast<int>(std::thread::hardware_concurrency());
   if (t < 1) t = 1;

@@ -119,3 +119,44 @@ def test_cpu_sampler_on_stored_samples(v, kind):
         rel = abs(float(pdf[k]) / r["pdf"] - 1.0)
         assert rel <= max(parity.PDF_TOL, parity.K_ULP * float(3 * kap[0] + 2 * kap_h[0]) * parity.EPS32), \
             (r["note"], rel)
+
+
+@pytest.mark.parametrize("kind", ["cap", "cap_extended"])
+def test_cpu_precise_meets_the_flat_bounds(v, kind):
+    """With precise=1 the host sampler recomputes ill-conditioned samples in double precision and meets
+    4e-6 rad / 1e-5 relative on every sample inside the contract, as vndf_sample does; the other
+    samples are those of the plain path, bit for bit."""
+    n = (1 << 17) + 3
+    if kind == "cap":
+        d = _inputs(n, seed=16)
+    else:
+        d = {k: t.numpy() for k, t in workloads.sphere_stream(n=n, seed=17).items()}
+    u1, u2 = philox.sample_uniforms(6, 0, 0, n)
+    args = (d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], u1, u2)
+    strict = v.vndf_cpu_sample(*args, method=kind, precise=True)
+    plain = v.vndf_cpu_sample(*args, method=kind)
+    wi = np.stack([d["wi_x"], d["wi_y"], d["wi_z"]])
+    st = parity.compare_cap(np.stack(strict[:3]), strict[3], u1, u2, wi, d["alpha_x"], d["alpha_y"], strict=True,
+                            extended=kind == "cap_extended")
+    print("cpu precise", kind, st)
+    changed = np.zeros(n, bool)
+    for a, b in zip(strict, plain):
+        changed |= a != b
+    assert 0 < changed.mean() < 1e-2  # only the flagged samples differ
+
+
+def test_cpu_precise_on_stored_samples(v):
+    """The stored 50-digit rows (tests/golden) inside the contract, at the flat bounds."""
+    import oracle_checks as oc
+    for kind in ("cap", "cap_extended"):
+        rows = [r for r in oc.golden_rows() if r["kind"] == kind and not np.isnan(r["one_plus_zi"])
+                and min(r["alpha_x"], r["alpha_y"]) >= 1e-3
+                and (kind == "cap_extended" or r["wi"][2] / np.linalg.norm(r["wi"]) >= 1e-4)]
+        wi = np.stack([r["wi"] for r in rows], axis=1).astype(np.float32)
+        col = {k: np.array([r[k] for r in rows], np.float32) for k in ("alpha_x", "alpha_y", "u1", "u2")}
+        wx, wy, wz, pdf = v.vndf_cpu_sample(wi[0], wi[1], wi[2], col["alpha_x"], col["alpha_y"], col["u1"],
+                                            col["u2"], method=kind, precise=True)
+        for k, r in enumerate(rows):
+            g = np.array([wx[k], wy[k], wz[k]], np.float64).reshape(3, 1)
+            assert float(parity.angle_between(g, r["wm"].reshape(3, 1))[0]) <= parity.ANGLE_TOL, r["note"]
+            assert abs(float(pdf[k]) / r["pdf"] - 1.0) <= parity.PDF_TOL, r["note"]
