@@ -62,7 +62,9 @@ __device__ __forceinline__ float3 block_sum3(float3 v, float (*sm)[kFitBlock / 3
   return r;  // identical in every warp (same inputs, same tree)
 }
 
-__global__ void __launch_bounds__(kFitBlock) fit_kernel(FitArgs a) {
+// 4 CTAs per SM (at most 64 registers): keeping the uniforms between the passes would otherwise
+// take the kernel to 74 registers and 3 CTAs.
+__global__ void __launch_bounds__(kFitBlock, 4) fit_kernel(FitArgs a) {
   __shared__ float sm[3][kFitBlock / 32];
   const int64_t step = *a.step + 1;  // 1-based step performed by this launch
   Rng r = a.rng;
@@ -74,12 +76,21 @@ __global__ void __launch_bounds__(kFitBlock) fit_kernel(FitArgs a) {
     const float ax = a.ax[t], ay = a.ay[t];
     Rng rt = r;
     rt.stream = a.rng.stream + uint32_t(t);
+    // When every thread has at most one group of 4 samples (S <= 4 x block), the uniforms of the
+    // forward pass are kept in registers for the adjoint pass instead of being drawn again.
+    const bool one_group = a.ns <= 4 * kFitBlock;
+    float ku1[4] = {0.f, 0.f, 0.f, 0.f}, ku2[4] = {0.f, 0.f, 0.f, 0.f};
     // ---- forward: lobe mean
     float3 sum = make_float3(0.f, 0.f, 0.f);
     for (int32_t j0 = 4 * threadIdx.x; j0 < a.ns; j0 += 4 * kFitBlock) {
       float u1[4], u2[4];
       uniforms2(rt, uint64_t(j0), u1[0], u2[0], u1[1], u2[1]);
       uniforms2(rt, uint64_t(j0 + 2), u1[2], u2[2], u1[3], u2[3]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        ku1[k] = u1[k];
+        ku2[k] = u2[k];
+      }
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         float mx, my, mz, p;
@@ -98,8 +109,16 @@ __global__ void __launch_bounds__(kFitBlock) fit_kernel(FitArgs a) {
     float3 ga = make_float3(0.f, 0.f, 0.f);
     for (int32_t j0 = 4 * threadIdx.x; j0 < a.ns; j0 += 4 * kFitBlock) {
       float u1[4], u2[4];
-      uniforms2(rt, uint64_t(j0), u1[0], u2[0], u1[1], u2[1]);
-      uniforms2(rt, uint64_t(j0 + 2), u1[2], u2[2], u1[3], u2[3]);
+      if (one_group) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          u1[k] = ku1[k];
+          u2[k] = ku2[k];
+        }
+      } else {
+        uniforms2(rt, uint64_t(j0), u1[0], u2[0], u1[1], u2[1]);
+        uniforms2(rt, uint64_t(j0 + 2), u1[2], u2[2], u1[3], u2[3]);
+      }
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         float mx, my, mz, p;
