@@ -384,13 +384,21 @@ size_t vndf_fit_workspace_bytes(int32_t n_texels);
  * t, S = samples_per_texel normals are drawn with the spherical-cap sampler
  * (Sec. 2 steps (1)-(3), Sec. 3.3) from Philox stream stream_id + t at global
  * indices counter_base + (step - 1) S + j, so every step draws fresh samples;
- *   m_t  = (1/S) sum_j wm_tj,      loss = (1 / 3T) sum_t |m_t - target_t|^2,
+ *   m_t  = (1/S) sum_j wm_tj,      loss = (1 / 3N) sum_t |m_t - target_t|^2
+ * (N = n_texels_total, else T),
  * the gradient with respect to (alpha_x, alpha_y) goes through the adjoint of
  * vndf_sample_backward, and Adam (Kingma & Ba 2015, with bias correction at
  * the 1-based step) updates alpha, which is then clamped to
  * [alpha_min, alpha_max].  The paper defines the sampler only; this loop is
  * the library's use of it.
  *   n_texels, samples_per_texel   T >= 0 and 1 <= S <= 2^20.
+ *   n_texels_total      size of the whole map when these T texels are one
+ *                       part of it (0 = T).  The loss and its gradient are
+ *                       normalised by it, so splitting a map into calls (one
+ *                       per GPU, each with stream_id = its first texel) gives
+ *                       the same updates, bit for bit, as one call over the
+ *                       whole map, and the calls' losses add up to its loss.
+ *                       Must be 0 or >= T.
  *   wi_*, target_*      per-texel incident direction and target mean (read).
  *   alpha_x, alpha_y    per-texel roughness (read and updated in place).
  *   adam_m_*, adam_v_*  Adam moments (read and updated; zero before step 1).
@@ -409,7 +417,7 @@ size_t vndf_fit_workspace_bytes(int32_t n_texels);
  * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, ALIGN, ARG,
  * WORKSPACE, CUDA).
  */
-int vndf_fit_step(int32_t n_texels, int32_t samples_per_texel,
+int vndf_fit_step(int32_t n_texels, int32_t n_texels_total, int32_t samples_per_texel,
                   const float *wi_x, const float *wi_y, const float *wi_z,
                   const float *target_x, const float *target_y, const float *target_z,
                   float *alpha_x, float *alpha_y,

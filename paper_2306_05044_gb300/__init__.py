@@ -55,8 +55,8 @@ SIGNATURES = {
     "vndf_albedo_autotune": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, _P, _I32, _F, _U64, _U64, _U32, _P, _P, _SZ,
                                             _P, _P, _P]),
     "vndf_fit_workspace_bytes": (_SZ, [_I32]),
-    "vndf_fit_step": (ctypes.c_int, [_I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _F, _F, _F, _F,
-                                     _F, _F, _U64, _U64, _U32, _P, _P, _SZ, _P]),
+    "vndf_fit_step": (ctypes.c_int, [_I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _F, _F,
+                                     _F, _F, _F, _F, _U64, _U64, _U32, _P, _P, _SZ, _P]),
     "vndf_microbench": (ctypes.c_int, [_I64, _I32, ctypes.c_int, ctypes.c_int, _U64, _P, _P]),
     "vndf_cpu_sample": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
                                        ctypes.c_int]),
@@ -360,7 +360,7 @@ def vndf_fit_workspace_bytes(n_texels):
 
 def vndf_fit_step(state, wi_x, wi_y, wi_z, target_x, target_y, target_z, samples_per_texel=1024, lr=1e-2,
                   beta1=0.9, beta2=0.999, eps=1e-8, alpha_min=1e-3, alpha_max=1.0, seed=5, counter_base=0,
-                  stream_id=0, loss=None, workspace=None, stream=None):
+                  stream_id=0, loss=None, workspace=None, stream=None, n_texels_total=0):
     """One fitting step in place; see vndf_fit_step in include/vndf.h.
 
     state: dict of device tensors alpha_x, alpha_y, m_x, m_y, v_x, v_y (float32, one per texel) and
@@ -370,7 +370,7 @@ def vndf_fit_step(state, wi_x, wi_y, wi_z, target_x, target_y, target_z, samples
     if workspace is None:
         workspace = torch.empty(max(vndf_fit_workspace_bytes(nt), 4), dtype=torch.uint8, device=wi_x.device)
     st = load().vndf_fit_step(
-        nt, int(samples_per_texel), _ptr(wi_x, "wi_x"), _ptr(wi_y, "wi_y"), _ptr(wi_z, "wi_z"),
+        nt, int(n_texels_total), int(samples_per_texel), _ptr(wi_x, "wi_x"), _ptr(wi_y, "wi_y"), _ptr(wi_z, "wi_z"),
         _ptr(target_x, "target_x"), _ptr(target_y, "target_y"), _ptr(target_z, "target_z"),
         _ptr(state["alpha_x"], "alpha_x"), _ptr(state["alpha_y"], "alpha_y"), _ptr(state["m_x"], "m_x"),
         _ptr(state["m_y"], "m_y"), _ptr(state["v_x"], "v_x"), _ptr(state["v_y"], "v_y"),

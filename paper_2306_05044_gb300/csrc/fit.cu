@@ -6,8 +6,8 @@
 // (1)-(3), Sec. 3.3) from Philox stream stream_id + t at global indices
 // counter_base + (step - 1) S + j:
 //   m_t   = (1/S) sum_j wm_tj                                  (lobe mean)
-//   L     = (1 / 3T) sum_t |m_t - target_t|^2                   (MSE)
-//   g_t   = dL/d(ax_t, ay_t) = (2 / 3T S) sum_j (m_t - target_t) . d wm_tj / d alpha
+//   L     = (1 / 3N) sum_t |m_t - target_t|^2                   (MSE; N texels in the whole map)
+//   g_t   = dL/d(ax_t, ay_t) = (2 / 3N S) sum_j (m_t - target_t) . d wm_tj / d alpha
 //   Adam (Kingma & Ba 2015) with bias correction at the 1-based step, then
 //   alpha is projected onto [alpha_min, alpha_max].
 // The step counter lives in device memory: the finishing kernel adds one, so
@@ -27,6 +27,7 @@ constexpr int kFitBlock = 256;
 
 struct FitArgs {
   int32_t nt, ns;
+  int32_t n_total;  // texels of the whole map (normalisation of the loss and its gradient)
   const float *wx, *wy, *wz, *tx, *ty, *tz;
   float *ax, *ay, *mx, *my, *vx, *vy;
   int64_t* step;
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(kFitBlock, 4) fit_kernel(FitArgs a) {
   Rng r = a.rng;
   r.base = a.rng.base + uint64_t(step - 1) * uint64_t(a.ns);
   const float inv_s = 1.f / float(a.ns);
-  const float gscale = 2.f / (3.f * float(a.nt));
+  const float gscale = 2.f / (3.f * float(a.n_total));
   for (int32_t t = blockIdx.x; t < a.nt; t += gridDim.x) {
     const float wx = a.wx[t], wy = a.wy[t], wz = a.wz[t];
     const float ax = a.ax[t], ay = a.ay[t];
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(kFitBlock, 4) fit_kernel(FitArgs a) {
   }
 }
 
-// Loss = sum of texel losses (texel order, fixed tree) / 3T; then advance the step counter.
+// Loss = sum of texel losses (texel order, fixed tree) / 3N; then advance the step counter.
 __global__ void __launch_bounds__(1024) fit_finish_kernel(FitArgs a) {
   __shared__ float sm[32];
   float v = 0.f;
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(1024) fit_finish_kernel(FitArgs a) {
   if (threadIdx.x < 32) {
     float s = warp_sum_fit(sm[threadIdx.x]);
     if (threadIdx.x == 0) {
-      if (a.loss) *a.loss = s / (3.f * float(a.nt));
+      if (a.loss) *a.loss = s / (3.f * float(a.n_total));
       *a.step += 1;
     }
   }
@@ -178,7 +179,8 @@ extern "C" size_t vndf_fit_workspace_bytes(int32_t n_texels) {
   return n_texels > 0 ? size_t(n_texels) * sizeof(float) : 0;
 }
 
-extern "C" int vndf_fit_step(int32_t n_texels, int32_t samples_per_texel, const float* wi_x, const float* wi_y,
+extern "C" int vndf_fit_step(int32_t n_texels, int32_t n_texels_total, int32_t samples_per_texel,
+                             const float* wi_x, const float* wi_y,
                              const float* wi_z, const float* target_x, const float* target_y, const float* target_z,
                              float* alpha_x, float* alpha_y, float* adam_m_x, float* adam_m_y, float* adam_v_x,
                              float* adam_v_y, int64_t* step, float lr, float beta1, float beta2, float eps,
@@ -186,6 +188,7 @@ extern "C" int vndf_fit_step(int32_t n_texels, int32_t samples_per_texel, const 
                              uint32_t stream_id, float* loss, void* workspace, size_t workspace_bytes,
                              void* cuda_stream) {
   if (n_texels < 0 || samples_per_texel < 1 || samples_per_texel > (1 << 20)) return VNDF_ERR_SIZE;
+  if (n_texels_total != 0 && n_texels_total < n_texels) return VNDF_ERR_SIZE;
   if (n_texels == 0) return VNDF_OK;
   if (!wi_x || !wi_y || !wi_z || !target_x || !target_y || !target_z || !alpha_x || !alpha_y || !adam_m_x ||
       !adam_m_y || !adam_v_x || !adam_v_y || !step)
@@ -198,7 +201,8 @@ extern "C" int vndf_fit_step(int32_t n_texels, int32_t samples_per_texel, const 
                     adam_v_x, adam_v_y, loss, workspace) ||
       !aligned(step, 8))
     return VNDF_ERR_ALIGN;
-  FitArgs a{n_texels, samples_per_texel, wi_x,     wi_y,     wi_z,     target_x,  target_y, target_z,
+  FitArgs a{n_texels, samples_per_texel, n_texels_total ? n_texels_total : n_texels,
+            wi_x,     wi_y,     wi_z,     target_x,  target_y, target_z,
             alpha_x,  alpha_y,           adam_m_x, adam_m_y, adam_v_x, adam_v_y,  step,     lr,
             beta1,    beta2,             eps,      alpha_min, alpha_max, make_rng(seed, counter_base, stream_id),
             static_cast<float*>(workspace), loss};

@@ -1,7 +1,7 @@
 // Status strings and the ABI version of libvndf.
 #include "vndf.h"
 
-extern "C" int vndf_abi_version(void) { return 2; }
+extern "C" int vndf_abi_version(void) { return 3; }
 
 extern "C" const char* vndf_status_string(int status) {
   switch (status) {

@@ -54,7 +54,7 @@ def test_status_strings(lib):
     for code in range(-7, 0):
         assert v.status_string(code) not in ("ok", "unknown status")
     assert v.status_string(-99) == "unknown status"
-    assert v.vndf_abi_version() == 2
+    assert v.vndf_abi_version() == 3
 
 
 FAKE = 0x10000  # 16-byte aligned host value; never dereferenced on the error paths

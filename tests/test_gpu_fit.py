@@ -115,3 +115,27 @@ def test_full_map_step_sampled_texels(v):
             np.testing.assert_allclose(_np(st["alpha_x"][sub]), new["ax"], rtol=1e-5, atol=1e-7)
             np.testing.assert_allclose(_np(st["alpha_y"][sub]), new["ay"], rtol=1e-5, atol=1e-7)
     assert np.isfinite(loss.item())
+
+
+def test_fit_split_map_equals_one_call(v):
+    """One map fitted as two parts (texels [0, T0) and [T0, T), each call with stream_id = its first
+    texel and n_texels_total = T) gives the same alpha and moments, bit for bit, as one call over the
+    map, and the parts' losses add up to its loss; the parts may run on different GPUs."""
+    d, wi, tg = _inputs(16)  # 256 texels
+    t_all, t0 = 256, 100
+    full = v.fit_state(d["alpha_x"], d["alpha_y"])
+    lf = torch.empty(1, device=DEV)
+    parts = [v.fit_state(d["alpha_x"][:t0].contiguous(), d["alpha_y"][:t0].contiguous()),
+             v.fit_state(d["alpha_x"][t0:].contiguous(), d["alpha_y"][t0:].contiguous())]
+    lp = [torch.empty(1, device=DEV), torch.empty(1, device=DEV)]
+    sl = [slice(0, t0), slice(t0, t_all)]
+    for step in range(3):
+        v.vndf_fit_step(full, *wi, *tg, seed=7, loss=lf)
+        for k in range(2):
+            v.vndf_fit_step(parts[k], *(x[sl[k]].contiguous() for x in wi), *(x[sl[k]].contiguous() for x in tg),
+                            seed=7, stream_id=sl[k].start, loss=lp[k], n_texels_total=t_all)
+        torch.cuda.synchronize()
+        assert abs((lp[0].item() + lp[1].item()) / lf.item() - 1.0) < 1e-6
+    for key in ("alpha_x", "alpha_y", "m_x", "m_y", "v_x", "v_y"):
+        assert torch.equal(torch.cat([parts[0][key], parts[1][key]]), full[key]), key
+    assert int(parts[0]["step"].item()) == int(parts[1]["step"].item()) == 3
