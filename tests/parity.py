@@ -29,7 +29,7 @@ import numpy as np
 from oracle import vndf
 
 EPS32 = 2.0 ** -24
-A_MP = 1e-9  # below this 1 + z_i' the 50-digit reference replaces the FP64 oracle
+A_MP = 1e-9  # below this 1 + z_i' (or u2 (1 + z_i')) the 50-digit reference replaces the FP64 oracle
 K_ULP = 8.0
 ANGLE_TOL = 4e-6
 PDF_TOL = 1e-5
@@ -60,11 +60,21 @@ def one_plus_zi(wi, ax, ay):
         return np.where(wz >= 0, 1.0 + wz / el, (sx * sx + sy * sy) / (el * (el - wz)))
 
 
+def fp64_weak(u2, wi, ax, ay):
+    """Extended-domain samples on which the FP64 oracle itself loses digits: 1 + z_i' < A_MP (its
+    cap bottom -z_i' is subtracted), or u2 (1 + z_i') < A_MP (then 1 - z = u2 (1 + z_i') lies near
+    the resolution of z next to 1, and sin(theta) = sqrt(1 - z^2) as the paper writes it has a
+    relative error of about 2^-53 / (u2 (1 + z_i')))."""
+    with np.errstate(invalid="ignore"):
+        a = one_plus_zi(wi, ax, ay)
+        return ~(a >= A_MP) | ~(np.asarray(u2, np.float64) * a >= A_MP)
+
+
 def compare_cap(wm_gpu, pdf_gpu, u1, u2, wi, ax, ay, strict=True, extended=False):
     """Check GPU cap samples against the oracle; returns a stats dict (asserts the bounds).
 
     With extended=True the inputs may lie below the horizon (the extended domain).  There
-    the FP64 oracle itself loses digits when 1 + z_i' < A_MP: such samples are excluded
+    the FP64 oracle itself loses digits (``fp64_weak``): such samples are excluded
     here and checked against the 50-digit reference by ``compare_cap_mp``."""
     wi = np.asarray(wi, np.float64)
     ax = np.asarray(ax, np.float64)
@@ -77,7 +87,7 @@ def compare_cap(wm_gpu, pdf_gpu, u1, u2, wi, ax, ay, strict=True, extended=False
     stats = {"n": int(u1.size), "out_of_domain": int((~ok).sum())}
     if extended:
         with np.errstate(invalid="ignore"):
-            tiny = ok & ~(one_plus_zi(wi, ax, ay) >= A_MP)
+            tiny = ok & fp64_weak(u2, wi, ax, ay)
         stats["left_to_mp_reference"] = int(tiny.sum())
         keep = ~tiny
         wm_ref, pdf_ref, wm_gpu = wm_ref[:, keep], pdf_ref[keep], wm_gpu[:, keep]
@@ -135,7 +145,7 @@ def compare_cap(wm_gpu, pdf_gpu, u1, u2, wi, ax, ay, strict=True, extended=False
 
 
 def compare_cap_mp(wm_gpu, pdf_gpu, u1, u2, wi, ax, ay, limit=2000):
-    """Extended-domain samples with 1 + z_i' < A_MP (the FP64 oracle's weak spot) against the
+    """Extended-domain samples on which the FP64 oracle is weak (``fp64_weak``) against the
     50-digit reference (oracle.vndf_mp), at the flat limits.  Checks at most ``limit`` of them."""
     try:
         from oracle import vndf_mp as mp
@@ -146,7 +156,7 @@ def compare_cap_mp(wm_gpu, pdf_gpu, u1, u2, wi, ax, ay, limit=2000):
     ay = np.asarray(ay, np.float64)
     ok = vndf.in_domain(wi, ax, ay, True)
     with np.errstate(invalid="ignore"):
-        idx = np.flatnonzero(ok & ~(one_plus_zi(wi, ax, ay) >= A_MP))[:limit]
+        idx = np.flatnonzero(ok & fp64_weak(u2, wi, ax, ay))[:limit]
     worst_a, worst_p = 0.0, 0.0
     for k in idx:
         m, p = mp.sample_with_pdf(u1[k], u2[k], wi[:, k], ax[k], ay[k])

@@ -160,3 +160,23 @@ def test_cpu_precise_on_stored_samples(v):
             g = np.array([wx[k], wy[k], wz[k]], np.float64).reshape(3, 1)
             assert float(parity.angle_between(g, r["wm"].reshape(3, 1))[0]) <= parity.ANGLE_TOL, r["note"]
             assert abs(float(pdf[k]) / r["pdf"] - 1.0) <= parity.PDF_TOL, r["note"]
+
+
+@pytest.mark.parametrize("kind", ["cap", "cap_extended"])
+def test_cpu_precise_on_wide_inputs(v, kind):
+    """Stress inputs (wi on the whole sphere with lengths 1e-3 to 1e3, roughness 1e-5 to 10, uniforms at
+    the ends of [0, 1)): every output finite, the flat bounds inside the contract, the condition-scaled
+    bound outside it, the exact fallback outside the domain; extended-domain samples on which FP64 is
+    weak are checked against the 50-digit reference."""
+    d = {k: t.numpy() for k, t in workloads.wide_stream(n=1 << 15, seed=18).items()}
+    u1, u2 = d["u1"].astype(np.float64), d["u2"].astype(np.float64)
+    out = v.vndf_cpu_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], d["u1"], d["u2"],
+                            method=kind, precise=True)
+    assert all(np.isfinite(t).all() for t in out)
+    wi = np.stack([d["wi_x"], d["wi_y"], d["wi_z"]])
+    ext = kind == "cap_extended"
+    st = parity.compare_cap(np.stack(out[:3]), out[3], u1, u2, wi, d["alpha_x"], d["alpha_y"], strict=True,
+                            extended=ext)
+    if ext:
+        st.update(parity.compare_cap_mp(np.stack(out[:3]), out[3], u1, u2, wi, d["alpha_x"], d["alpha_y"], limit=150))
+    print("cpu wide", kind, st)

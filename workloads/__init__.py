@@ -29,6 +29,11 @@ Workloads (sizes are the defaults):
                        the horizon), alpha_x, alpha_y ~ log-U[1e-3, 1].
 * ``hemisphere_stream`` 2^28 directions for the stand-alone hemisphere sampler:
                        uniform on the whole sphere, lengths ~ log-U[0.5, 2].
+* ``wide_stream``      stress inputs for the tests: wi uniform on the whole sphere
+                       with lengths ~ log-U[1e-3, 1e3], alpha_x, alpha_y ~
+                       log-U[1e-5, 10] independently, and explicit uniforms on the
+                       2^-24 grid of [0, 1) with 1 % of them set to the ends and
+                       quarter points (0, 2^-24, 1/4, 1/2, 3/4, 1 - 2^-24).
 """
 import math
 
@@ -137,3 +142,19 @@ def hemisphere_stream(n=1 << 28, seed=14, device="cpu"):
     r = _log_uniform(g, n, 0.5, 2.0, device)
     wx, wy, wz = _f32(wx * r, wy * r, wz * r)
     return {"wi_x": wx, "wi_y": wy, "wi_z": wz}
+
+
+def wide_stream(n=1 << 16, seed=15, device="cpu"):
+    g = _gen(seed, device)
+    wx, wy, wz = _directions(g, n, -1.0, 1.0, device)
+    r = _log_uniform(g, n, 1e-3, 1e3, device)
+    ax = _log_uniform(g, n, 1e-5, 10.0, device)
+    ay = _log_uniform(g, n, 1e-5, 10.0, device)
+    k = torch.floor(torch.rand(2, n, generator=g, dtype=torch.float64, device=device) * 2.0 ** 24)
+    u = k * 2.0 ** -24
+    special = torch.tensor([0.0, 2.0 ** -24, 0.25, 0.5, 0.75, 1.0 - 2.0 ** -24], dtype=torch.float64, device=device)
+    pick = torch.rand(2, n, generator=g, dtype=torch.float64, device=device) < 0.01
+    which = torch.randint(0, special.numel(), (2, n), generator=g, device=device)
+    u = torch.where(pick, special[which], u)
+    wx, wy, wz, ax, ay, u1, u2 = _f32(wx * r, wy * r, wz * r, ax, ay, u[0], u[1])
+    return {"wi_x": wx, "wi_y": wy, "wi_z": wz, "alpha_x": ax, "alpha_y": ay, "u1": u1, "u2": u2}
