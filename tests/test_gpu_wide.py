@@ -105,3 +105,38 @@ def test_reflection_on_wide_inputs(v, wide):
     assert ang.max() <= 2 * parity.ANGLE_TOL
     assert np.abs(pg[cont] / pr[cont] - 1.0).max() <= parity.PDF_TOL
     print(f"wide reflection: {int(cont.sum())} samples in the contract, wo max {ang.max():.2e} rad")
+
+
+@pytest.mark.parametrize("ext", [False, True])
+def test_adjoint_on_wide_inputs(v, wide, ext):
+    """The generic adjoint on the stress inputs: finite everywhere, zero outside the domain, and inside the
+    contract (and where FP64 is not weak) the complex-step products to p99.9 1e-3 of the largest component."""
+    from oracle import grad
+    d, h = wide
+    n = d["wi_x"].numel()
+    g = torch.Generator(device=DEV).manual_seed(3)
+    gw = [torch.randn(n, generator=g, device=DEV) for _ in range(3)]
+    out = v.vndf_sample(*(d[k] for k in KEYS), u1=d["u1"], u2=d["u2"], method="cap_extended" if ext else "cap")
+    gp = (1.0 / torch.clamp(out[3], min=1e-30)).contiguous()  # d log pdf
+    gr = v.vndf_sample_backward(*(d[k] for k in KEYS), u1=d["u1"], u2=d["u2"], g_wm_x=gw[0], g_wm_y=gw[1],
+                                g_wm_z=gw[2], g_pdf=gp, extended=ext)
+    got = np.stack(_np(*gr))
+    assert np.isfinite(got).all()
+    wi = np.stack([h["wi_x"], h["wi_y"], h["wi_z"]])
+    ax, ay = h["alpha_x"], h["alpha_y"]
+    ok = ovndf.in_domain(wi, ax, ay, ext)
+    assert np.all(got[:, ~ok] == 0.0)
+    cont = ok & (np.minimum(ax, ay) >= 1e-3)
+    if not ext:
+        cont &= wi[2] / np.sqrt(ovndf.dot(wi, wi)) >= 1e-4
+    else:
+        cont &= ~parity.fp64_weak(h["u2"], wi, ax, ay)
+    idx = np.flatnonzero(cont)[:20000]
+    gwn = np.stack(_np(*gw))[:, idx]
+    rwi, rax, ray = grad.vjp(h["u1"][idx], h["u2"][idx], wi[:, idx], ax[idx], ay[idx], gwn, _np(gp)[0][idx],
+                             extended=ext)
+    ref = np.concatenate([rwi, rax[None], ray[None]])
+    err = np.abs(got[:, idx] - ref).max(axis=0) / np.maximum(np.abs(ref).max(axis=0), 1e-30)
+    print(f"wide adjoint ext={ext}: {idx.size} samples, median {np.median(err):.1e} p99.9 {np.quantile(err, 0.999):.1e}"
+          f" max {err.max():.1e}")
+    assert np.quantile(err, 0.999) < 1e-3
