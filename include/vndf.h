@@ -321,10 +321,12 @@ size_t vndf_albedo_workspace_bytes(int32_t n_queries, int32_t max_samples_per_qu
  * Fresnel F0 + (1 - F0)(1 - wi.wm)^5; terms with wo below the surface are 0.
  *   n_queries          number of queries (>= 0); 0 is a no-op.
  *   wi_*, alpha_*      per-query direction (upper hemisphere, any length) and
- *                      roughness; alpha_y = NULL means isotropic.
+ *                      roughness; alpha_y = NULL means isotropic.  A query
+ *                      outside the sampler's domain (wi.z <= 0, alpha <= 0,
+ *                      non-finite) yields E_q = NaN.
  *   n_samples          per-query sample counts N_q (int32, device).  A count
  *                      outside [0, max_samples_per_query] yields E_q = NaN; a
- *                      count of 0 yields E_q = 0.
+ *                      count of 0 (in the domain) yields E_q = 0.
  *   max_samples_per_query  the bound the workspace was sized for (<= 2^30).
  *   f0                 Schlick reflectance at normal incidence.
  *   seed, counter_base, stream_id  Philox: query q draws from stream

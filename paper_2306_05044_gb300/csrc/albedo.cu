@@ -71,13 +71,20 @@ __global__ void __launch_bounds__(1024) albedo_prologue_kernel(AlbedoArgs a) {
   int32_t* offsets = a.ctl + 2;
   int32_t* done = a.ctl + 3 + a.nq;
   int32_t local = 0;
+  // a query outside the sampler's domain (wi.z <= 0, alpha <= 0, non-finite) or with a count outside
+  // [0, max] gets no work and E = NaN
+  auto usable = [&](int32_t q) {
+    const int32_t n = a.ns[q];
+    const float ax = a.ax[q], ay = a.ay ? a.ay[q] : ax;
+    return n >= 0 && n <= a.max_n && in_domain(a.wx[q], a.wy[q], a.wz[q], ax, ay);
+  };
   for (int32_t q = q0; q < q1; ++q) {
     const int32_t n = a.ns[q];
-    const bool valid = n >= 0 && n <= a.max_n;
+    const bool valid = usable(q);
     const int32_t groups = valid ? (n + kGroupSamples - 1) / kGroupSamples : 0;
     local += (groups + a.groups_per_item - 1) / a.groups_per_item;
     done[q] = 0;
-    if (!valid) a.E[q] = __int_as_float(0x7fc00000);  // NaN: count outside [0, max]
+    if (!valid) a.E[q] = __int_as_float(0x7fc00000);  // NaN
     else if (n == 0) a.E[q] = 0.f;
   }
   // exclusive scan of the per-thread totals (fixed order)
@@ -104,7 +111,7 @@ __global__ void __launch_bounds__(1024) albedo_prologue_kernel(AlbedoArgs a) {
   for (int32_t q = q0; q < q1; ++q) {
     offsets[q] = run;
     const int32_t n = a.ns[q];
-    const bool valid = n >= 0 && n <= a.max_n;
+    const bool valid = usable(q);
     const int32_t groups = valid ? (n + kGroupSamples - 1) / kGroupSamples : 0;
     run += (groups + a.groups_per_item - 1) / a.groups_per_item;
   }

@@ -124,3 +124,37 @@ def test_albedo_edge_counts(v):
     ref = _oracle(tn, ok, seed=7, base=3, sid=100)
     err = np.abs(E[ok] - ref)
     assert np.all(err <= 1e-5 * np.abs(ref) + 1e-7), (E[ok], ref)
+
+
+def test_albedo_on_wide_queries(v):
+    """Stress queries: roughness 1e-5 to 10 per axis (anisotropic), wi of any length on the upper
+    hemisphere down to grazing 1e-4, counts 0 to 3000 (ragged, many below one group), plus queries
+    outside the domain (wi.z <= 0, alpha = 0): E = NaN outside the domain, 0 for a count of 0, and
+    elsewhere finite, in [0, 1] and equal to the oracle's same-u estimate."""
+    g = torch.Generator().manual_seed(23)
+    q = 512
+    ct = torch.exp(torch.empty(q, dtype=torch.float64).uniform_(np.log(1e-4), 0.0, generator=g))
+    phi = torch.empty(q, dtype=torch.float64).uniform_(0.0, 2 * np.pi, generator=g)
+    r = torch.exp(torch.empty(q, dtype=torch.float64).uniform_(np.log(1e-2), np.log(1e2), generator=g))
+    st = torch.sqrt(1 - ct * ct)
+    wx, wy, wz = st * torch.cos(phi) * r, st * torch.sin(phi) * r, ct * r
+    ax = torch.exp(torch.empty(q, dtype=torch.float64).uniform_(np.log(1e-5), np.log(10.0), generator=g))
+    ay = torch.exp(torch.empty(q, dtype=torch.float64).uniform_(np.log(1e-5), np.log(10.0), generator=g))
+    ns = torch.randint(0, 3001, (q,), generator=g, dtype=torch.int32)
+    wz[:8] = -wz[:8]  # below the horizon: outside the domain
+    ax[8:12] = 0.0    # alpha = 0: outside the domain
+    ns[12:16] = 0
+    d = {k: t.to(torch.float32).to(DEV) for k, t in (("wi_x", wx), ("wi_y", wy), ("wi_z", wz), ("alpha_x", ax),
+                                                        ("alpha_y", ay))}
+    d["n_samples"] = ns.to(DEV)
+    E = v.vndf_albedo_batched(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], d["n_samples"],
+                              max_samples_per_query=3000)
+    e = E.cpu().numpy().astype(np.float64)
+    assert np.all(np.isnan(e[:12])) and np.all(e[12:16] == 0.0)
+    assert np.all(np.isfinite(e[12:])) and e[12:].min() >= 0.0 and e[12:].max() <= 1.0
+    idx = np.arange(16, q)
+    with np.errstate(all="ignore"):
+        ref = _oracle(d, idx)
+    err = np.abs(e[idx] - ref)
+    print(f"wide albedo: max abs err {err.max():.2e} over {idx.size} queries")
+    assert np.all(err <= 1e-5 * np.abs(ref) + 2e-7)
