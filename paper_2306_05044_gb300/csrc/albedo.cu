@@ -72,17 +72,15 @@ __global__ void __launch_bounds__(1024) albedo_prologue_kernel(AlbedoArgs a) {
   int32_t* done = a.ctl + 3 + a.nq;
   int32_t local = 0;
   // a query outside the sampler's domain (wi.z <= 0, alpha <= 0, non-finite) or with a count outside
-  // [0, max] gets no work and E = NaN
-  auto usable = [&](int32_t q) {
-    const int32_t n = a.ns[q];
-    const float ax = a.ax[q], ay = a.ay ? a.ay[q] : ax;
-    return n >= 0 && n <= a.max_n && in_domain(a.wx[q], a.wy[q], a.wz[q], ax, ay);
-  };
+  // [0, max] gets no work and E = NaN; its item count is parked in offsets[q] until the scan is known
   for (int32_t q = q0; q < q1; ++q) {
     const int32_t n = a.ns[q];
-    const bool valid = usable(q);
+    const float ax = a.ax[q], ay = a.ay ? a.ay[q] : ax;
+    const bool valid = n >= 0 && n <= a.max_n && in_domain(a.wx[q], a.wy[q], a.wz[q], ax, ay);
     const int32_t groups = valid ? (n + kGroupSamples - 1) / kGroupSamples : 0;
-    local += (groups + a.groups_per_item - 1) / a.groups_per_item;
+    const int32_t items = (groups + a.groups_per_item - 1) / a.groups_per_item;
+    offsets[q] = items;
+    local += items;
     done[q] = 0;
     if (!valid) a.E[q] = __int_as_float(0x7fc00000);  // NaN
     else if (n == 0) a.E[q] = 0.f;
@@ -109,11 +107,9 @@ __global__ void __launch_bounds__(1024) albedo_prologue_kernel(AlbedoArgs a) {
   __syncthreads();
   int32_t run = (w > 0 ? warp_tot[w - 1] : 0) + incl - local;
   for (int32_t q = q0; q < q1; ++q) {
+    const int32_t items = offsets[q];  // written above by this thread
     offsets[q] = run;
-    const int32_t n = a.ns[q];
-    const bool valid = usable(q);
-    const int32_t groups = valid ? (n + kGroupSamples - 1) / kGroupSamples : 0;
-    run += (groups + a.groups_per_item - 1) / a.groups_per_item;
+    run += items;
   }
   if (t == 1023) {
     offsets[a.nq] = run;
