@@ -364,7 +364,9 @@ def vndf_fit_step(state, wi_x, wi_y, wi_z, target_x, target_y, target_z, samples
     """One fitting step in place; see vndf_fit_step in include/vndf.h.
 
     state: dict of device tensors alpha_x, alpha_y, m_x, m_y, v_x, v_y (float32, one per texel) and
-    step (int64, one element).  Returns the loss tensor (one float, before the update) or None.
+    step (int64, one element).  n_texels_total: the whole map's texel count when these texels are a part
+    of it (pass stream_id = the part's first texel); 0 means this call's count.  Returns the loss tensor
+    (one float, before the update) or None.
     """
     nt = wi_x.numel()
     if workspace is None:
