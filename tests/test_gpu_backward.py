@@ -2,7 +2,8 @@
 
 The reference gradient is the oracle's vector-Jacobian product (oracle.grad,
 complex step through Sec. 2 / Sec. 3.3 / Eq. 1 in FP64), pinned against
-central differences on the CPU.  Per sample the error is measured against the
+central differences on the CPU; one test also takes FP64 central differences of
+the oracle's forward map as the reference directly.  Per sample the error is measured against the
 largest reference component, e = max_k |g_k - r_k| / max_k |r_k|.  Like the
 forward, the adjoint inherits the conditioning of h = c + i, so a small tail
 of ill-conditioned samples is reported rather than bounded by a flat limit.
@@ -11,6 +12,7 @@ import numpy as np
 import pytest
 import torch
 
+import parity
 import workloads
 from oracle import grad, philox, vndf as ovndf
 
@@ -78,6 +80,41 @@ def test_backward_matches_complex_step(v, iso, explicit):
     gw = got[:3]
     hom = np.abs((gw * wi).sum(0)) / (np.sqrt((gw ** 2).sum(0)) * np.sqrt((wi ** 2).sum(0)) + 1e-30)
     assert np.quantile(hom, 0.999) < 1e-3
+
+
+@pytest.mark.parametrize("ext", [False, True])
+def test_backward_matches_central_differences(v, ext):
+    """The adjoint against FP64 central finite differences of the oracle's forward map, a referee
+    independent of the complex step: g . J with J[k] = (f(x + s e_k) - f(x - s e_k)) / 2s,
+    s = 1e-6 max(1, |x_k|).  Extended: wi on the whole sphere.  The differences lose accuracy where
+    the step reaches a singularity, so the samples within 1e-2 of a = 1 + i.z = 0 are left to the
+    complex-step tests, as are those on which the FP64 forward itself is weak."""
+    n = 8195
+    d = (workloads.sphere_stream if ext else workloads.adjoint_2e24)(n=n, seed=21, device=DEV)
+    keys = ("wi_x", "wi_y", "wi_z", "alpha_x", "alpha_y")
+    wi = np.stack([_np(d[k]) for k in keys[:3]])
+    ax, ay = _np(d["alpha_x"]), _np(d["alpha_y"])
+    u1, u2 = philox.sample_uniforms(31, 0, 0, n)
+    ok = ovndf.in_domain(wi, ax, ay, ext)
+    rng = np.random.default_rng(8)
+    gw = rng.standard_normal((3, n))
+    with np.errstate(all="ignore"):
+        _, pdf = ovndf.sample_vndf_with_pdf(u1, u2, wi, ax, ay, extended=ext)
+        gp = np.where(ok, rng.standard_normal(n) / pdf, 0.0)  # pdf and wm terms of comparable size
+    gw32, gp32 = gw.astype(np.float32), gp.astype(np.float32)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32), device=DEV)  # noqa: E731
+    out = v.vndf_sample_backward(*(d[k] for k in keys), u1=t(u1), u2=t(u2), g_wm_x=t(gw32[0]), g_wm_y=t(gw32[1]),
+                                 g_wm_z=t(gw32[2]), g_pdf=t(gp32), extended=ext)
+    got = np.stack([_np(x) for x in out])
+    assert np.isfinite(got).all() and np.all(got[:, ~ok] == 0.0)
+    keep = ok & (parity.one_plus_zi(wi, ax, ay) >= 1e-2) & ~parity.fp64_weak(u2, wi, ax, ay)
+    idx = np.flatnonzero(keep)
+    assert idx.size > (0.6 if ext else 0.99) * n  # sphere: 75 % kept (small alpha pushes i.z to -1)
+    with np.errstate(all="ignore"):
+        jac = grad.jacobian_central_difference(u1[idx], u2[idx], wi[:, idx], ax[idx], ay[idx], extended=ext)
+    g = np.concatenate([gw32.astype(np.float64), gp32.astype(np.float64)[None]])[:, idx]
+    ref = np.einsum("ion,on->in", jac, g)
+    _check_errors(_errors(got[:, idx], ref), f"backward vs central differences ext={ext}")
 
 
 def test_backward_optional_outputs_and_inputs(v):
