@@ -251,17 +251,19 @@ def vndf_sample_hemisphere(wi_x, wi_y, wi_z, u1=None, u2=None, seed=0, counter_b
 
 def vndf_sample_backward(wi_x, wi_y, wi_z, alpha_x, alpha_y=None, u1=None, u2=None, seed=0, counter_base=0,
                          stream_id=0, g_wm_x=None, g_wm_y=None, g_wm_z=None, g_pdf=None, want_wi=True,
-                         want_alpha=True, n=None, stream=None, extended=False):
+                         want_alpha=True, n=None, stream=None, extended=False, outputs=None):
     """Gradients of (wm, pdf) w.r.t. (wi, alpha) for fixed u; see vndf_sample_backward (and, with
     extended=True, vndf_sample_backward_extended) in include/vndf.h.
 
     Returns (g_wi_x, g_wi_y, g_wi_z, g_alpha_x, g_alpha_y); entries not requested are None.
-    With alpha_y=None (isotropic) g_alpha_x holds d/d alpha and g_alpha_y is None.
+    With alpha_y=None (isotropic) g_alpha_x holds d/d alpha and g_alpha_y is None.  ``outputs`` may
+    pass preallocated (g_wi_x, g_wi_y, g_wi_z, g_alpha_x, g_alpha_y); those not requested are ignored.
     """
     n = wi_x.numel() if n is None else int(n)
-    g_wi = [_out(None, n, wi_x) for _ in range(3)] if want_wi else [None, None, None]
-    g_ax = _out(None, n, wi_x) if want_alpha else None
-    g_ay = _out(None, n, wi_x) if (want_alpha and alpha_y is not None) else None
+    given = list(outputs) if outputs is not None else [None] * 5
+    g_wi = [_out(given[k], n, wi_x) for k in range(3)] if want_wi else [None, None, None]
+    g_ax = _out(given[3], n, wi_x) if want_alpha else None
+    g_ay = _out(given[4], n, wi_x) if (want_alpha and alpha_y is not None) else None
     name = "vndf_sample_backward_extended" if extended else "vndf_sample_backward"
     st = getattr(load(), name)(
         n, _ptr(wi_x, "wi_x"), _ptr(wi_y, "wi_y"), _ptr(wi_z, "wi_z"), _ptr(alpha_x, "alpha_x"),
