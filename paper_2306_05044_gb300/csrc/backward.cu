@@ -25,6 +25,11 @@
 #ifndef VNDF_BWD_MIN_BLOCKS
 #define VNDF_BWD_MIN_BLOCKS 3
 #endif
+// 1 = the loss's partial-sum kernel is a programmatic dependent launch of the loss kernel before it:
+// it is launched while that kernel runs and waits (in hardware) for its completion before reading.
+#ifndef VNDF_LOSS_PDL
+#define VNDF_LOSS_PDL 1
+#endif
 
 namespace vndf {
 
@@ -249,6 +254,9 @@ __global__ void __launch_bounds__(kBwdBlock, 3) loss_backward_kernel(BwdArgs a, 
                                                                   int64_t chunks, float* partials,
                                                                   unsigned* sum_counter) {
   if (sum_counter && blockIdx.x == 0 && threadIdx.x == 0) *sum_counter = 0u;  // read by sum_partials_kernel
+#if VNDF_LOSS_PDL
+  asm volatile("griddepcontrol.launch_dependents;");  // the sum kernel may be scheduled; it waits for us
+#endif
   for (int64_t ch = ch0 + blockIdx.x; ch < chunks; ch += gridDim.x) {
     const int64_t e = ch * kChunk + 4 * int64_t(threadIdx.x);
     float X[4], Y[4], Z[4], AX[4], AY[4], U1[4], U2[4], CX[4], CY[4], CZ[4];
@@ -371,6 +379,9 @@ __global__ void __launch_bounds__(kBwdBlock, VNDF_BWD_MIN_BLOCKS) loss_backward_
                                                                        float* partials, unsigned* sum_counter) {
   constexpr int NS = loss_streams_in<PHILOX, ISO>();
   if (blockIdx.x == 0 && threadIdx.x == 0) *sum_counter = 0u;  // read by sum_partials_kernel
+#if VNDF_LOSS_PDL
+  asm volatile("griddepcontrol.launch_dependents;");  // the sum kernel may be scheduled; it waits for us
+#endif
   extern __shared__ float4 smem_l[];  // [2][NS][kBwdBlock]
   float4* mine = smem_l + threadIdx.x;
   if (int64_t(blockIdx.x) < chunks)
@@ -451,6 +462,9 @@ __global__ void __launch_bounds__(kSumBlock) sum_partials_kernel(const float* pa
                                                                  int64_t nseg, unsigned* counter, float* out) {
   __shared__ float smem[32];
   __shared__ bool last;
+  // as a programmatic dependent launch: wait until the loss kernel before it has completed and its
+  // writes are visible (returns at once after an ordinary launch)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   for (int64_t b = blockIdx.x; b < nseg; b += gridDim.x) {
     const int64_t j0 = b * kSegPartials, j1 = j0 + kSegPartials < m ? j0 + kSegPartials : m;
     float v = 0.f;
@@ -537,7 +551,23 @@ int launch_loss(const BwdArgs& a, int64_t n, bool vec, const LossWorkspace& w, f
   }
   const int64_t nseg = loss_segments(groups);
   const unsigned sgrid = static_cast<unsigned>(nseg < 65535 ? nseg : 65535);
+#if VNDF_LOSS_PDL
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(sgrid);
+  cfg.blockDim = dim3(kSumBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const float* cpartials = partials;
+  if (cudaLaunchKernelEx(&cfg, sum_partials_kernel, cpartials, groups, w.seg, nseg, w.counter, loss) != cudaSuccess)
+    return VNDF_ERR_CUDA;
+#else
   sum_partials_kernel<<<sgrid, kSumBlock, 0, s>>>(partials, groups, w.seg, nseg, w.counter, loss);
+#endif
   return launch_status();
 }
 
