@@ -233,8 +233,15 @@ def sample_case(theta_deg, phi_deg, ax, ay, n, seed, method="cap"):
 def chi2_vs_pdf_pvalue(theta_deg, phi_deg, ax, ay, n=1_000_000, seed=8):
     """P8: sampled histogram against expected counts from the pdf."""
     wm = sample_case(theta_deg, phi_deg, ax, ay, n, seed)
+    return chi2_samples_vs_pdf_pvalue(wm, direction(theta_deg, phi_deg), ax, ay)
+
+
+def chi2_samples_vs_pdf_pvalue(wm, wi, ax, ay):
+    """Chi-square p-value of the normals wm (3, n), drawn for one (wi, ax, ay), against the expected
+    counts from the quadrature of Eq. 1 over each histogram bin (bins with fewer than 5 pooled)."""
+    n = wm.shape[1]
     obs = counts(wm, ax, ay)
-    exp = n * expected_bin_probabilities(direction(theta_deg, phi_deg), ax, ay)
+    exp = n * expected_bin_probabilities(wi, ax, ay)
     keep = exp >= 5
     o = np.append(obs[keep], obs[~keep].sum())
     e = np.append(exp[keep], exp[~keep].sum())
