@@ -450,8 +450,15 @@ def _extended_case(theta_deg, phi_deg, ax, ay, n, seed):
 
 def extended_chi2_vs_pdf_pvalue(theta_deg, phi_deg, ax, ay, n=1_000_000, seed=26):
     wm = _extended_case(theta_deg, phi_deg, ax, ay, n, seed)
+    return extended_chi2_samples_vs_pdf_pvalue(wm, direction(theta_deg, phi_deg), ax, ay)
+
+
+def extended_chi2_samples_vs_pdf_pvalue(wm, wi, ax, ay):
+    """Chi-square p-value of normals wm (3, n) drawn for one wi (below the horizon allowed) against
+    the quadrature of the extended density over each histogram bin."""
+    n = wm.shape[1]
     obs = counts(wm, ax, ay)
-    exp = n * extended_expected_bin_probabilities(direction(theta_deg, phi_deg), ax, ay)
+    exp = n * extended_expected_bin_probabilities(wi, ax, ay)
     keep = exp >= 5
     o = np.append(obs[keep], obs[~keep].sum())
     e = np.append(exp[keep], exp[~keep].sum())

@@ -6,6 +6,8 @@ directly: P8, a chi-square of the normals' histogram against the quadrature of E
 bin (2^22 samples per case, 4x the oracle's own test, where the quadrature is still far finer
 than the counting noise), and P7, the cap sampler against the prior polar-disk sampler, whose
 distributions the paper claims equal (two-sample chi-square, 2^23 samples each, no quadrature).
+The extended method is held to its own density for incident directions below the horizon (2^21
+samples per case).
 """
 import numpy as np
 import pytest
@@ -51,4 +53,13 @@ def test_gpu_cap_matches_prior_sampler(v, case):
     b, _ = _draw(v, case, 1 << 23, "polar", 42)
     p = oc.two_sample_chi2_pvalue(oc.counts(a, case[2], case[3]), oc.counts(b, case[2], case[3]))
     print(case, f"P7 p = {p:.3g}")
+    assert p > 1e-3
+
+
+@pytest.mark.parametrize("case", oc.EXT_CASES[:4])
+def test_gpu_extended_histogram_matches_pdf(v, case):
+    wm, wi = _draw(v, case, 1 << 21, "cap_extended", 51)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        p = oc.extended_chi2_samples_vs_pdf_pvalue(wm, wi, case[2], case[3])
+    print(case, f"extended P8 p = {p:.3g}")
     assert p > 1e-3
