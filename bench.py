@@ -581,7 +581,7 @@ def fwd_bwd(vndf, dev, rank, world, timed, peak, log2n):
             "ms_per_step": ms, "steps": steps,
             "hbm": {"algorithmic_bytes": 52 * n, "achieved_gbs": 52 * n / (ms * 1e-3) / 1e9,
                     "frac": 52 * n / (ms * 1e-3) / 1e9 / peak},
-            "kernels": "loss_backward_pipe_kernel (+ loss_backward_kernel for a ragged last chunk) + sum_partials_kernel"}
+            "kernels": "loss_backward_pipe_kernel (+ loss_backward_kernel for a ragged last chunk) + sum_partials_kernel (programmatic dependent launch)"}
 
 
 def backward_generic(vndf, dev, rank, world, timed, peak, log2n):
