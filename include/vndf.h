@@ -20,9 +20,26 @@
  * - `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
  *   are asynchronous and allocate no memory.
  * - n = 0 is a no-op that returns VNDF_OK without examining any pointer.
+ * - Output arrays must not overlap input arrays or one another: a kernel may
+ *   store an output before it has read every input it still needs (the
+ *   double-float recomputation of an ill-conditioned sample rereads the
+ *   sample's inputs after its FP32 result has been stored).  A call in which
+ *   an output pointer equals an input pointer or another output pointer is
+ *   rejected with VNDF_ERR_ARG; partial overlaps cannot be told from the
+ *   pointers and give undefined results.  Inputs may share memory.
  * - Host-side argument errors return a negative VNDF_ERR_* code before any
- *   work is enqueued.  A failed launch returns VNDF_ERR_CUDA.  Errors that
- *   happen while the kernel runs surface at the caller's next synchronisation.
+ *   work is enqueued.  A failed launch, or a current device that cannot be
+ *   queried (launch shapes are sized from its multiprocessor count), returns
+ *   VNDF_ERR_CUDA.  Errors that happen while the kernel runs surface at the
+ *   caller's next synchronisation.
+ * - Fault injection, for testing a caller's error handling without making a
+ *   GPU fail: when the environment variable VNDF_FAULT is "launch", "align"
+ *   or "workspace", optionally followed by "@" and an entry point's name
+ *   (e.g. "launch@vndf_sample"), every GPU entry point (or only the named
+ *   one) returns, after its argument checks and before it enqueues anything,
+ *   VNDF_ERR_CUDA, VNDF_ERR_ALIGN or (entry points that take a workspace
+ *   only) VNDF_ERR_WORKSPACE.  The variable is read on every call; unset or
+ *   empty, it has no effect.
  * - Domain: wi.z > 0, alpha_x > 0, alpha_y > 0, all finite.  wi need not be
  *   unit length (the method is invariant to its scale).  A sample outside the
  *   domain raises no error: it returns wm = (0, 0, 1) and pdf = 0.
@@ -96,7 +113,8 @@ int vndf_pointer_device_accessible(const void *p);
  * [0, 1), Sec. 2).  Values lie in [0, 1 - 2^-24] and are exact float32.
  *   n        number of samples (0 <= n < 2^62); n = 0 is a no-op.
  *   u1, u2   outputs, n floats each (device).
- * Returns VNDF_OK, VNDF_ERR_NULL, VNDF_ERR_SIZE, VNDF_ERR_ALIGN or VNDF_ERR_CUDA.
+ * Returns VNDF_OK, VNDF_ERR_NULL, VNDF_ERR_SIZE, VNDF_ERR_ALIGN, VNDF_ERR_ARG
+ * (u1 == u2) or VNDF_ERR_CUDA.
  */
 int vndf_rng_uniform(int64_t n, uint64_t seed, uint64_t counter_base, uint32_t stream_id,
                      float *u1, float *u2, void *cuda_stream);
@@ -166,7 +184,7 @@ int vndf_sample_reflection(int64_t n,
  *   Q   = wm.x^2/alpha_x^2 + wm.y^2/alpha_y^2 + wm.z^2,
  * which is G1(wi) max(0, wi.wm) D(wm) / wi.z for unit wm.  wm is used as given
  * (unit length expected); wm.z <= 0 gives 0.  alpha_y = NULL means isotropic.
- * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, ALIGN, CUDA).
+ * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, ALIGN, ARG, CUDA).
  */
 int vndf_pdf(int64_t n,
              const float *wi_x, const float *wi_y, const float *wi_z,
@@ -306,7 +324,9 @@ int vndf_sample_loss_backward(int64_t n,
 /* Device workspace (bytes) for vndf_albedo_batched / vndf_albedo_autotune with
  * n_queries queries of at most max_samples_per_query samples each:
  * control words (item scan, counters) plus one float per 256-sample group
- * slot.  0 when n_queries <= 0. */
+ * slot.  0 when n_queries <= 0 or when the batch exceeds the limits of
+ * vndf_albedo_batched (max_samples_per_query > 2^30, or n_queries x
+ * ceil(max_samples_per_query / 256) >= 2^31). */
 size_t vndf_albedo_workspace_bytes(int32_t n_queries, int32_t max_samples_per_query);
 
 /*
@@ -327,7 +347,10 @@ size_t vndf_albedo_workspace_bytes(int32_t n_queries, int32_t max_samples_per_qu
  *   n_samples          per-query sample counts N_q (int32, device).  A count
  *                      outside [0, max_samples_per_query] yields E_q = NaN; a
  *                      count of 0 (in the domain) yields E_q = 0.
- *   max_samples_per_query  the bound the workspace was sized for (<= 2^30).
+ *   max_samples_per_query  the bound the workspace was sized for (<= 2^30,
+ *                      and n_queries x ceil(max_samples_per_query / 256)
+ *                      < 2^31 so that every 256-sample group slot has an
+ *                      int32 index; larger batches return VNDF_ERR_SIZE).
  *   f0                 Schlick reflectance at normal incidence.
  *   seed, counter_base, stream_id  Philox: query q draws from stream
  *                      stream_id + q, sample j from global index counter_base + j.
@@ -473,7 +496,7 @@ int vndf_microbench(int64_t lanes, int32_t samples_per_lane, int method, int pre
  *                      benchmark times.  Ignored for the prior sampler.
  *   threads            host threads (0 = all hardware threads).
  * Results do not depend on the thread count.
- * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, METHOD).
+ * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, METHOD, ARG).
  */
 int vndf_cpu_sample(int64_t n,
                     const float *wi_x, const float *wi_y, const float *wi_z,
@@ -506,6 +529,10 @@ int vndf_cpu_sample(int64_t n,
  *   - All calls on a device share the one array.  Each call resets the parts it
  *     reads, but calls that overlap on the GPU (concurrent streams, or several
  *     host threads) race on it: order them on one stream.
+ *   - The cached address belongs to the device's current context: after
+ *     cudaDeviceReset (or anything else that destroys and recreates the
+ *     primary context) it is stale, and the entry point must not be called
+ *     again in that process.
  * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, ALIGN, ARG, CUDA).
  */
 int vndf_albedo_batched_noalloc(int32_t n_queries,

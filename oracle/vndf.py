@@ -26,7 +26,7 @@ follow:
 * ``projected_area``       Eq. 4 carried through M (App. A): sigma(wi) = |M^-1 wi| sigma_std(z_i')
 * ``sample_hemisphere``    Sec. 3.3 used stand-alone: the cap sample normalised, with its Eq. 2 density
 
-Readings where the paper is silent (each is listed in the design notes):
+Readings where the paper is silent (domain, extended domain, scale of wi, which uniform drives which angle):
 * Domain: wi.z > 0, alpha_x > 0, alpha_y > 0, all inputs finite.  Outside it a
   sample returns the defined fallback wm = (0, 0, 1) with pdf = 0.
 * Extended domain (``extended=True``): the construction of Sec. 3.2-3.3 never

@@ -304,23 +304,46 @@ int launch_albedo(AlbedoArgs a, const AlbedoConfig& c, cudaStream_t s) {
 
 using namespace vndf;
 
+namespace vndf {
+// Work items, their offsets and the item total are int32: every group slot of
+// the batch (n_queries x ceil(max / 256), which bounds the items) must have an
+// index below 2^31.
+inline bool albedo_fits_int32(int32_t n_queries, int32_t max_samples) {
+  const int64_t gmax = (int64_t(max_samples) + kGroupSamples - 1) / kGroupSamples;
+  return int64_t(n_queries) * gmax < (int64_t(1) << 31);
+}
+}  // namespace vndf
+
 extern "C" size_t vndf_albedo_workspace_bytes(int32_t n_queries, int32_t max_samples_per_query) {
-  if (n_queries <= 0 || max_samples_per_query < 0) return 0;
+  if (n_queries <= 0 || max_samples_per_query < 0 || max_samples_per_query > (1 << 30)) return 0;
+  if (!albedo_fits_int32(n_queries, max_samples_per_query)) return 0;
   const size_t gmax = (size_t(max_samples_per_query) + kGroupSamples - 1) / kGroupSamples;
   return albedo_partials_offset(n_queries) + size_t(n_queries) * gmax * sizeof(float);
 }
 
 namespace vndf {
+// Checks of everything but the workspace.
+int albedo_validate_args(int32_t n_queries, const float* wi_x, const float* wi_y, const float* wi_z,
+                         const float* alpha_x, const float* alpha_y, const int32_t* n_samples, int32_t max_samples,
+                         float* E) {
+  if (n_queries < 0 || max_samples < 0 || max_samples > (1 << 30)) return VNDF_ERR_SIZE;
+  if (n_queries == 0) return VNDF_OK;
+  if (!albedo_fits_int32(n_queries, max_samples)) return VNDF_ERR_SIZE;
+  if (!wi_x || !wi_y || !wi_z || !alpha_x || !n_samples || !E) return VNDF_ERR_NULL;
+  if (!all_aligned4(wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples, E)) return VNDF_ERR_ALIGN;
+  if (aliased({E}, {wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples})) return VNDF_ERR_ARG;
+  return VNDF_OK;
+}
+
 int albedo_validate(int32_t n_queries, const float* wi_x, const float* wi_y, const float* wi_z, const float* alpha_x,
                     const float* alpha_y, const int32_t* n_samples, int32_t max_samples, float* E,
                     void* workspace, size_t workspace_bytes) {
-  if (n_queries < 0 || max_samples < 0 || max_samples > (1 << 30)) return VNDF_ERR_SIZE;
-  if (n_queries == 0) return VNDF_OK;
-  if (!wi_x || !wi_y || !wi_z || !alpha_x || !n_samples || !E) return VNDF_ERR_NULL;
-  if (!all_aligned4(wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples, E)) return VNDF_ERR_ALIGN;
+  const int st = albedo_validate_args(n_queries, wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples, max_samples, E);
+  if (st != VNDF_OK || n_queries == 0) return st;
   if (!workspace || workspace_bytes < vndf_albedo_workspace_bytes(n_queries, max_samples))
     return VNDF_ERR_WORKSPACE;
   if (!aligned(workspace, 256)) return VNDF_ERR_ALIGN;
+  if (aliased({E, workspace}, {wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples})) return VNDF_ERR_ARG;
   return VNDF_OK;
 }
 
@@ -348,11 +371,14 @@ AlbedoArgs albedo_args(int32_t n_queries, const float* wi_x, const float* wi_y, 
 }
 }  // namespace vndf
 
-extern "C" int vndf_albedo_batched(int32_t n_queries, const float* wi_x, const float* wi_y, const float* wi_z,
-                                   const float* alpha_x, const float* alpha_y, const int32_t* n_samples,
-                                   int32_t max_samples_per_query, float f0, uint64_t seed, uint64_t counter_base,
-                                   uint32_t stream_id, float* E, void* workspace, size_t workspace_bytes,
-                                   const int32_t* config, void* cuda_stream) {
+namespace vndf {
+// vndf_albedo_batched after its argument checks and with the name under which
+// an injected fault is looked up (the no-allocation variant runs the same path).
+int albedo_batched_entry(const char* name, int32_t n_queries, const float* wi_x, const float* wi_y,
+                         const float* wi_z, const float* alpha_x, const float* alpha_y, const int32_t* n_samples,
+                         int32_t max_samples_per_query, float f0, uint64_t seed, uint64_t counter_base,
+                         uint32_t stream_id, float* E, void* workspace, size_t workspace_bytes,
+                         const int32_t* config, bool takes_workspace, void* cuda_stream) {
   const int st = albedo_validate(n_queries, wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples,
                                  max_samples_per_query, E, workspace, workspace_bytes);
   if (st != VNDF_OK || n_queries == 0) return st;
@@ -361,9 +387,21 @@ extern "C" int vndf_albedo_batched(int32_t n_queries, const float* wi_x, const f
     c = AlbedoConfig{config[0], config[1], config[2]};
     if (!config_ok(c)) return VNDF_ERR_ARG;
   }
+  if (const int f = pre_launch(name, takes_workspace)) return f;
   const AlbedoArgs a = albedo_args(n_queries, wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples,
                                    max_samples_per_query, f0, seed, counter_base, stream_id, E, workspace);
   return launch_albedo(a, c, static_cast<cudaStream_t>(cuda_stream));
+}
+}  // namespace vndf
+
+extern "C" int vndf_albedo_batched(int32_t n_queries, const float* wi_x, const float* wi_y, const float* wi_z,
+                                   const float* alpha_x, const float* alpha_y, const int32_t* n_samples,
+                                   int32_t max_samples_per_query, float f0, uint64_t seed, uint64_t counter_base,
+                                   uint32_t stream_id, float* E, void* workspace, size_t workspace_bytes,
+                                   const int32_t* config, void* cuda_stream) {
+  return albedo_batched_entry("vndf_albedo_batched", n_queries, wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples,
+                              max_samples_per_query, f0, seed, counter_base, stream_id, E, workspace,
+                              workspace_bytes, config, true, cuda_stream);
 }
 
 extern "C" int vndf_albedo_autotune(int32_t n_queries, const float* wi_x, const float* wi_y, const float* wi_z,
@@ -376,6 +414,7 @@ extern "C" int vndf_albedo_autotune(int32_t n_queries, const float* wi_x, const 
                                  max_samples_per_query, E, workspace, workspace_bytes);
   if (st != VNDF_OK) return st;
   if (n_queries == 0) return VNDF_ERR_SIZE;
+  if (const int f = pre_launch("vndf_albedo_autotune", true)) return f;
   const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   AlbedoArgs a = albedo_args(n_queries, wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples, max_samples_per_query, f0,
                              seed, counter_base, stream_id, E, workspace);
@@ -474,17 +513,20 @@ extern "C" int vndf_albedo_batched_noalloc(int32_t n_queries, const float* wi_x,
                                            const int32_t* n_samples, int32_t max_samples_per_query, float f0,
                                            uint64_t seed, uint64_t counter_base, uint32_t stream_id, float* E,
                                            const int32_t* config, void* cuda_stream) {
-  if (n_queries < 0 || max_samples_per_query < 0 || max_samples_per_query > (1 << 30)) return VNDF_ERR_SIZE;
-  if (n_queries == 0) return VNDF_OK;
+  const int st = albedo_validate_args(n_queries, wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples,
+                                      max_samples_per_query, E);
+  if (st != VNDF_OK || n_queries == 0) return st;
   if (vndf_albedo_workspace_bytes(n_queries, max_samples_per_query) > VNDF_ALBEDO_NOALLOC_SCRATCH_BYTES)
     return VNDF_ERR_SIZE;
+  if (config && !config_ok(AlbedoConfig{config[0], config[1], config[2]})) return VNDF_ERR_ARG;
+  if (const int f = injected_fault("vndf_albedo_batched_noalloc", false)) return f;
   void* scratch = nullptr;
   const int rc = scratch_address(&scratch);
   if (rc != VNDF_OK) return rc;
   // The prologue kernel rewrites every control word the persistent kernel reads,
   // and each group partial is written before it is read, so what an earlier call
   // left in the array never leaks into this one.
-  return vndf_albedo_batched(n_queries, wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples, max_samples_per_query, f0,
-                             seed, counter_base, stream_id, E, scratch, VNDF_ALBEDO_NOALLOC_SCRATCH_BYTES, config,
-                             cuda_stream);
+  return albedo_batched_entry("vndf_albedo_batched_noalloc", n_queries, wi_x, wi_y, wi_z, alpha_x, alpha_y,
+                              n_samples, max_samples_per_query, f0, seed, counter_base, stream_id, E, scratch,
+                              VNDF_ALBEDO_NOALLOC_SCRATCH_BYTES, config, false, cuda_stream);
 }

@@ -577,7 +577,7 @@ using namespace vndf;
 
 namespace vndf {
 template <bool EXT>
-int backward_entry(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z, const float* alpha_x,
+int backward_entry(const char* name, int64_t n, const float* wi_x, const float* wi_y, const float* wi_z, const float* alpha_x,
                    const float* alpha_y, const float* u1, const float* u2, uint64_t seed, uint64_t counter_base,
                    uint32_t stream_id, const float* g_wm_x, const float* g_wm_y, const float* g_wm_z,
                    const float* g_pdf, float* g_wi_x, float* g_wi_y, float* g_wi_z, float* g_alpha_x,
@@ -594,6 +594,10 @@ int backward_entry(int64_t n, const float* wi_x, const float* wi_y, const float*
   if (!all_aligned4(wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, g_wm_x, g_wm_y, g_wm_z, g_pdf, g_wi_x, g_wi_y,
                     g_wi_z, g_alpha_x, g_alpha_y))
     return VNDF_ERR_ALIGN;
+  if (aliased({g_wi_x, g_wi_y, g_wi_z, g_alpha_x, g_alpha_y},
+              {wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, g_wm_x, g_wm_y, g_wm_z, g_pdf}))
+    return VNDF_ERR_ARG;
+  if (const int f = pre_launch(name)) return f;
   BwdArgs a{wi_x,   wi_y,   wi_z,   alpha_x, alpha_y,   u1,        u2,       g_wm_x,
             g_wm_y, g_wm_z, g_pdf,  g_wi_x,  g_wi_y,    g_wi_z,    g_alpha_x, g_alpha_y,
             make_rng(seed, counter_base, stream_id)};
@@ -613,8 +617,9 @@ extern "C" int vndf_sample_backward(int64_t n, const float* wi_x, const float* w
                                     const float* g_wm_y, const float* g_wm_z, const float* g_pdf, float* g_wi_x,
                                     float* g_wi_y, float* g_wi_z, float* g_alpha_x, float* g_alpha_y,
                                     void* cuda_stream) {
-  return backward_entry<false>(n, wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, seed, counter_base, stream_id, g_wm_x,
-                               g_wm_y, g_wm_z, g_pdf, g_wi_x, g_wi_y, g_wi_z, g_alpha_x, g_alpha_y, cuda_stream);
+  return backward_entry<false>("vndf_sample_backward", n, wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, seed,
+                               counter_base, stream_id, g_wm_x, g_wm_y, g_wm_z, g_pdf, g_wi_x, g_wi_y, g_wi_z,
+                               g_alpha_x, g_alpha_y, cuda_stream);
 }
 
 extern "C" int vndf_sample_backward_extended(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z,
@@ -623,8 +628,9 @@ extern "C" int vndf_sample_backward_extended(int64_t n, const float* wi_x, const
                                              uint32_t stream_id, const float* g_wm_x, const float* g_wm_y,
                                              const float* g_wm_z, const float* g_pdf, float* g_wi_x, float* g_wi_y,
                                              float* g_wi_z, float* g_alpha_x, float* g_alpha_y, void* cuda_stream) {
-  return backward_entry<true>(n, wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, seed, counter_base, stream_id, g_wm_x,
-                              g_wm_y, g_wm_z, g_pdf, g_wi_x, g_wi_y, g_wi_z, g_alpha_x, g_alpha_y, cuda_stream);
+  return backward_entry<true>("vndf_sample_backward_extended", n, wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, seed,
+                              counter_base, stream_id, g_wm_x, g_wm_y, g_wm_z, g_pdf, g_wi_x, g_wi_y, g_wi_z,
+                              g_alpha_x, g_alpha_y, cuda_stream);
 }
 
 extern "C" size_t vndf_loss_workspace_bytes(int64_t n) {
@@ -653,6 +659,10 @@ extern "C" int vndf_sample_loss_backward(int64_t n, const float* wi_x, const flo
   if (!all_aligned4(wi_x, wi_y, wi_z, alpha_x, alpha_y, c_x, c_y, c_z, u1, u2, g_wi_x, g_wi_y, g_wi_z,
                     g_alpha_x, g_alpha_y, loss, workspace))
     return VNDF_ERR_ALIGN;
+  if (aliased({g_wi_x, g_wi_y, g_wi_z, g_alpha_x, g_alpha_y, loss, workspace},
+              {wi_x, wi_y, wi_z, alpha_x, alpha_y, c_x, c_y, c_z, u1, u2}))
+    return VNDF_ERR_ARG;
+  if (const int f = pre_launch("vndf_sample_loss_backward", true)) return f;
   BwdArgs a{wi_x, wi_y,   wi_z,   alpha_x, alpha_y,   u1,        u2,       c_x,
             c_y,  c_z,    nullptr, g_wi_x, g_wi_y,    g_wi_z,    g_alpha_x, g_alpha_y,
             make_rng(seed, counter_base, stream_id)};

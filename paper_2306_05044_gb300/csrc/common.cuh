@@ -5,6 +5,7 @@
 
 #include <atomic>
 #include <cstdint>
+#include <initializer_list>
 
 #include "vndf.h"
 
@@ -27,17 +28,53 @@ inline bool all_aligned16(P... p) {
 }
 
 // Multiprocessor count of the current device (cached per device; several host
-// threads may ask at once, and all of them store the same value).
+// threads may ask at once, and all of them store the same value).  0 when the
+// device or its attribute cannot be queried: nothing is assumed about the part.
 inline int sm_count() {
   static std::atomic<int> cache[64];  // zero-initialised (static storage)
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
-  int v = cache[dev].load(std::memory_order_relaxed);
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 0;
+  int v = dev < 64 ? cache[dev].load(std::memory_order_relaxed) : 0;
   if (v == 0) {
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
-    cache[dev].store(v, std::memory_order_relaxed);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 0;
+    if (dev < 64) cache[dev].store(v, std::memory_order_relaxed);
   }
   return v;
+}
+
+// Host-side fault injection (status.cu), for testing how callers handle the
+// library's error returns without making any GPU fail.  The environment
+// variable VNDF_FAULT = "<kind>" or "<kind>@<entry point name>" makes the
+// named entry point (every one, without a name) return, after its argument
+// checks and before it enqueues any work:
+//   launch     VNDF_ERR_CUDA, as if a kernel launch had failed;
+//   align      VNDF_ERR_ALIGN, as if a pointer were misaligned;
+//   workspace  VNDF_ERR_WORKSPACE, only in entry points that take a workspace.
+// Unset or empty: VNDF_OK (no effect).
+int injected_fault(const char* entry, bool takes_workspace);
+
+// Status of an entry point just before it enqueues work: an injected fault,
+// else VNDF_ERR_CUDA when the current device cannot be queried (launch shapes
+// are sized from its multiprocessor count), else VNDF_OK.
+inline int pre_launch(const char* entry, bool takes_workspace = false) {
+  const int f = injected_fault(entry, takes_workspace);
+  if (f != VNDF_OK) return f;
+  return sm_count() > 0 ? VNDF_OK : VNDF_ERR_CUDA;
+}
+
+// True when a non-NULL output pointer equals another output pointer or an
+// input pointer.  Outputs must not overlap inputs (a kernel may write an
+// output before it has read every input it needs); exact equality is the
+// overlap that can be detected from pointers alone.
+inline bool aliased(std::initializer_list<const void*> outs, std::initializer_list<const void*> ins) {
+  for (auto o = outs.begin(); o != outs.end(); ++o) {
+    if (*o == nullptr) continue;
+    for (auto p = outs.begin(); p != o; ++p)
+      if (*p == *o) return true;
+    for (const void* i : ins)
+      if (i == *o) return true;
+  }
+  return false;
 }
 
 // Grid for a grid-stride loop over `work` items with `block` threads per CTA:

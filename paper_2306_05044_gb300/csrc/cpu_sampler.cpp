@@ -228,6 +228,17 @@ extern "C" int vndf_cpu_sample(int64_t n, const float* wi_x, const float* wi_y, 
     return VNDF_ERR_METHOD;
   if (n == 0) return VNDF_OK;
   if (!wi_x || !wi_y || !wi_z || !alpha_x || !u1 || !u2 || !wm_x || !wm_y || !wm_z) return VNDF_ERR_NULL;
+  {  // outputs must not overlap the inputs or each other (exact equality is what can be checked)
+    const void* outs[] = {wm_x, wm_y, wm_z, pdf};
+    const void* ins[] = {wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2};
+    for (int o = 0; o < 4; ++o) {
+      if (outs[o] == nullptr) continue;
+      for (int p = 0; p < o; ++p)
+        if (outs[p] == outs[o]) return VNDF_ERR_ARG;
+      for (const void* i : ins)
+        if (i == outs[o]) return VNDF_ERR_ARG;
+    }
+  }
   const HostArgs h{wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, wm_x, wm_y, wm_z, pdf};
   const bool want_pdf = pdf != nullptr, strict = precise != 0;
   auto body = [&](int64_t i0, int64_t i1) {

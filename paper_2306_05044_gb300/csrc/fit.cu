@@ -201,6 +201,11 @@ extern "C" int vndf_fit_step(int32_t n_texels, int32_t n_texels_total, int32_t s
                     adam_v_x, adam_v_y, loss, workspace) ||
       !aligned(step, 8))
     return VNDF_ERR_ALIGN;
+  // alpha and the Adam moments are read and updated in place; each must be an array of its own
+  if (aliased({alpha_x, alpha_y, adam_m_x, adam_m_y, adam_v_x, adam_v_y, step, loss, workspace},
+              {wi_x, wi_y, wi_z, target_x, target_y, target_z}))
+    return VNDF_ERR_ARG;
+  if (const int f = pre_launch("vndf_fit_step", true)) return f;
   FitArgs a{n_texels, samples_per_texel, n_texels_total ? n_texels_total : n_texels,
             wi_x,     wi_y,     wi_z,     target_x,  target_y, target_z,
             alpha_x,  alpha_y,           adam_m_x, adam_m_y, adam_v_x, adam_v_y,  step,     lr,

@@ -192,6 +192,8 @@ extern "C" int vndf_sample_hemisphere(int64_t n, const float* wi_x, const float*
   if (!wi_x || !wi_y || !wi_z || !wm_x || !wm_y || !wm_z) return VNDF_ERR_NULL;
   if ((u1 == nullptr) != (u2 == nullptr)) return VNDF_ERR_ARG;
   if (!all_aligned4(wi_x, wi_y, wi_z, u1, u2, wm_x, wm_y, wm_z, pdf)) return VNDF_ERR_ALIGN;
+  if (aliased({wm_x, wm_y, wm_z, pdf}, {wi_x, wi_y, wi_z, u1, u2})) return VNDF_ERR_ARG;
+  if (const int f = pre_launch("vndf_sample_hemisphere")) return f;
   const HemiArgs a{wi_x, wi_y, wi_z, u1, u2, wm_x, wm_y, wm_z, pdf, make_rng(seed, counter_base, stream_id)};
   const bool vec = all_aligned16(wi_x, wi_y, wi_z, u1, u2, wm_x, wm_y, wm_z, pdf);
   const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);

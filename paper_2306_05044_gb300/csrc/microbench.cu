@@ -86,6 +86,7 @@ extern "C" int vndf_microbench(int64_t lanes, int32_t samples_per_lane, int meth
   if (lanes == 0) return VNDF_OK;
   if (!sums) return VNDF_ERR_NULL;
   if (!aligned(sums, 16)) return VNDF_ERR_ALIGN;
+  if (const int f = pre_launch("vndf_microbench")) return f;
   const Rng r = make_rng(seed, 0, 0);
   const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const unsigned grid = grid_for(lanes, kMicroBlock, 8, 16);

@@ -267,6 +267,8 @@ extern "C" int vndf_sample_reflection(int64_t n, const float* wi_x, const float*
   if ((u1 == nullptr) != (u2 == nullptr)) return VNDF_ERR_ARG;
   if (!all_aligned4(wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, wo_x, wo_y, wo_z, pdf, weight))
     return VNDF_ERR_ALIGN;
+  if (aliased({wo_x, wo_y, wo_z, pdf, weight}, {wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2})) return VNDF_ERR_ARG;
+  if (const int f = pre_launch("vndf_sample_reflection")) return f;
   const ReflArgs a{wi_x, wi_y, wi_z, alpha_x, alpha_y, u1,     u2,
                    f0,   wo_x, wo_y, wo_z,    pdf,     weight, make_rng(seed, counter_base, stream_id)};
   const bool vec = all_aligned16(wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, wo_x, wo_y, wo_z, pdf, weight);

@@ -401,6 +401,8 @@ extern "C" int vndf_rng_uniform(int64_t n, uint64_t seed, uint64_t counter_base,
   if (n == 0) return VNDF_OK;
   if (!u1 || !u2) return VNDF_ERR_NULL;
   if (!all_aligned4(u1, u2)) return VNDF_ERR_ALIGN;
+  if (aliased({u1, u2}, {})) return VNDF_ERR_ARG;
+  if (const int f = pre_launch("vndf_rng_uniform")) return f;
   const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const Rng r = make_rng(seed, counter_base, stream_id);
   int64_t done = 0;
@@ -425,6 +427,8 @@ extern "C" int vndf_sample(int64_t n, const float* wi_x, const float* wi_y, cons
   if (!wi_x || !wi_y || !wi_z || !alpha_x || !wm_x || !wm_y || !wm_z) return VNDF_ERR_NULL;
   if ((u1 == nullptr) != (u2 == nullptr)) return VNDF_ERR_ARG;
   if (!all_aligned4(wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, wm_x, wm_y, wm_z, pdf)) return VNDF_ERR_ALIGN;
+  if (aliased({wm_x, wm_y, wm_z, pdf}, {wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2})) return VNDF_ERR_ARG;
+  if (const int f = pre_launch("vndf_sample")) return f;
   SampleArgs a{wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, wm_x, wm_y, wm_z, pdf,
                make_rng(seed, counter_base, stream_id)};
   const bool vec = all_aligned16(wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2, wm_x, wm_y, wm_z, pdf);
@@ -435,13 +439,15 @@ extern "C" int vndf_sample(int64_t n, const float* wi_x, const float* wi_y, cons
 }
 
 template <bool EXT>
-int pdf_entry(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z, const float* alpha_x,
+int pdf_entry(const char* name, int64_t n, const float* wi_x, const float* wi_y, const float* wi_z, const float* alpha_x,
               const float* alpha_y, const float* wm_x, const float* wm_y, const float* wm_z, float* pdf,
               void* cuda_stream) {
   if (n < 0 || n >= kMaxN) return VNDF_ERR_SIZE;
   if (n == 0) return VNDF_OK;
   if (!wi_x || !wi_y || !wi_z || !alpha_x || !wm_x || !wm_y || !wm_z || !pdf) return VNDF_ERR_NULL;
   if (!all_aligned4(wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf)) return VNDF_ERR_ALIGN;
+  if (aliased({pdf}, {wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z})) return VNDF_ERR_ARG;
+  if (const int f = pre_launch(name)) return f;
   const bool vec = all_aligned16(wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf);
   const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   return alpha_y ? launch_pdf<false, EXT>(n, wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf, vec, s)
@@ -451,11 +457,11 @@ int pdf_entry(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z
 extern "C" int vndf_pdf(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z, const float* alpha_x,
                         const float* alpha_y, const float* wm_x, const float* wm_y, const float* wm_z, float* pdf,
                         void* cuda_stream) {
-  return pdf_entry<false>(n, wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf, cuda_stream);
+  return pdf_entry<false>("vndf_pdf", n, wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf, cuda_stream);
 }
 
 extern "C" int vndf_pdf_extended(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z,
                                  const float* alpha_x, const float* alpha_y, const float* wm_x, const float* wm_y,
                                  const float* wm_z, float* pdf, void* cuda_stream) {
-  return pdf_entry<true>(n, wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf, cuda_stream);
+  return pdf_entry<true>("vndf_pdf_extended", n, wi_x, wi_y, wi_z, alpha_x, alpha_y, wm_x, wm_y, wm_z, pdf, cuda_stream);
 }

@@ -1,4 +1,8 @@
-// Status strings and the ABI version of libvndf.
+// Status strings, the ABI version and host-side fault injection of libvndf.
+#include <cstdlib>
+#include <cstring>
+
+#include "common.cuh"
 #include "vndf.h"
 
 extern "C" int vndf_abi_version(void) { return 3; }
@@ -40,3 +44,23 @@ extern "C" int vndf_pointer_device_accessible(const void* p) {
       return 0;
   }
 }
+
+namespace vndf {
+
+// VNDF_FAULT = "<kind>[@<entry point>]" (see common.cuh).  Read on every call,
+// so a test can set and clear it between calls; an unset variable costs one
+// getenv per call, far below the cost of a launch.
+int injected_fault(const char* entry, bool takes_workspace) {
+  const char* spec = std::getenv("VNDF_FAULT");
+  if (spec == nullptr || *spec == '\0') return VNDF_OK;
+  const char* at = std::strchr(spec, '@');
+  const size_t kind_len = at ? size_t(at - spec) : std::strlen(spec);
+  if (at && std::strcmp(at + 1, entry) != 0) return VNDF_OK;
+  auto is = [&](const char* k) { return kind_len == std::strlen(k) && std::strncmp(spec, k, kind_len) == 0; };
+  if (is("launch")) return VNDF_ERR_CUDA;
+  if (is("align")) return VNDF_ERR_ALIGN;
+  if (is("workspace")) return takes_workspace ? VNDF_ERR_WORKSPACE : VNDF_OK;
+  return VNDF_OK;
+}
+
+}  // namespace vndf

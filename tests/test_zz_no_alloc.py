@@ -6,11 +6,12 @@ plugin that only receives pointers).  It keeps its scratch in a fixed device
 array inside the library.  This file is named so that pytest collects it last.
 It calls the entry point through the C ABI twice in a row (the second call
 reuses the array the first one left behind) and compares each result with
-vndf_albedo_batched at the tolerance the albedo tests use.
+vndf_albedo_batched bit for bit: both run the same kernels, and the albedo sums
+run in an order fixed by the data, so any difference (a control word or
+partial left over from the previous call) is a fault, however small.
 """
 import ctypes
 
-import numpy as np
 import pytest
 import torch
 
@@ -44,12 +45,11 @@ def test_noalloc_matches_workspace_entry_point_twice(lib):
     for seed in (3, 17):  # two calls in a row, with different streams of samples
         ref = lib.vndf_albedo_batched(g["wi_x"], g["wi_y"], g["wi_z"], g["alpha_x"], None, g["n_samples"],
                                       max_samples_per_query=65536, seed=seed)
-        E = torch.full((nq,), -1.0, device=DEV)
+        E = torch.full((nq,), float("nan"), device=DEV)  # a query never finished stays NaN
         assert _call_noalloc(lib, g, nq, 65536, seed, E) == 0
         torch.cuda.synchronize()
-        got = E.cpu().numpy().astype(np.float64)
-        want = ref.cpu().numpy().astype(np.float64)
-        assert np.all(np.abs(got - want) <= 1e-5 * np.abs(want) + 1e-7)
+        assert torch.isfinite(ref).all()
+        assert torch.equal(E, ref)
 
 
 def test_noalloc_rejects_batches_larger_than_its_scratch(lib):
