@@ -64,7 +64,10 @@ def parse_args():
     p.add_argument("--no-extended", action="store_true")
     p.add_argument("--no-isotropic", action="store_true")
     p.add_argument("--no-pdf", action="store_true")
-    p.add_argument("--log2n-adjoint", type=int, default=24)
+    p.add_argument("--log2n-adjoint", type=int, nargs="+", default=[24, 26],
+                   help="sizes of the fused forward+adjoint leg (2^k samples; the first is the workload's)")
+    p.add_argument("--detail-out", default=None,
+                   help="also write the full record (every leg with every field) to this file")
     return p.parse_args()
 
 
@@ -119,11 +122,16 @@ def measured_traffic_per_sample():
         return None
 
 
-def issue_roofline(kernel, samples, ms, clock_mhz):
+def issue_roofline(kernel, samples, ms, clock):
     """ALU issue roofline of a compute-bound kernel: thread instructions per second against
-    SMs x 4 schedulers x 32 lanes x SM clock.  Instructions per sample come from the committed
-    ncu summary (null when the kernel sources changed since)."""
+    SMs x 4 schedulers x 32 lanes x SM clock, the clock being the median sampled during this
+    kernel's own timed region (`clock`, the leg's clock record; the maximum clock when none was
+    taken).  Instructions per sample come from the committed ncu summary (null when the kernel
+    sources changed since)."""
     import torch
+    clock_mhz = (clock or {}).get("sm_mhz")
+    basis = "sampled" if clock_mhz else "maximum"
+    clock_mhz = clock_mhz or max_sm_clock_mhz()
     try:
         vals = {}
         for path in ISSUE_FILES:
@@ -138,7 +146,8 @@ def issue_roofline(kernel, samples, ms, clock_mhz):
     max_mhz = max_sm_clock_mhz()
     peak_max = sms * LANES_PER_SM * max_mhz * 1e6 / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s", "frac": achieved / peak,
-            "thread_inst_per_sample": per, "peak_basis": f"{sms} SMs x 128 lanes x {clock_mhz:.0f} MHz (sampled)",
+            "thread_inst_per_sample": per, "peak_basis": f"{sms} SMs x 128 lanes x {clock_mhz:.0f} MHz ({basis})",
+            "clock_mhz": clock_mhz, "reasons": (clock or {}).get("reasons"),
             "peak_at_max_clock": peak_max, "frac_at_max_clock": achieved / peak_max}
 
 
@@ -361,11 +370,96 @@ def cpu_baseline(budget_s=15.0):
     return {"value": n / wall / 1e9, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
             "sample": f"{chunks} chunks of {m} samples of the anisotropic workload recipe (one seed per chunk), "
                       f"FP64 numpy oracle (Philox + cap sampler + pdf), one process per core, {wall:.1f} s of "
-                      f"oracle time on the busiest core"}
+                      f"oracle time on the busiest core",
+            "sample_short": f"{chunks}x2^20 samples of the workload recipe, FP64 numpy oracle, {pool.cores} "
+                            f"processes, {wall:.0f} s"}
 
 
 def emit(obj):
-    print(json.dumps(obj), flush=True)
+    print(json.dumps(obj, separators=(",", ":")), flush=True)
+
+
+def _sig(x, digits=4):
+    """Floats rounded to `digits` significant digits, recursively (keeps the printed line short)."""
+    if isinstance(x, bool) or x is None:
+        return x
+    if isinstance(x, float):
+        return float(f"{x:.{digits}g}") if math.isfinite(x) else None
+    if isinstance(x, dict):
+        return {k: _sig(v, digits) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [_sig(v, digits) for v in x]
+    return x
+
+
+def _leg(d, hbm_key=None):
+    """One leg in short form: Gsamples/s, ms per step, HBM and issue fractions, the leg's own median SM
+    clock (MHz) and any clock-event reasons seen during its timed region."""
+    if d is None:
+        return None
+    out = {"value": d.get("value"), "ms": d.get("ms_per_step", d.get("ms_per_launch"))}
+    hbm = d.get(hbm_key) if hbm_key else d.get("roofline_frac", d.get("hbm_frac"))
+    if isinstance(hbm, dict):
+        hbm = hbm.get("frac")
+    if hbm is not None:
+        out["hbm"] = hbm
+    issue = (d.get("issue") or {}).get("frac")
+    if issue is not None:
+        out["issue"] = issue
+    clock = d.get("clock") or {}
+    if clock.get("sm_mhz"):
+        out["mhz"] = clock["sm_mhz"]
+    if clock.get("reasons"):
+        out["reasons"] = clock["reasons"]
+    return out
+
+
+def compact_line(r):
+    """The printed JSON line: the contract's keys first, then every leg in short form (value, fractions,
+    own clock), then the longer records.  The full record of every leg goes to stderr (and --detail-out)."""
+    line = {k: r[k] for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "gpu_launches")}
+    rf = r["roofline"]
+    line["roofline"] = {k: rf[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+    line["roofline"]["kernel"] = "sample_pipe_kernel (cap, Philox, anisotropic, pdf)"
+    if "fwd_bwd" in r:
+        line["fwd_bwd"] = {k: _leg(v, "hbm") for k, v in r["fwd_bwd"].items()}
+    if "albedo" in r:
+        line["albedo"] = dict(_leg(r["albedo"]), cfg=list(r["albedo"]["config"].values()))
+    if "prior_sampler" in r:
+        line["prior_sampler"] = dict(_leg(r["prior_sampler"]), cap_over_prior=r["prior_sampler"]["cap_over_prior"])
+    if "extended" in r:
+        line["extended"] = {k: _leg(v) for k, v in r["extended"].items()}
+    for k in ("reflection", "pdf", "isotropic", "fit"):
+        if k in r:
+            line[k] = _leg(r[k])
+    if "backward_generic" in r:
+        line["backward_generic"] = _leg(r["backward_generic"], "hbm")
+    if "paper_protocol" in r:
+        pp = r["paper_protocol"]
+        line["paper_protocol"] = {k: _leg(pp[k]) for k in ("cap", "cap_strict", "polar")}
+        line["paper_protocol"]["cap_over_prior"] = pp["cap_over_prior"]
+    if "cpu_protocol" in r:
+        cp = r["cpu_protocol"]
+        line["cpu_protocol"] = {t: {"cap": cp[t]["cap"]["value"], "polar": cp[t]["polar"]["value"],
+                                    "cap_over_prior": cp[t]["cap_over_prior"]}
+                                for t in cp if t.startswith("threads_")}
+    line["config"] = r["config"]
+    line["clocks"] = {k: v for k, v in (r.get("clocks") or {}).items() if k != "remeasured_after"} or None
+    if r.get("clocks") and r["clocks"].get("remeasured_after"):
+        line["clocks"]["remeasured"] = True
+    if "e2e" in r:
+        e = r["e2e"]
+        line["e2e"] = {k: e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step", "ms_per_step")}
+        line["e2e"]["how"] = "zero_copy" if e.get("alternatives", {}).get("zero_copy") is not None and \
+            e["value"] == e["alternatives"]["zero_copy"]["value"] else "copy_pipeline"
+        line["e2e"]["alternatives"] = {k: (v or {}).get("value") for k, v in e.get("alternatives", {}).items()}
+    if "cpu_baseline" in r:
+        cb = r["cpu_baseline"]
+        line["cpu_baseline"] = dict(cb, sample=cb.get("sample_short", cb["sample"]))
+        line["cpu_baseline"].pop("sample_short", None)
+    line["detail"] = "full record of every leg on stderr"
+    return _sig(line)
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -431,11 +525,11 @@ def run_ours(args, rank, world):
         if world > 1:
             torch.distributed.barrier()
 
-    def timed(fn, steps, warmup, clocks=False):
+    def timed(fn, steps, warmup, clocks=True):
         for _ in range(warmup):
             fn()
         barrier()
-        sampler = ClockSampler(dev) if clocks else None
+        sampler = ClockSampler(dev) if clocks and not args.no_clocks else None
         if sampler:
             sampler.start()
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
@@ -450,7 +544,7 @@ def run_ours(args, rank, world):
         return total, per, clock
 
     steps, warm = max(args.steps, 1), max(args.warmup, 3)
-    total, per, clock = timed(step, steps, warm, clocks=not args.no_clocks)
+    total, per, clock = timed(step, steps, warm)
     first_clock = None
     if clock_rejected(clock):  # throttled or clock-locked during the timed region: measure once more
         first_clock = clock
@@ -481,36 +575,37 @@ def run_ours(args, rank, world):
     }
 
     if not args.no_prior:
-        ptotal, pper, _ = timed(lambda: step("polar"), steps, warm)
+        ptotal, pper, pclock = timed(lambda: step("polar"), steps, warm)
         pv = world * n * steps / (ptotal * 1e-3) / 1e9
         result["prior_sampler"] = {
             "value": pv, "unit": UNIT, "ms_per_step": ptotal / steps,
             "roofline_frac": BYTES_PER_SAMPLE * n / (ptotal / steps * 1e-3) / 1e9 / peak,
-            "cap_over_prior": value / pv}
+            "cap_over_prior": value / pv, "clock": pclock}
         result["gpu_launches_prior"] = steps
 
-    clk = (clock or {}).get("sm_mhz") or (clock or {}).get("sm_max_mhz") or 2070.0
     if not args.no_reflection:
-        rt, _, _ = timed(lambda: vndf.vndf_sample_reflection(
+        rt, _, rclock = timed(lambda: vndf.vndf_sample_reflection(
             d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], seed=2, counter_base=base, wo_x=outs[0],
             wo_y=outs[1], wo_z=outs[2], pdf=outs[3], weight=refl_w), steps, warm)
         rv = world * n * steps / (rt * 1e-3) / 1e9
         result["reflection"] = {"value": rv, "unit": UNIT, "ms_per_step": rt / steps,
                                 "roofline_frac": 40 * n / (rt / steps * 1e-3) / 1e9 / peak,
                                 "bytes_per_sample": 40, "note": "wo, pdf and F G2/G1 weight per sample (App. A)",
-                                "issue": issue_roofline("reflection", n, rt / steps, clk)}
+                                "issue": issue_roofline("reflection", n, rt / steps, rclock),
+                                "clock": rclock}
         result["gpu_launches_reflection"] = steps
 
     if not args.no_extended:
-        result["extended"] = extended_legs(vndf, dev, base, n, outs, timed, steps, warm, world, peak, clk)
+        result["extended"] = extended_legs(vndf, dev, base, n, outs, timed, steps, warm, world, peak)
         result["gpu_launches_extended"] = 2 * steps
 
     if not args.no_pdf:
-        pt, _, _ = timed(lambda: vndf.vndf_pdf(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], outs[0],
-                                               outs[1], outs[2], pdf=outs[3]), steps, warm)
+        pt, _, pdclock = timed(lambda: vndf.vndf_pdf(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"],
+                                                     outs[0], outs[1], outs[2], pdf=outs[3]), steps, warm)
         result["pdf"] = {"value": world * n * steps / (pt * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": pt / steps,
                          "bytes_per_sample": 36, "roofline_frac": 36 * n / (pt / steps * 1e-3) / 1e9 / peak,
-                         "note": "vndf_pdf at the headline's sampled normals (wi, alpha, wm in; pdf out)"}
+                         "note": "vndf_pdf at the headline's sampled normals (wi, alpha, wm in; pdf out)",
+                         "clock": pdclock}
         result["gpu_launches_pdf"] = steps
 
     if not args.no_isotropic:
@@ -518,29 +613,32 @@ def run_ours(args, rank, world):
         result["gpu_launches_isotropic"] = result["isotropic"]["launches"]
 
     if not args.no_fwd_bwd:
-        result["fwd_bwd"] = fwd_bwd(vndf, dev, rank, world, timed, peak, args.log2n_adjoint)
-        result["fwd_bwd"]["issue"] = issue_roofline("loss_backward", 1 << args.log2n_adjoint,
-                                                    result["fwd_bwd"]["ms_per_step"], clk)
-        result["gpu_launches_fwd_bwd"] = 2 * result["fwd_bwd"]["steps"]
-        result["backward_generic"] = backward_generic(vndf, dev, rank, world, timed, peak, args.log2n_adjoint)
+        result["fwd_bwd"] = {}
+        for k in args.log2n_adjoint:
+            leg = fwd_bwd(vndf, dev, rank, world, timed, peak, k)
+            leg["issue"] = issue_roofline("loss_backward", 1 << k, leg["ms_per_step"], leg["clock"])
+            result["fwd_bwd"][f"2e{k}"] = leg
+            result[f"gpu_launches_fwd_bwd_2e{k}"] = 2 * leg["steps"]
+        result["backward_generic"] = backward_generic(vndf, dev, rank, world, timed, peak, args.log2n_adjoint[0])
         result["gpu_launches_backward_generic"] = result["backward_generic"]["steps"]
 
     if not args.no_albedo:
         result["albedo"] = albedo(vndf, dev, rank, world, timed)
         result["albedo"]["issue"] = issue_roofline("albedo", result["albedo"]["samples"],
-                                                   result["albedo"]["ms_per_step"], clk)
+                                                   result["albedo"]["ms_per_step"], result["albedo"]["clock"])
         result["gpu_launches_albedo"] = 2 * result["albedo"]["steps"]
 
     if not args.no_microbench:
         result["paper_protocol"] = microbench(vndf, dev, world, timed)
         for m, k in (("cap", "microbench_cap"), ("cap_strict", "microbench_cap_strict"), ("polar", "microbench_polar")):
-            result["paper_protocol"][m]["issue"] = issue_roofline(
-                k, result["paper_protocol"]["samples_per_step"], result["paper_protocol"][m]["ms_per_step"], clk)
+            leg = result["paper_protocol"][m]
+            leg["issue"] = issue_roofline(k, result["paper_protocol"]["samples_per_step"], leg["ms_per_step"],
+                                          leg["clock"])
 
     if not args.no_fit:
         result["fit"] = fit_leg(vndf, dev, rank, world, timed)
         result["fit"]["issue"] = issue_roofline("fit", result["fit"]["samples_per_step"],
-                                                result["fit"]["ms_per_step"], clk)
+                                                result["fit"]["ms_per_step"], result["fit"]["clock"])
         result["gpu_launches_fit"] = 2 * result["fit"]["steps"]
 
     if not args.no_e2e:
@@ -555,7 +653,12 @@ def run_ours(args, rank, world):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline()
     if rank == 0:
-        emit(result)
+        detail = json.dumps(result)
+        print(detail, file=sys.stderr, flush=True)
+        if args.detail_out:
+            with open(args.detail_out, "w") as fh:
+                fh.write(detail + "\n")
+        emit(compact_line(result))
 
 
 def fwd_bwd(vndf, dev, rank, world, timed, peak, log2n):
@@ -573,12 +676,12 @@ def fwd_bwd(vndf, dev, rank, world, timed, peak, log2n):
                                        d["c_y"], d["c_z"], seed=4, counter_base=rank * n, workspace=ws,
                                        outputs=outs)
 
-    steps = 100
-    total, per, _ = timed(step, steps, 5)
+    steps = max(20, (500 << 24) >> log2n)  # about 70 ms of timed work, so the clock record has samples
+    total, per, clock = timed(step, steps, 5)
     ms = total / steps
     del d
     return {"workload": f"adjoint_2e{log2n}", "value": world * n / (ms * 1e-3) / 1e9, "unit": UNIT,
-            "ms_per_step": ms, "steps": steps,
+            "ms_per_step": ms, "steps": steps, "clock": clock,
             "hbm": {"algorithmic_bytes": 52 * n, "achieved_gbs": 52 * n / (ms * 1e-3) / 1e9,
                     "frac": 52 * n / (ms * 1e-3) / 1e9 / peak},
             "kernels": "loss_backward_pipe_kernel (+ loss_backward_kernel for a ragged last chunk) + sum_partials_kernel (programmatic dependent launch)"}
@@ -599,12 +702,12 @@ def backward_generic(vndf, dev, rank, world, timed, peak, log2n):
         vndf.vndf_sample_backward(*(d[k] for k in keys), seed=4, counter_base=rank * n, g_wm_x=d["c_x"],
                                   g_wm_y=d["c_y"], g_wm_z=d["c_z"], g_pdf=gp)
 
-    steps = 100
-    total, _, _ = timed(step, steps, 5)
+    steps = max(20, (500 << 24) >> log2n)
+    total, _, clock = timed(step, steps, 5)
     ms = total / steps
     del d
     return {"workload": f"adjoint_2e{log2n}", "value": world * n / (ms * 1e-3) / 1e9, "unit": UNIT,
-            "ms_per_step": ms, "steps": steps, "bytes_per_sample": 56,
+            "ms_per_step": ms, "steps": steps, "bytes_per_sample": 56, "clock": clock,
             "hbm": {"algorithmic_bytes": 56 * n, "achieved_gbs": 56 * n / (ms * 1e-3) / 1e9,
                     "frac": 56 * n / (ms * 1e-3) / 1e9 / peak},
             "kernels": "backward_pipe_kernel (vector path), backward_scalar_kernel for a ragged tail"}
@@ -629,11 +732,12 @@ def albedo(vndf, dev, rank, world, timed):
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=side):
         vndf.vndf_albedo_batched(*args, stream_id=rank * nq, E=E, workspace=ws)
-    steps = 100
-    tot, per, _ = timed(graph.replay, steps, 5)
+    steps = 500
+    tot, per, clock = timed(graph.replay, steps, 5)
     ms = tot / steps
     return {"workload": "albedo_grid_4096", "queries": nq, "samples": total,
             "value": world * total / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "clock": clock,
             "config": {"warps_per_cta": best[0], "groups_per_item": best[1], "ctas_per_sm": best[2]},
             "captured": "cuda graph (prologue + persistent kernel)",
             "E_range": [float(E.min().item()), float(E.max().item())]}
@@ -661,13 +765,13 @@ def isotropic_leg(vndf, dev, rank, world, timed, peak):
     with torch.cuda.graph(graph, stream=side):
         for _ in range(reps):
             call()
-    tot, _, _ = timed(graph.replay, steps, 3)
+    tot, _, clock = timed(graph.replay, steps, 3)
     ms = tot / (steps * reps)
     return {"workload": "isotropic_2e20", "samples": n, "value": world * n / (ms * 1e-3) / 1e9, "unit": UNIT,
             "ms_per_launch": ms, "launches": steps * reps, "bytes_per_sample": 40,
             "achieved_gbs": 40 * n / (ms * 1e-3) / 1e9, "hbm_frac": 40 * n / (ms * 1e-3) / 1e9 / peak,
             "note": "L2-resident (42 MB < 129 MB L2): the HBM fraction can exceed 1; launch-bound at this size",
-            "captured": f"cuda graph of {reps} launches"}
+            "captured": f"cuda graph of {reps} launches", "clock": clock}
 
 
 def microbench(vndf, dev, world, timed):
@@ -678,9 +782,11 @@ def microbench(vndf, dev, world, timed):
     out = {"protocol": "64 samples per lane, inputs in registers, 16 B written per lane", "lanes": lanes,
            "samples_per_step": lanes * spl}
     for key, method, precise in (("cap", "cap", False), ("cap_strict", "cap", True), ("polar", "polar", False)):
-        tot, per, _ = timed(lambda: vndf.vndf_microbench(lanes, spl, method, 1, sums=sums, precise=precise), 20, 3)
-        ms = tot / 20
-        out[key] = {"value": world * lanes * spl / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms}
+        tot, per, clock = timed(lambda: vndf.vndf_microbench(lanes, spl, method, 1, sums=sums, precise=precise),
+                                60, 3)
+        ms = tot / 60
+        out[key] = {"value": world * lanes * spl / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+                    "clock": clock}
     out["cap"]["note"] = "plain FP32 cap sampler: the prior sampler's accuracy class (tails above 4e-6 rad ~1e-5)"
     out["cap_strict"]["note"] = "as vndf_sample: ill-conditioned samples redone in double-float, all within 4e-6 rad"
     out["cap_over_prior"] = out["cap"]["value"] / out["polar"]["value"]
@@ -689,7 +795,7 @@ def microbench(vndf, dev, world, timed):
     return out
 
 
-def extended_legs(vndf, dev, base, n, outs, timed, steps, warm, world, peak, clk):
+def extended_legs(vndf, dev, base, n, outs, timed, steps, warm, world, peak):
     """The extended domain (2^28 sphere workload, half below the horizon) and the stand-alone
     hemisphere sampler (2^28 directions of mixed length), HBM-resident, Philox in-kernel."""
     import torch
@@ -697,24 +803,25 @@ def extended_legs(vndf, dev, base, n, outs, timed, steps, warm, world, peak, clk
     import workloads
     res = {}
     d = workloads.sphere_stream(n=n, device=dev)
-    t, _, _ = timed(lambda: vndf.vndf_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], seed=2,
-                                             counter_base=base, method="cap_extended", wm_x=outs[0], wm_y=outs[1],
-                                             wm_z=outs[2], pdf=outs[3]), steps, warm)
+    t, _, clock = timed(lambda: vndf.vndf_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"],
+                                                 seed=2, counter_base=base, method="cap_extended", wm_x=outs[0],
+                                                 wm_y=outs[1], wm_z=outs[2], pdf=outs[3]), steps, warm)
     ms = t / steps
     res["sphere"] = {"workload": "sphere_stream_2e28", "value": world * n / (ms * 1e-3) / 1e9, "unit": UNIT,
                      "ms_per_step": ms, "bytes_per_sample": BYTES_PER_SAMPLE,
                      "roofline_frac": BYTES_PER_SAMPLE * n / (ms * 1e-3) / 1e9 / peak,
-                     "method": "spherical_cap_extended", "issue": issue_roofline("extended", n, ms, clk)}
+                     "method": "spherical_cap_extended", "issue": issue_roofline("extended", n, ms, clock),
+                     "clock": clock}
     del d
     h = workloads.hemisphere_stream(n=n, device=dev)
-    t, _, _ = timed(lambda: vndf.vndf_sample_hemisphere(h["wi_x"], h["wi_y"], h["wi_z"], seed=2, counter_base=base,
-                                                        wm_x=outs[0], wm_y=outs[1], wm_z=outs[2], pdf=outs[3]),
-                    steps, warm)
+    t, _, clock = timed(lambda: vndf.vndf_sample_hemisphere(h["wi_x"], h["wi_y"], h["wi_z"], seed=2,
+                                                            counter_base=base, wm_x=outs[0], wm_y=outs[1],
+                                                            wm_z=outs[2], pdf=outs[3]), steps, warm)
     ms = t / steps
     res["hemisphere"] = {"workload": "hemisphere_stream_2e28", "value": world * n / (ms * 1e-3) / 1e9,
                          "unit": UNIT, "ms_per_step": ms, "bytes_per_sample": 28,
                          "roofline_frac": 28 * n / (ms * 1e-3) / 1e9 / peak,
-                         "issue": issue_roofline("hemisphere", n, ms, clk)}
+                         "issue": issue_roofline("hemisphere", n, ms, clock), "clock": clock}
     del h
     torch.cuda.empty_cache()
     return res
@@ -779,14 +886,15 @@ def fit_leg(vndf, dev, rank, world, timed):
     graph.replay()
     torch.cuda.synchronize(dev)
     first = float(loss.item())
-    steps = 20
-    tot, per, _ = timed(graph.replay, steps, 2)
+    steps = 100
+    tot, per, clock = timed(graph.replay, steps, 2)
     ms = tot / steps
     samples = nt * 1024
     return {"workload": "roughness_map_256x256", "texels": nt, "samples_per_step": samples,
             "value": world * samples / (ms * 1e-3) / 1e9, "unit": "Gsamples/s (fwd + adjoint per sample)",
             "ms_per_step": ms, "steps": steps, "captured": "cuda graph (fit kernel + loss/step kernel)",
-            "loss_first": first, "loss_last": float(loss.item()), "steps_done": int(st["step"].item())}
+            "loss_first": first, "loss_last": float(loss.item()), "steps_done": int(st["step"].item()),
+            "clock": clock}
 
 
 def e2e(vndf, d, n, base, dev, stream, steps, warm, barrier, world):

@@ -49,3 +49,63 @@ def test_roofline_denominators(monkeypatch, tmp_path):
     (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6787.6, "sm_max_mhz": 2032}')
     assert bench.hbm_peak() == (6787.6, "measured")
     assert bench.max_sm_clock_mhz() == 2032.0
+
+
+def _full_record():
+    """A record with every leg bench.py times, with full-precision floats, shaped as run_ours builds it."""
+    x = 1.0 / 3.0
+    clock = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 28, "source": "nvml 5 ms"}
+    issue = {"bound": "alu", "achieved": 28.4 + x, "peak": 40.27 + x, "frac": 0.7 + x / 10}
+    leg = lambda **kw: dict({"value": 100 + x, "ms_per_step": 1 + x, "roofline_frac": 0.9 + x / 10,  # noqa: E731
+                             "issue": issue, "clock": clock}, **kw)
+    fb = lambda: dict(leg(), hbm={"frac": 0.89 + x / 100}, steps=500)  # noqa: E731
+    r = {k: v for k, v in zip(("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                               "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "gpu_launches"),
+                              (bench.METRIC, 185.7 + x, "Gsamples/s", 1, 20, 5, 1.44 + x, True, "weak", None, "f32",
+                               "synthetic", 20))}
+    r["roofline"] = {"bound": "hbm", "achieved": 6688 + x, "peak": 6792.1, "unit": "GB/s", "frac": 0.98 + x / 100,
+                     "traffic": 9532143042.56, "peak_kind": "measured copy bandwidth", "algorithmic_bytes": 1}
+    r["config"] = {"workload": bench.WORKLOAD, "samples_per_gpu": 1 << 28, "method": "spherical_cap",
+                   "rng": "philox4x32-10 in-kernel", "alpha": "log-uniform [1e-3, 1] x, y independent",
+                   "cos_theta_i": "uniform [1e-4, 1]",
+                   "l2": "inputs larger than L2 (9.66 GB touched per step); no flush",
+                   "parallelism": "index-range shards x1"}
+    r["clocks"] = clock
+    r["fwd_bwd"] = {"2e24": fb(), "2e26": fb()}
+    r["backward_generic"] = fb()
+    r["albedo"] = dict(leg(), config={"warps_per_cta": 16, "groups_per_item": 2, "ctas_per_sm": 4})
+    r["prior_sampler"] = dict(leg(), cap_over_prior=1.06 + x)
+    r["extended"] = {"sphere": leg(), "hemisphere": leg()}
+    for k in ("reflection", "pdf", "isotropic", "fit"):
+        r[k] = leg()
+    r["paper_protocol"] = {"cap": leg(), "cap_strict": leg(), "polar": leg(), "cap_over_prior": 1.33 + x}
+    row = {"cap": {"value": 0.2 + x}, "cap_strict": {"value": 0.2 + x}, "polar": {"value": 0.14 + x},
+           "cap_over_prior": 1.5 + x}
+    r["cpu_protocol"] = {"threads_1": row, "threads_16": row, "paper_reference": "p"}
+    e = {"value": 9.3 + x, "unit": "Gsamples/s", "h2d_bytes_per_step": 20 << 28, "d2h_bytes_per_step": 16 << 28,
+         "ms_per_step": 28.9 + x, "pipeline": "zero copy"}
+    r["e2e"] = dict(e, alternatives={"copy_pipeline": dict(e, value=7.4 + x), "zero_copy": e})
+    r["cpu_baseline"] = {"value": 0.0497 + x / 1000, "unit": "Gsamples/s", "cores": 16, "kind": "oracle",
+                         "sample": "x" * 300, "sample_short": "1424x2^20 samples, FP64 numpy oracle, 16 processes"}
+    return r
+
+
+def test_printed_line_is_short_and_complete():
+    """The printed line must fit in the few KB of stdout a driver keeps: every leg in short form (value,
+    fractions, own clock), the long records only on stderr."""
+    import json
+    line = bench.compact_line(_full_record())
+    text = json.dumps(line, separators=(",", ":"))
+    assert len(text) < 2800, len(text)
+    keys = list(line)
+    assert keys[:13] == ["metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                         "scaling", "vs_baseline", "dtype", "data", "gpu_launches"]
+    for k in ("roofline", "fwd_bwd", "albedo", "prior_sampler", "extended", "config", "clocks", "e2e",
+              "cpu_baseline"):
+        assert k in line, k
+    assert set(line["fwd_bwd"]) == {"2e24", "2e26"}
+    for leg in (line["fwd_bwd"]["2e24"], line["albedo"], line["extended"]["sphere"]):
+        assert leg["issue"] is not None and leg["mhz"] == 2070.0
+    assert line["fwd_bwd"]["2e26"]["hbm"] is not None
+    assert line["e2e"]["how"] == "zero_copy" and line["e2e"]["h2d_bytes_per_step"] == 20 << 28
+    assert line["cpu_baseline"]["sample"].startswith("1424x2^20")
