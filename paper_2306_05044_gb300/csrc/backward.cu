@@ -14,13 +14,18 @@
 #include "staging.cuh"
 #include "vndf_adjoint.cuh"
 
-// Staged fused kernel: 1 = full chunks go through loss_backward_pipe_kernel; its grid
-// (at most this many waves of 8 CTAs per SM) and resident CTAs per SM.
+// Staged kernels: 1 = full chunks go through backward_pipe_kernel / loss_backward_pipe_kernel; their
+// grids (at most this many waves of 8 CTAs per SM, of which 3 are resident) and resident CTAs per SM.
+// Measured on GB300 (fused at 2^24 / 2^26 samples, generic at 2^24): 1 wave 141.7 / 539.1 / 146.2 us,
+// 4 waves 141.7 / 529.5 / 139.4, 8 waves 147.7 / 525.5 / 137.6, 16 waves 158.0 / 528.0 / 145.6.
 #ifndef VNDF_BWD_STAGED
 #define VNDF_BWD_STAGED 1
 #endif
 #ifndef VNDF_BWD_WAVES
-#define VNDF_BWD_WAVES 1
+#define VNDF_BWD_WAVES 8
+#endif
+#ifndef VNDF_LOSS_WAVES
+#define VNDF_LOSS_WAVES 4
 #endif
 #ifndef VNDF_BWD_MIN_BLOCKS
 #define VNDF_BWD_MIN_BLOCKS 3
@@ -537,7 +542,7 @@ int launch_loss(const BwdArgs& a, int64_t n, bool vec, const LossWorkspace& w, f
       constexpr size_t smem = size_t(2) * loss_streams_in<PHILOX, ISO>() * kBwdBlock * 16;
       if (!ensure_dynamic_smem<loss_backward_pipe_kernel<PHILOX, ISO>>(smem)) return VNDF_ERR_CUDA;
       loss_backward_pipe_kernel<PHILOX, ISO>
-          <<<grid_for(full * kBwdBlock, kBwdBlock, 8, VNDF_BWD_WAVES), kBwdBlock, smem, s>>>(a, full, partials,
+          <<<grid_for(full * kBwdBlock, kBwdBlock, 8, VNDF_LOSS_WAVES), kBwdBlock, smem, s>>>(a, full, partials,
                                                                                           w.counter);
     }
     if (full < chunks)

@@ -64,7 +64,8 @@ template <bool PHILOX, bool PDF>
 __global__ void __launch_bounds__(kHemiBlock, 3) hemi_pipe_kernel(HemiArgs a, int64_t n4) {
   constexpr int NS = hemi_streams_in<PHILOX>();
   extern __shared__ float4 smem_h[];  // [2][NS][kHemiBlock], then one rescue queue per warp
-  RescueQueue& rq = reinterpret_cast<RescueQueue*>(smem_h + 2 * NS * kHemiBlock)[threadIdx.x >> 5];
+  RescueQueue* const queues = reinterpret_cast<RescueQueue*>(smem_h + 2 * NS * kHemiBlock);
+  RescueQueue& rq = queues[threadIdx.x >> 5];
   int pending = 0;  // warp-uniform
   const int64_t stride = int64_t(gridDim.x) * kHemiBlock;
   const int64_t q0 = int64_t(blockIdx.x) * kHemiBlock + threadIdx.x;
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(kHemiBlock, 3) hemi_pipe_kernel(HemiArgs a, in
       rescue_drain(rq, pending, false, redo);
     }
   }
-  if constexpr (kBatched) rescue_drain(rq, pending, true, redo);
+  if constexpr (kBatched) rescue_drain_cta(queues, pending, redo);
   cp_async_wait<0>();
 }
 

@@ -133,7 +133,8 @@ template <bool PHILOX, bool ISO>
 __global__ void __launch_bounds__(kReflBlock, 3) reflect_pipe_kernel(ReflArgs a, int64_t n4) {
   constexpr int NS = streams_in<PHILOX, ISO>();
   extern __shared__ float4 smem_r[];  // [2][NS][kReflBlock], then one rescue queue per warp
-  RescueQueue& rq = reinterpret_cast<RescueQueue*>(smem_r + 2 * NS * kReflBlock)[threadIdx.x >> 5];
+  RescueQueue* const queues = reinterpret_cast<RescueQueue*>(smem_r + 2 * NS * kReflBlock);
+  RescueQueue& rq = queues[threadIdx.x >> 5];
   int pending = 0;  // warp-uniform
   const int64_t stride = int64_t(gridDim.x) * kReflBlock;
   const int64_t q0 = int64_t(blockIdx.x) * kReflBlock + threadIdx.x;
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(kReflBlock, 3) reflect_pipe_kernel(ReflArgs a,
       rescue_drain(rq, pending, false, redo);
     }
   }
-  if constexpr (kBatched) rescue_drain(rq, pending, true, redo);
+  if constexpr (kBatched) rescue_drain_cta(queues, pending, redo);
   cp_async_wait<0>();
 }
 

@@ -14,6 +14,13 @@
 // Both calls are warp-collective: every lane of the warp makes them, with a
 // warp-uniform `count`.  __syncwarp orders this warp's earlier global stores
 // (the FP32 group results) before the recomputed ones.
+//
+// What is left in the queues when the warps finish (fewer than 32 per warp;
+// a warp of a 2^28-sample launch flags only a few to a few dozen samples in
+// all) is recomputed by the whole CTA at once (rescue_drain_cta): one
+// barrier, then every thread takes entries of the concatenated queues in turn,
+// so a handful of flagged samples no longer costs each warp a full pass of the
+// slow path with one or two lanes active.
 #pragma once
 #include <cstdint>
 
@@ -51,6 +58,27 @@ __device__ __forceinline__ void rescue_drain(RescueQueue& q, int& count, bool al
     if (lane < take) fn(q.idx[base + lane]);
     count = base;
     __syncwarp();
+  }
+}
+
+// CTA-collective (every thread of the block, after its warp's last push):
+// the entries left in all warps' queues, recomputed by all threads of the
+// block.  `queues` is the block's array of per-warp queues, `count` this
+// warp's (warp-uniform) number of waiting entries.  The barrier orders every
+// warp's earlier global stores before the recomputed ones, which another warp
+// of the block may now write.
+template <class Fn>
+__device__ __forceinline__ void rescue_drain_cta(RescueQueue* queues, int count, Fn&& fn) {
+  __shared__ int s_count[32];
+  const int warps = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) s_count[threadIdx.x >> 5] = count;
+  __syncthreads();
+  int total = 0;
+  for (int w = 0; w < warps; ++w) total += s_count[w];
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    int w = 0, k = e;
+    while (k >= s_count[w]) k -= s_count[w++];  // ends: e < total
+    fn(queues[w].idx[k]);
   }
 }
 

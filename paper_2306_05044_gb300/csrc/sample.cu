@@ -20,8 +20,12 @@
 #ifndef VNDF_SAMPLE_MIN_BLOCKS
 #define VNDF_SAMPLE_MIN_BLOCKS 3
 #endif
+// Grid of the staged streaming kernel: at most this many waves of 8 CTAs per SM (3 are resident).
+// Measured at 2^28 samples on GB300: 4 waves 1444 us (cap) / 1624 us (extended domain), 8 waves
+// 1428 / 1589, 16 waves 1414 / 1526, 32 waves 1452 / 1533.  Smaller CTAs' shares balance the tail
+// and let each CTA's final recomputation of its ill-conditioned samples overlap other CTAs' streaming.
 #ifndef VNDF_SAMPLE_WAVES
-#define VNDF_SAMPLE_WAVES 4
+#define VNDF_SAMPLE_WAVES 16
 #endif
 #ifndef VNDF_SAMPLE_PREFETCH
 #define VNDF_SAMPLE_PREFETCH 1
@@ -141,7 +145,8 @@ __global__ void __launch_bounds__(kSampleBlock, VNDF_SAMPLE_MIN_BLOCKS) sample_p
   constexpr int S = VNDF_SAMPLE_STAGES;
   constexpr int NS = streams_in<PHILOX, ISO>();
   extern __shared__ float4 smem[];  // [S][NS][kSampleBlock], then one rescue queue per warp
-  RescueQueue& rq = reinterpret_cast<RescueQueue*>(smem + S * NS * kSampleBlock)[threadIdx.x >> 5];
+  RescueQueue* const queues = reinterpret_cast<RescueQueue*>(smem + S * NS * kSampleBlock);
+  RescueQueue& rq = queues[threadIdx.x >> 5];
   int pending = 0;  // warp-uniform
   const int64_t stride = int64_t(gridDim.x) * kSampleBlock;
   const int64_t q0 = int64_t(blockIdx.x) * kSampleBlock + threadIdx.x;
@@ -229,7 +234,7 @@ __global__ void __launch_bounds__(kSampleBlock, VNDF_SAMPLE_MIN_BLOCKS) sample_p
       }
     }
   }
-  if constexpr (kBatched) rescue_drain(rq, pending, true, redo);
+  if constexpr (kBatched) rescue_drain_cta(queues, pending, redo);
   cp_async_wait<0>();
 }
 
