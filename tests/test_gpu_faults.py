@@ -85,3 +85,28 @@ def test_every_binding_raises_the_injected_status(v, monkeypatch):
         if name != "vndf_albedo_autotune":
             call()
     torch.cuda.synchronize()
+
+
+def test_in_place_calls_are_rejected_before_any_work(v):
+    """An output aliasing an input would let the batched double-float recomputation reread overwritten inputs;
+    every entry point refuses such a call with VNDF_ERR_ARG and leaves the buffers untouched."""
+    n = (1 << 16) + 3
+    d = workloads.sphere_stream(n=n, seed=15, device=DEV)  # below-horizon inputs: many flagged samples
+    wi = [d["wi_x"], d["wi_y"], d["wi_z"]]
+    al = [d["alpha_x"], d["alpha_y"]]
+    keep = [t.clone() for t in wi + al]
+    calls = [
+        lambda: v.vndf_sample(*wi, *al, seed=1, method="cap_extended", wm_x=wi[0]),
+        lambda: v.vndf_sample(*wi, *al, seed=1, pdf=al[1]),
+        lambda: v.vndf_sample_reflection(*wi, *al, seed=1, wo_z=wi[2]),
+        lambda: v.vndf_sample_hemisphere(*wi, seed=1, wm_y=wi[1]),
+        lambda: v.vndf_pdf(*wi, *al, wi[0], wi[1], wi[2], pdf=wi[2]),
+        lambda: v.vndf_sample_backward(*wi, *al, seed=1, g_pdf=al[0], outputs=(None, None, None, al[0], None)),
+    ]
+    for call in calls:
+        with pytest.raises(v.VndfError) as err:
+            call()
+        assert err.value.status == -7
+    torch.cuda.synchronize()
+    for a, b in zip(wi + al, keep):
+        assert torch.equal(a, b)
