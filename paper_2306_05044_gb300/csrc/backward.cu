@@ -58,6 +58,8 @@ __device__ __forceinline__ void store4(float* p, int64_t e, const float (&d)[4])
 
 template <bool PHILOX, bool ISO, bool EXT>
 __global__ void __launch_bounds__(kBwdBlock, 3) backward_vec4_kernel(BwdArgs a, int64_t n4) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t stride = int64_t(gridDim.x) * kBwdBlock;
   for (int64_t q = int64_t(blockIdx.x) * kBwdBlock + threadIdx.x; q < n4; q += stride) {
     const int64_t e = 4 * q;
@@ -110,6 +112,8 @@ __global__ void __launch_bounds__(kBwdBlock, 3) backward_vec4_kernel(BwdArgs a, 
 
 template <bool PHILOX, bool ISO, bool EXT>
 __global__ void __launch_bounds__(kBwdBlock) backward_scalar_kernel(BwdArgs a, int64_t begin, int64_t n) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t stride = int64_t(gridDim.x) * kBwdBlock;
   for (int64_t e = begin + int64_t(blockIdx.x) * kBwdBlock + threadIdx.x; e < n; e += stride) {
     const float ax = a.ax[e];
@@ -166,6 +170,8 @@ __device__ __forceinline__ void bwd_stage(const BwdArgs& a, int64_t e, float4* s
 
 template <bool PHILOX, bool ISO, bool EXT>
 __global__ void __launch_bounds__(kBwdBlock, VNDF_BWD_MIN_BLOCKS) backward_pipe_kernel(BwdArgs a, int64_t n4) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int kFixed = bwd_fixed_streams<PHILOX, ISO>();
   const bool has_g = a.gmx != nullptr, has_p = a.gp != nullptr;
   const int ns = kFixed + (has_g ? 3 : 0) + (has_p ? 1 : 0);
@@ -258,6 +264,7 @@ template <bool PHILOX, bool ISO, bool VEC>
 __global__ void __launch_bounds__(kBwdBlock, 3) loss_backward_kernel(BwdArgs a, int64_t n, int64_t ch0,
                                                                   int64_t chunks, float* partials,
                                                                   unsigned* sum_counter) {
+  pdl_wait();
   if (sum_counter && blockIdx.x == 0 && threadIdx.x == 0) *sum_counter = 0u;  // read by sum_partials_kernel
 #if VNDF_LOSS_PDL
   asm volatile("griddepcontrol.launch_dependents;");  // the sum kernel may be scheduled; it waits for us
@@ -383,6 +390,7 @@ template <bool PHILOX, bool ISO>
 __global__ void __launch_bounds__(kBwdBlock, VNDF_BWD_MIN_BLOCKS) loss_backward_pipe_kernel(BwdArgs a, int64_t chunks,
                                                                        float* partials, unsigned* sum_counter) {
   constexpr int NS = loss_streams_in<PHILOX, ISO>();
+  pdl_wait();
   if (blockIdx.x == 0 && threadIdx.x == 0) *sum_counter = 0u;  // read by sum_partials_kernel
 #if VNDF_LOSS_PDL
   asm volatile("griddepcontrol.launch_dependents;");  // the sum kernel may be scheduled; it waits for us
@@ -502,16 +510,18 @@ int launch_backward(const BwdArgs& a, int64_t n, bool vec, cudaStream_t s) {
       constexpr size_t smem_max = size_t(2) * (bwd_fixed_streams<PHILOX, ISO>() + 4) * kBwdBlock * 16;
       if (!ensure_dynamic_smem<backward_pipe_kernel<PHILOX, ISO, EXT>>(smem_max)) return VNDF_ERR_CUDA;
       const int ns = bwd_fixed_streams<PHILOX, ISO>() + (a.gmx ? 3 : 0) + (a.gp ? 1 : 0);
-      backward_pipe_kernel<PHILOX, ISO, EXT><<<grid_for(n4, kBwdBlock, 8, VNDF_BWD_WAVES), kBwdBlock,
-                                               size_t(2) * ns * kBwdBlock * 16, s>>>(a, n4);
-    } else {
-      backward_vec4_kernel<PHILOX, ISO, EXT><<<grid_for(n4, kBwdBlock, 8, 32), kBwdBlock, 0, s>>>(a, n4);
+      if (!launch_pdl(backward_pipe_kernel<PHILOX, ISO, EXT>, grid_for(n4, kBwdBlock, 8, VNDF_BWD_WAVES), kBwdBlock,
+                      size_t(2) * ns * kBwdBlock * 16, s, a, n4))
+        return VNDF_ERR_CUDA;
+    } else if (!launch_pdl(backward_vec4_kernel<PHILOX, ISO, EXT>, grid_for(n4, kBwdBlock, 8, 32), kBwdBlock, 0, s,
+                           a, n4)) {
+      return VNDF_ERR_CUDA;
     }
     done = 4 * n4;
   }
-  if (done < n)
-    backward_scalar_kernel<PHILOX, ISO, EXT>
-        <<<grid_for(n - done, kBwdBlock, 8, 32), kBwdBlock, 0, s>>>(a, done, n);
+  if (done < n && !launch_pdl(backward_scalar_kernel<PHILOX, ISO, EXT>, grid_for(n - done, kBwdBlock, 8, 32),
+                              kBwdBlock, 0, s, a, done, n))
+    return VNDF_ERR_CUDA;
   return launch_status();
 }
 
@@ -541,18 +551,19 @@ int launch_loss(const BwdArgs& a, int64_t n, bool vec, const LossWorkspace& w, f
     {
       constexpr size_t smem = size_t(2) * loss_streams_in<PHILOX, ISO>() * kBwdBlock * 16;
       if (!ensure_dynamic_smem<loss_backward_pipe_kernel<PHILOX, ISO>>(smem)) return VNDF_ERR_CUDA;
-      loss_backward_pipe_kernel<PHILOX, ISO>
-          <<<grid_for(full * kBwdBlock, kBwdBlock, 8, VNDF_LOSS_WAVES), kBwdBlock, smem, s>>>(a, full, partials,
-                                                                                          w.counter);
+      if (!launch_pdl(loss_backward_pipe_kernel<PHILOX, ISO>, grid_for(full * kBwdBlock, kBwdBlock, 8, VNDF_LOSS_WAVES),
+                      kBwdBlock, smem, s, a, full, partials, w.counter))
+        return VNDF_ERR_CUDA;
     }
     if (full < chunks)
       loss_backward_kernel<PHILOX, ISO, true><<<1, kBwdBlock, 0, s>>>(a, n, full, chunks, partials, nullptr);
   } else {
     const unsigned grid = grid_for(chunks * kBwdBlock, kBwdBlock, 8, 16);
-    if (vec)
-      loss_backward_kernel<PHILOX, ISO, true><<<grid, kBwdBlock, 0, s>>>(a, n, 0, chunks, partials, w.counter);
-    else
-      loss_backward_kernel<PHILOX, ISO, false><<<grid, kBwdBlock, 0, s>>>(a, n, 0, chunks, partials, w.counter);
+    const bool ok = vec ? launch_pdl(loss_backward_kernel<PHILOX, ISO, true>, grid, kBwdBlock, 0, s, a, n, 0, chunks,
+                                     partials, w.counter)
+                        : launch_pdl(loss_backward_kernel<PHILOX, ISO, false>, grid, kBwdBlock, 0, s, a, n, 0, chunks,
+                                     partials, w.counter);
+    if (!ok) return VNDF_ERR_CUDA;
   }
   const int64_t nseg = loss_segments(groups);
   const unsigned sgrid = static_cast<unsigned>(nseg < 65535 ? nseg : 65535);

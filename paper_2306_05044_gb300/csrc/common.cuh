@@ -88,6 +88,36 @@ inline unsigned grid_for(int64_t work, int block, int per_sm, int waves) {
 
 inline int launch_status() { return cudaGetLastError() == cudaSuccess ? VNDF_OK : VNDF_ERR_CUDA; }
 
+// Programmatic dependent launch.  A kernel launched with launch_pdl may be scheduled before the work ahead
+// of it in the stream has finished: its CTAs become resident once every CTA of the kernel ahead has
+// signalled pdl_trigger (or exited), and each first waits in hardware (pdl_wait) until that kernel has
+// completed and its writes are visible.  Every kernel launched this way calls pdl_wait before it reads an
+// input or writes an output, so results are those of an ordinary launch: what it hides is the launch
+// latency between back-to-back calls (measured: 2^22 samples 32.2 -> 30.2 us per call).  While the stream
+// is being captured into a CUDA graph the launch is an ordinary one: inside a graph the early-resident
+// CTAs measured slower (2^20 samples 7.1 -> 9.9 us per replayed launch).  After an ordinary launch
+// pdl_wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline bool launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &capture) != cudaSuccess) return false;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = capture == cudaStreamCaptureStatusNone ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...) == cudaSuccess;
+}
+
 // Streaming (evict-first) 128-bit loads and stores: every byte is touched once.
 __device__ __forceinline__ float4 ld_stream(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
 __device__ __forceinline__ void st_stream(float* p, float4 v) { __stcs(reinterpret_cast<float4*>(p), v); }

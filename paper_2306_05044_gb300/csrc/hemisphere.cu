@@ -62,6 +62,8 @@ __device__ __forceinline__ float4 hemi_one(float wx, float wy, float wz, float u
 // samples are queued per warp and redone 32 at a time (rescue.cuh).
 template <bool PHILOX, bool PDF>
 __global__ void __launch_bounds__(kHemiBlock, 3) hemi_pipe_kernel(HemiArgs a, int64_t n4) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int NS = hemi_streams_in<PHILOX>();
   extern __shared__ float4 smem_h[];  // [2][NS][kHemiBlock], then one rescue queue per warp
   RescueQueue* const queues = reinterpret_cast<RescueQueue*>(smem_h + 2 * NS * kHemiBlock);
@@ -147,6 +149,8 @@ __global__ void __launch_bounds__(kHemiBlock, 3) hemi_pipe_kernel(HemiArgs a, in
 
 template <bool PHILOX, bool PDF>
 __global__ void __launch_bounds__(kHemiBlock) hemi_scalar_kernel(HemiArgs a, int64_t begin, int64_t n) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t stride = int64_t(gridDim.x) * kHemiBlock;
   for (int64_t e = begin + int64_t(blockIdx.x) * kHemiBlock + threadIdx.x; e < n; e += stride) {
     float u1, u2;
@@ -172,11 +176,15 @@ int launch_hemi(const HemiArgs& a, int64_t n, bool vec, cudaStream_t s) {
     constexpr size_t smem =
         size_t(2) * hemi_streams_in<PHILOX>() * kHemiBlock * 16 + (kHemiBlock / 32) * sizeof(RescueQueue);
     if (!ensure_dynamic_smem<hemi_pipe_kernel<PHILOX, PDF>>(smem)) return VNDF_ERR_CUDA;
-    hemi_pipe_kernel<PHILOX, PDF><<<grid_for(n4, kHemiBlock, 8, VNDF_SAMPLE_WAVES), kHemiBlock, smem, s>>>(a, n4);
+    if (!launch_pdl(hemi_pipe_kernel<PHILOX, PDF>, grid_for(n4, kHemiBlock, 8, VNDF_SAMPLE_WAVES), kHemiBlock, smem, s,
+                    a, n4))
+      return VNDF_ERR_CUDA;
     done = 4 * n4;
   }
   if (done < n)
-    hemi_scalar_kernel<PHILOX, PDF><<<grid_for(n - done, kHemiBlock, 8, 32), kHemiBlock, 0, s>>>(a, done, n);
+    if (!launch_pdl(hemi_scalar_kernel<PHILOX, PDF>, grid_for(n - done, kHemiBlock, 8, 32), kHemiBlock, 0, s, a, done,
+                    n))
+      return VNDF_ERR_CUDA;
   return launch_status();
 }
 

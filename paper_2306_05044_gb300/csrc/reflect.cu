@@ -131,6 +131,8 @@ __device__ __forceinline__ void refl_stage(const ReflArgs& a, int64_t e, float4*
 // ill-conditioned samples are queued per warp and redone 32 at a time (rescue.cuh).
 template <bool PHILOX, bool ISO>
 __global__ void __launch_bounds__(kReflBlock, 3) reflect_pipe_kernel(ReflArgs a, int64_t n4) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int NS = streams_in<PHILOX, ISO>();
   extern __shared__ float4 smem_r[];  // [2][NS][kReflBlock], then one rescue queue per warp
   RescueQueue* const queues = reinterpret_cast<RescueQueue*>(smem_r + 2 * NS * kReflBlock);
@@ -215,6 +217,8 @@ __global__ void __launch_bounds__(kReflBlock, 3) reflect_pipe_kernel(ReflArgs a,
 
 template <bool PHILOX, bool ISO>
 __global__ void __launch_bounds__(kReflBlock) reflect_scalar_kernel(ReflArgs a, int64_t begin, int64_t n) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t stride = int64_t(gridDim.x) * kReflBlock;
   for (int64_t e = begin + int64_t(blockIdx.x) * kReflBlock + threadIdx.x; e < n; e += stride) {
     const float ax = a.ax[e];
@@ -245,11 +249,15 @@ int launch_reflect(const ReflArgs& a, int64_t n, bool vec, cudaStream_t s) {
     constexpr size_t smem =
         size_t(2) * streams_in<PHILOX, ISO>() * kReflBlock * 16 + (kReflBlock / 32) * sizeof(RescueQueue);
     if (!ensure_dynamic_smem<reflect_pipe_kernel<PHILOX, ISO>>(smem)) return VNDF_ERR_CUDA;
-    reflect_pipe_kernel<PHILOX, ISO><<<grid_for(n4, kReflBlock, 8, VNDF_SAMPLE_WAVES), kReflBlock, smem, s>>>(a, n4);
+    if (!launch_pdl(reflect_pipe_kernel<PHILOX, ISO>, grid_for(n4, kReflBlock, 8, VNDF_SAMPLE_WAVES), kReflBlock, smem,
+                    s, a, n4))
+      return VNDF_ERR_CUDA;
     done = 4 * n4;
   }
   if (done < n)
-    reflect_scalar_kernel<PHILOX, ISO><<<grid_for(n - done, kReflBlock, 8, 32), kReflBlock, 0, s>>>(a, done, n);
+    if (!launch_pdl(reflect_scalar_kernel<PHILOX, ISO>, grid_for(n - done, kReflBlock, 8, 32), kReflBlock, 0, s, a,
+                    done, n))
+      return VNDF_ERR_CUDA;
   return launch_status();
 }
 

@@ -36,6 +36,10 @@
 #ifndef VNDF_SAMPLE_MIN_ITERS
 #define VNDF_SAMPLE_MIN_ITERS 4
 #endif
+// 1 = vndf_sample's kernels are programmatic dependent launches (common.cuh: launch_pdl).
+#ifndef VNDF_SAMPLE_PDL
+#define VNDF_SAMPLE_PDL 1
+#endif
 // Ill-conditioned samples: 1 = queued per warp and redone 32 at a time
 // (rescue.cuh); 0 = each redone in place by its own lane.
 #ifndef VNDF_RESCUE_BATCHED
@@ -142,6 +146,8 @@ __device__ __forceinline__ void stage_group(const SampleArgs& a, int64_t e, floa
 
 template <int METHOD, bool PHILOX, bool ISO, bool PDF>
 __global__ void __launch_bounds__(kSampleBlock, VNDF_SAMPLE_MIN_BLOCKS) sample_pipe_kernel(SampleArgs a, int64_t n4) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int S = VNDF_SAMPLE_STAGES;
   constexpr int NS = streams_in<PHILOX, ISO>();
   extern __shared__ float4 smem[];  // [S][NS][kSampleBlock], then one rescue queue per warp
@@ -240,6 +246,8 @@ __global__ void __launch_bounds__(kSampleBlock, VNDF_SAMPLE_MIN_BLOCKS) sample_p
 
 template <int METHOD, bool PHILOX, bool ISO, bool PDF>
 __global__ void __launch_bounds__(kBlock) sample_scalar_kernel(SampleArgs a, int64_t begin, int64_t n) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t stride = int64_t(gridDim.x) * kBlock;
   for (int64_t e = begin + int64_t(blockIdx.x) * kBlock + threadIdx.x; e < n; e += stride) {
     const float ax = a.ax[e];
@@ -288,16 +296,27 @@ int launch_sample(const SampleArgs& a, int64_t n, bool vec, cudaStream_t s) {
         constexpr size_t smem = size_t(VNDF_SAMPLE_STAGES) * streams_in<PHILOX, ISO>() * kSampleBlock * 16 +
                                 (kSampleBlock / 32) * sizeof(RescueQueue);
         if (!ensure_dynamic_smem<sample_pipe_kernel<METHOD, PHILOX, ISO, PDF>>(smem)) return VNDF_ERR_CUDA;
-        sample_pipe_kernel<METHOD, PHILOX, ISO, PDF><<<grid, kSampleBlock, smem, s>>>(a, n4);
+        if (VNDF_SAMPLE_PDL) {
+          if (!launch_pdl(sample_pipe_kernel<METHOD, PHILOX, ISO, PDF>, grid, kSampleBlock, smem, s, a, n4))
+            return VNDF_ERR_CUDA;
+        } else {
+          sample_pipe_kernel<METHOD, PHILOX, ISO, PDF><<<grid, kSampleBlock, smem, s>>>(a, n4);
+        }
       } else {
         sample_vec4_kernel<METHOD, PHILOX, ISO, PDF><<<grid, kSampleBlock, 0, s>>>(a, n4);
       }
       done = 4 * n4;
     }
   }
-  if (done < n)
-    sample_scalar_kernel<METHOD, PHILOX, ISO, PDF>
-        <<<grid_for(n - done, kBlock, 8, 32), kBlock, 0, s>>>(a, done, n);
+  if (done < n) {
+    const unsigned grid = grid_for(n - done, kBlock, 8, 32);
+    if (VNDF_SAMPLE_PDL) {
+      if (!launch_pdl(sample_scalar_kernel<METHOD, PHILOX, ISO, PDF>, grid, kBlock, 0, s, a, done, n))
+        return VNDF_ERR_CUDA;
+    } else {
+      sample_scalar_kernel<METHOD, PHILOX, ISO, PDF><<<grid, kBlock, 0, s>>>(a, done, n);
+    }
+  }
   return launch_status();
 }
 
@@ -320,6 +339,8 @@ int dispatch_rng(const SampleArgs& a, int64_t n, bool vec, cudaStream_t s) {
 
 // ---------------------------------------------------------------- uniforms
 __global__ void __launch_bounds__(kBlock) rng_vec4_kernel(Rng r, float* u1, float* u2, int64_t n4) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t stride = int64_t(gridDim.x) * kBlock;
   for (int64_t q = int64_t(blockIdx.x) * kBlock + threadIdx.x; q < n4; q += stride) {
     float U1[4], U2[4];
@@ -331,6 +352,8 @@ __global__ void __launch_bounds__(kBlock) rng_vec4_kernel(Rng r, float* u1, floa
 
 __global__ void __launch_bounds__(kBlock) rng_scalar_kernel(Rng r, float* u1, float* u2, int64_t begin,
                                                             int64_t n) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t stride = int64_t(gridDim.x) * kBlock;
   for (int64_t e = begin + int64_t(blockIdx.x) * kBlock + threadIdx.x; e < n; e += stride) {
     float a, b;
@@ -346,6 +369,8 @@ __global__ void __launch_bounds__(kBlock) pdf_vec4_kernel(const float* wx, const
                                                           const float* ax, const float* ay, const float* mx,
                                                           const float* my, const float* mz, float* pdf,
                                                           int64_t n4) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t stride = int64_t(gridDim.x) * kBlock;
   for (int64_t q = int64_t(blockIdx.x) * kBlock + threadIdx.x; q < n4; q += stride) {
     const int64_t e = 4 * q;
@@ -373,6 +398,8 @@ __global__ void __launch_bounds__(kBlock) pdf_scalar_kernel(const float* wx, con
                                                             const float* ax, const float* ay, const float* mx,
                                                             const float* my, const float* mz, float* pdf,
                                                             int64_t begin, int64_t n) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t stride = int64_t(gridDim.x) * kBlock;
   for (int64_t e = begin + int64_t(blockIdx.x) * kBlock + threadIdx.x; e < n; e += stride) {
     const float a = ax[e];
@@ -386,13 +413,14 @@ int launch_pdf(int64_t n, const float* wx, const float* wy, const float* wz, con
   int64_t done = 0;
   if (vec && n / 4 > 0) {
     const int64_t n4 = n / 4;
-    pdf_vec4_kernel<ISO, EXT>
-        <<<grid_for(n4, kBlock, 8, 32), kBlock, 0, s>>>(wx, wy, wz, ax, ay, mx, my, mz, pdf, n4);
+    if (!launch_pdl(pdf_vec4_kernel<ISO, EXT>, grid_for(n4, kBlock, 8, 32), kBlock, 0, s, wx, wy, wz, ax, ay, mx, my,
+                    mz, pdf, n4))
+      return VNDF_ERR_CUDA;
     done = 4 * n4;
   }
-  if (done < n)
-    pdf_scalar_kernel<ISO, EXT><<<grid_for(n - done, kBlock, 8, 32), kBlock, 0, s>>>(wx, wy, wz, ax, ay, mx, my,
-                                                                                       mz, pdf, done, n);
+  if (done < n && !launch_pdl(pdf_scalar_kernel<ISO, EXT>, grid_for(n - done, kBlock, 8, 32), kBlock, 0, s, wx, wy,
+                              wz, ax, ay, mx, my, mz, pdf, done, n))
+    return VNDF_ERR_CUDA;
   return launch_status();
 }
 
@@ -413,10 +441,11 @@ extern "C" int vndf_rng_uniform(int64_t n, uint64_t seed, uint64_t counter_base,
   int64_t done = 0;
   if (all_aligned16(u1, u2) && n / 4 > 0) {
     const int64_t n4 = n / 4;
-    rng_vec4_kernel<<<grid_for(n4, kBlock, 8, 32), kBlock, 0, s>>>(r, u1, u2, n4);
+    if (!launch_pdl(rng_vec4_kernel, grid_for(n4, kBlock, 8, 32), kBlock, 0, s, r, u1, u2, n4)) return VNDF_ERR_CUDA;
     done = 4 * n4;
   }
-  if (done < n) rng_scalar_kernel<<<grid_for(n - done, kBlock, 8, 32), kBlock, 0, s>>>(r, u1, u2, done, n);
+  if (done < n && !launch_pdl(rng_scalar_kernel, grid_for(n - done, kBlock, 8, 32), kBlock, 0, s, r, u1, u2, done, n))
+    return VNDF_ERR_CUDA;
   return launch_status();
 }
 
