@@ -422,6 +422,8 @@ def compact_line(r):
     rf = r["roofline"]
     line["roofline"] = {k: rf[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
     line["roofline"]["kernel"] = "sample_pipe_kernel (cap, Philox, anisotropic, pdf)"
+    if r.get("rescued_frac") is not None:
+        line["rescued"] = r["rescued_frac"]
     if "fwd_bwd" in r:
         line["fwd_bwd"] = {k: _leg(v, "hbm") for k, v in r["fwd_bwd"].items()}
     if "albedo" in r:
@@ -430,6 +432,8 @@ def compact_line(r):
         line["prior_sampler"] = dict(_leg(r["prior_sampler"]), cap_over_prior=r["prior_sampler"]["cap_over_prior"])
     if "extended" in r:
         line["extended"] = {k: _leg(v) for k, v in r["extended"].items()}
+        if "rescued_frac" in r["extended"].get("sphere", {}):
+            line["extended"]["sphere"]["rescued"] = r["extended"]["sphere"]["rescued_frac"]
     for k in ("reflection", "pdf", "isotropic", "fit"):
         if k in r:
             line[k] = _leg(r[k])
@@ -553,6 +557,10 @@ def run_ours(args, rank, world):
             clock = dict(clock, remeasured_after=first_clock)
     value = world * n * steps / (total * 1e-3) / 1e9
     avg_ms = total / steps
+    # share of the samples recomputed in double-float (untimed diagnostic, same arguments as the step)
+    rescued = vndf.vndf_rescue_count(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], seed=2,
+                                     counter_base=base)
+    rescued_frac = float(rescued.item()) / n
 
     peak, peak_kind = hbm_peak()
     achieved = BYTES_PER_SAMPLE * n / (avg_ms * 1e-3) / 1e9
@@ -570,6 +578,7 @@ def run_ours(args, rank, world):
                      "traffic": (tps * n) if tps is not None else None,
                      "algorithmic_bytes": BYTES_PER_SAMPLE * n, "kernel": "sample_pipe_kernel<cap, philox, aniso, pdf>"},
         "gpu_launches": steps,
+        "rescued_frac": rescued_frac,
         "clocks": clock,
         "per_step_ms": {"min": min(per), "median": statistics.median(per), "max": max(per)},
     }
@@ -807,7 +816,10 @@ def extended_legs(vndf, dev, base, n, outs, timed, steps, warm, world, peak):
                                                  seed=2, counter_base=base, method="cap_extended", wm_x=outs[0],
                                                  wm_y=outs[1], wm_z=outs[2], pdf=outs[3]), steps, warm)
     ms = t / steps
+    rescued = vndf.vndf_rescue_count(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], seed=2,
+                                     counter_base=base, method="cap_extended")
     res["sphere"] = {"workload": "sphere_stream_2e28", "value": world * n / (ms * 1e-3) / 1e9, "unit": UNIT,
+                     "rescued_frac": float(rescued.item()) / n,
                      "ms_per_step": ms, "bytes_per_sample": BYTES_PER_SAMPLE,
                      "roofline_frac": BYTES_PER_SAMPLE * n / (ms * 1e-3) / 1e9 / peak,
                      "method": "spherical_cap_extended", "issue": issue_roofline("extended", n, ms, clock),

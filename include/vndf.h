@@ -149,6 +149,28 @@ int vndf_sample(int64_t n,
                 void *cuda_stream);
 
 /*
+ * vndf_rescue_count -- how many of these samples vndf_sample recomputes in
+ * double-float.  The FP32 half vector h = c + i of the cap sampler (Sec. 3.3)
+ * sums O(1) terms whose rounding the unstretch divides by |v|; vndf_sample
+ * flags the samples whose condition number exceeds 24 and recomputes them
+ * (the paper's method is exact; this is how the library meets its accuracy
+ * bound in FP32).  This diagnostic runs the same per-sample function and
+ * condition test on the same arguments as vndf_sample, discards the results
+ * and writes the number of flagged samples, so a caller can see how often the
+ * slow path runs on its inputs.  Arguments as for vndf_sample, plus:
+ *   count    output, one unsigned 64-bit integer in device memory (8-byte
+ *            aligned), set to 0 and then to the count; 0 for the prior sampler,
+ *            which has no such path.
+ * Returns VNDF_OK or a negative VNDF_ERR_* code (NULL, SIZE, ALIGN, METHOD, ARG, CUDA).
+ */
+int vndf_rescue_count(int64_t n,
+                      const float *wi_x, const float *wi_y, const float *wi_z,
+                      const float *alpha_x, const float *alpha_y,
+                      const float *u1, const float *u2,
+                      uint64_t seed, uint64_t counter_base, uint32_t stream_id,
+                      int method, unsigned long long *count, void *cuda_stream);
+
+/*
  * vndf_sample_reflection -- sample a reflected direction from the GGX
  * microfacet BRDF through the spherical-cap VNDF sampler (App. A, "Importance
  * Sampling Using the GGX VNDF"): wm is drawn exactly as vndf_sample draws it

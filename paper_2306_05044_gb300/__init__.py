@@ -37,6 +37,7 @@ SIGNATURES = {
     "vndf_rng_uniform": (ctypes.c_int, [_I64, _U64, _U64, _U32, _P, _P, _P]),
     "vndf_sample": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _U64, _U64, _U32, ctypes.c_int,
                                    _P, _P, _P, _P, _P]),
+    "vndf_rescue_count": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _U64, _U64, _U32, ctypes.c_int, _P, _P]),
     "vndf_pdf": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "vndf_pdf_extended": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "vndf_sample_hemisphere": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _U64, _U64, _U32, _P, _P, _P, _P, _P]),
@@ -191,6 +192,22 @@ def vndf_sample(wi_x, wi_y, wi_z, alpha_x, alpha_y=None, u1=None, u2=None, seed=
         _stream(stream, wi_x.device))
     _check("vndf_sample", st)
     return wm_x, wm_y, wm_z, pdf
+
+
+def vndf_rescue_count(wi_x, wi_y, wi_z, alpha_x, alpha_y=None, u1=None, u2=None, seed=0, counter_base=0,
+                      stream_id=0, method="cap", count=None, n=None, stream=None):
+    """Number of samples vndf_sample recomputes in double-float for these arguments (a device int64 tensor of
+    one element, or ``count`` if given); see vndf_rescue_count in include/vndf.h."""
+    n = wi_x.numel() if n is None else int(n)
+    if count is None:
+        count = torch.empty(1, dtype=torch.int64, device=wi_x.device)
+    st = load().vndf_rescue_count(
+        n, _ptr(wi_x, "wi_x"), _ptr(wi_y, "wi_y"), _ptr(wi_z, "wi_z"), _ptr(alpha_x, "alpha_x"),
+        _ptr(alpha_y, "alpha_y"), _ptr(u1, "u1"), _ptr(u2, "u2"), int(seed) & (2**64 - 1),
+        int(counter_base) & (2**64 - 1), int(stream_id) & 0xFFFFFFFF, _method(method),
+        _ptr(count, "count", torch.int64), _stream(stream, wi_x.device))
+    _check("vndf_rescue_count", st)
+    return count
 
 
 def vndf_sample_reflection(wi_x, wi_y, wi_z, alpha_x, alpha_y=None, u1=None, u2=None, seed=0, counter_base=0,

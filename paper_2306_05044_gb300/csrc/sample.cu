@@ -337,6 +337,48 @@ int dispatch_rng(const SampleArgs& a, int64_t n, bool vec, cudaStream_t s) {
   return a.u1 ? dispatch_iso<METHOD, false>(a, n, vec, s) : dispatch_iso<METHOD, true>(a, n, vec, s);
 }
 
+// ---------------------------------------------------------------- recomputation count
+// How many samples vndf_sample recomputes in double-float for these inputs: the same per-sample
+// function and condition test, the results discarded, the flags counted (ballot per warp, one atomic).
+template <int METHOD, bool PHILOX, bool ISO>
+__global__ void __launch_bounds__(kBlock) rescue_count_kernel(SampleArgs a, int64_t n, unsigned long long* count) {
+  pdl_trigger();
+  pdl_wait();
+  const int64_t stride = int64_t(gridDim.x) * kBlock;
+  unsigned long long mine = 0;
+  for (int64_t e = int64_t(blockIdx.x) * kBlock + threadIdx.x; e < n; e += stride) {
+    const float ax = a.ax[e];
+    const float ay = ISO ? ax : a.ay[e];
+    float u1, u2;
+    if constexpr (PHILOX) {
+      uniforms1(a.rng, uint64_t(e), u1, u2);
+    } else {
+      u1 = a.u1[e];
+      u2 = a.u2[e];
+    }
+    float mx, my, mz, p;
+    mine += sample_one<METHOD, false, true>(a.wx[e], a.wy[e], a.wz[e], ax, ay, u1, u2, mx, my, mz, p) ? 1u : 0u;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(count, mine);
+}
+
+template <int METHOD>
+int launch_rescue_count(const SampleArgs& a, int64_t n, unsigned long long* count, cudaStream_t s) {
+  const unsigned grid = grid_for(n, kBlock, 8, 8);
+  if (a.u1) {
+    return (a.ay ? launch_pdl(rescue_count_kernel<METHOD, false, false>, grid, kBlock, 0, s, a, n, count)
+                 : launch_pdl(rescue_count_kernel<METHOD, false, true>, grid, kBlock, 0, s, a, n, count))
+               ? launch_status()
+               : VNDF_ERR_CUDA;
+  }
+  return (a.ay ? launch_pdl(rescue_count_kernel<METHOD, true, false>, grid, kBlock, 0, s, a, n, count)
+               : launch_pdl(rescue_count_kernel<METHOD, true, true>, grid, kBlock, 0, s, a, n, count))
+             ? launch_status()
+             : VNDF_ERR_CUDA;
+}
+
 // ---------------------------------------------------------------- uniforms
 __global__ void __launch_bounds__(kBlock) rng_vec4_kernel(Rng r, float* u1, float* u2, int64_t n4) {
   pdl_trigger();
@@ -470,6 +512,32 @@ extern "C" int vndf_sample(int64_t n, const float* wi_x, const float* wi_y, cons
   if (method == VNDF_METHOD_SPHERICAL_CAP) return dispatch_rng<kMethodCap>(a, n, vec, s);
   if (method == VNDF_METHOD_POLAR_DISK) return dispatch_rng<kMethodPolar>(a, n, vec, s);
   return dispatch_rng<kMethodCapExt>(a, n, vec, s);
+}
+
+extern "C" int vndf_rescue_count(int64_t n, const float* wi_x, const float* wi_y, const float* wi_z,
+                                 const float* alpha_x, const float* alpha_y, const float* u1, const float* u2,
+                                 uint64_t seed, uint64_t counter_base, uint32_t stream_id, int method,
+                                 unsigned long long* count, void* cuda_stream) {
+  if (n < 0 || n >= kMaxN) return VNDF_ERR_SIZE;
+  if (method != VNDF_METHOD_SPHERICAL_CAP && method != VNDF_METHOD_POLAR_DISK &&
+      method != VNDF_METHOD_SPHERICAL_CAP_EXTENDED)
+    return VNDF_ERR_METHOD;
+  if (!count) return VNDF_ERR_NULL;
+  if (!aligned(count, 8)) return VNDF_ERR_ALIGN;
+  if (n > 0) {
+    if (!wi_x || !wi_y || !wi_z || !alpha_x) return VNDF_ERR_NULL;
+    if ((u1 == nullptr) != (u2 == nullptr)) return VNDF_ERR_ARG;
+    if (!all_aligned4(wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2)) return VNDF_ERR_ALIGN;
+    if (aliased({count}, {wi_x, wi_y, wi_z, alpha_x, alpha_y, u1, u2})) return VNDF_ERR_ARG;
+  }
+  if (const int f = pre_launch("vndf_rescue_count")) return f;
+  const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaMemsetAsync(count, 0, sizeof(unsigned long long), s) != cudaSuccess) return VNDF_ERR_CUDA;
+  if (n == 0 || method == VNDF_METHOD_POLAR_DISK) return VNDF_OK;  // the prior sampler has no such path
+  const SampleArgs a{wi_x,    wi_y,    wi_z,    alpha_x, alpha_y, u1, u2, nullptr, nullptr, nullptr, nullptr,
+                     make_rng(seed, counter_base, stream_id)};
+  return method == VNDF_METHOD_SPHERICAL_CAP ? launch_rescue_count<kMethodCap>(a, n, count, s)
+                                             : launch_rescue_count<kMethodCapExt>(a, n, count, s);
 }
 
 template <bool EXT>

@@ -176,6 +176,8 @@ def _entry_calls(lib):
                                                     p[9], p[10], p[11], p[12], 1e-2, 0.9, 0.999, 1e-8, 1e-3, 1.0,
                                                     1, 0, 0, p[13], p[14], ws_fit, None), True),
         "vndf_microbench": (lambda: lib.vndf_microbench(64, 8, 0, 0, 1, p[0], None), False),
+        "vndf_rescue_count": (lambda: lib.vndf_rescue_count(64, p[0], p[1], p[2], p[3], p[4], None, None, 0, 0, 0, 0,
+                                                            p[5], None), False),
     }
 
 
@@ -260,3 +262,16 @@ def test_albedo_batches_past_int32_group_indices_are_rejected(lib):
                                            None, None) == -2
     assert lib.vndf_albedo_batched_noalloc(16, p[0], p[1], p[2], p[3], None, p[4], big, 0.04, 1, 0, 0, p[5],
                                            None, None) == -2  # beyond the fixed scratch array
+
+
+def test_rescue_count_rejects_bad_arguments(lib):
+    p = _ptrs(8)
+    call = lambda n=64, wx=p[0], method=0, count=p[5], u=(None, None): lib.vndf_rescue_count(  # noqa: E731
+        n, wx, p[1], p[2], p[3], p[4], u[0], u[1], 0, 0, 0, method, count, None)
+    assert call(n=-1) == -2
+    assert call(method=9) == -4
+    assert call(count=None) == -1
+    assert call(count=p[5] + 4) == -3
+    assert call(wx=None) == -1
+    assert call(u=(p[6], None)) == -7
+    assert call(count=p[0]) == -7  # the count aliases an input

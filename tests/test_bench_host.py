@@ -75,7 +75,8 @@ def _full_record():
     r["backward_generic"] = fb()
     r["albedo"] = dict(leg(), config={"warps_per_cta": 16, "groups_per_item": 2, "ctas_per_sm": 4})
     r["prior_sampler"] = dict(leg(), cap_over_prior=1.06 + x)
-    r["extended"] = {"sphere": leg(), "hemisphere": leg()}
+    r["extended"] = {"sphere": dict(leg(), rescued_frac=4.5e-3 + x / 1e4), "hemisphere": leg()}
+    r["rescued_frac"] = 7e-4 + x / 1e5
     for k in ("reflection", "pdf", "isotropic", "fit"):
         r[k] = leg()
     r["paper_protocol"] = {"cap": leg(), "cap_strict": leg(), "polar": leg(), "cap_over_prior": 1.33 + x}
@@ -107,5 +108,6 @@ def test_printed_line_is_short_and_complete():
     for leg in (line["fwd_bwd"]["2e24"], line["albedo"], line["extended"]["sphere"]):
         assert leg["issue"] is not None and leg["mhz"] == 2070.0
     assert line["fwd_bwd"]["2e26"]["hbm"] is not None
+    assert line["rescued"] > 0 and line["extended"]["sphere"]["rescued"] > 0
     assert line["e2e"]["how"] == "zero_copy" and line["e2e"]["h2d_bytes_per_step"] == 20 << 28
     assert line["cpu_baseline"]["sample"].startswith("1424x2^20")
