@@ -251,10 +251,15 @@ __global__ void __launch_bounds__(512, 2) albedo_kernel(AlbedoArgs a) {
       float U1[kLaneSamples], U2[kLaneSamples];
 #pragma unroll
       for (int s = 0; s < kLaneSamples; s += 2) uniforms2(r, uint64_t(j0 + s), U1[s], U2[s], U1[s + 1], U2[s + 1]);
+      if ((g + 1) * kGroupSamples <= n) {  // a full group (warp-uniform): no per-sample bound
 #pragma unroll
-      for (int s = 0; s < kLaneSamples; ++s) {
-        const float w = albedo_weight(c, a.f0, U1[s], U2[s]);
-        acc += j0 + s < n ? w : 0.f;
+        for (int s = 0; s < kLaneSamples; ++s) acc += albedo_weight(c, a.f0, U1[s], U2[s]);
+      } else {
+#pragma unroll
+        for (int s = 0; s < kLaneSamples; ++s) {
+          const float w = albedo_weight(c, a.f0, U1[s], U2[s]);
+          acc += j0 + s < n ? w : 0.f;
+        }
       }
       acc = warp_tree(acc);
       if (lane == 0) a.partials[size_t(q) * a.gmax + g] = acc;
