@@ -22,10 +22,11 @@
 #endif
 // Grid of the staged streaming kernel: at most this many waves of 8 CTAs per SM (3 are resident).
 // Measured at 2^28 samples on GB300: 4 waves 1444 us (cap) / 1624 us (extended domain), 8 waves
-// 1428 / 1589, 16 waves 1414 / 1526, 32 waves 1452 / 1533.  Smaller CTAs' shares balance the tail
-// and let each CTA's final recomputation of its ill-conditioned samples overlap other CTAs' streaming.
+// 1428 / 1589, 16 waves 1411 / 1524, 20 waves 1409 / 1499, 24 waves 1420 / 1504, 32 waves 1452 / 1533.
+// Smaller CTA shares balance the tail and let each CTA's final recomputation of its ill-conditioned
+// samples overlap other CTAs' streaming.
 #ifndef VNDF_SAMPLE_WAVES
-#define VNDF_SAMPLE_WAVES 16
+#define VNDF_SAMPLE_WAVES 20
 #endif
 #ifndef VNDF_SAMPLE_PREFETCH
 #define VNDF_SAMPLE_PREFETCH 1
