@@ -421,6 +421,30 @@ int vndf_albedo_autotune(int32_t n_queries,
                          float *E, void *workspace, size_t workspace_bytes,
                          int32_t *best_config, float *best_ms, void *cuda_stream);
 
+/*
+ * vndf_albedo_set_config -- set the launch configuration that
+ * vndf_albedo_batched (and its no-allocation variant) use on the current
+ * device when called with config = NULL, as vndf_albedo_autotune does after
+ * timing; NULL restores the default.  Lets a caller reuse a configuration it
+ * tuned earlier (for instance one stored on disk by the Python binding's
+ * autotune cache) without timing again.  The configuration only chooses the
+ * launch shape: E is the same for every configuration.
+ *   config   three int32 on the host (warps per CTA 1-16, groups per item
+ *            1-256, CTAs per SM 1-32), or NULL.
+ * Returns VNDF_OK, VNDF_ERR_ARG (a value out of range), VNDF_ERR_SIZE (a
+ * device ordinal above 63) or VNDF_ERR_CUDA (no current device).
+ */
+int vndf_albedo_set_config(const int32_t *config);
+
+/*
+ * vndf_albedo_get_config -- the configuration a config = NULL call of
+ * vndf_albedo_batched uses on the current device, written to three int32 on
+ * the host.  Returns 1 when it was set (by vndf_albedo_autotune or
+ * vndf_albedo_set_config), 0 when it is the default, VNDF_ERR_NULL or
+ * VNDF_ERR_CUDA.
+ */
+int vndf_albedo_get_config(int32_t *config);
+
 /* Device workspace (bytes) for vndf_fit_step: one float per texel. */
 size_t vndf_fit_workspace_bytes(int32_t n_texels);
 

@@ -55,6 +55,8 @@ SIGNATURES = {
                                            _P, _P]),
     "vndf_albedo_autotune": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, _P, _I32, _F, _U64, _U64, _U32, _P, _P, _SZ,
                                             _P, _P, _P]),
+    "vndf_albedo_set_config": (ctypes.c_int, [_P]),
+    "vndf_albedo_get_config": (ctypes.c_int, [_P]),
     "vndf_fit_workspace_bytes": (_SZ, [_I32]),
     "vndf_fit_step": (ctypes.c_int, [_I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _F, _F,
                                      _F, _F, _F, _F, _U64, _U64, _U32, _P, _P, _SZ, _P]),
@@ -358,9 +360,76 @@ def vndf_albedo_batched(wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples, max_sampl
     return E
 
 
+def vndf_albedo_set_config(config):
+    """Set (or, with None, reset) the launch configuration config=None albedo calls use on the current device."""
+    cfg = None if config is None else (ctypes.c_int32 * 3)(*[int(c) for c in config])
+    _check("vndf_albedo_set_config", load().vndf_albedo_set_config(cfg))
+
+
+def vndf_albedo_get_config():
+    """(configuration a config=None albedo call uses on the current device, whether it was set or tuned)."""
+    cfg = (ctypes.c_int32 * 3)()
+    st = load().vndf_albedo_get_config(cfg)
+    if st < 0:
+        raise VndfError("vndf_albedo_get_config", st)
+    return tuple(cfg), st == 1
+
+
+def tune_cache_key(device_name, sm_count, n_queries, max_samples_per_query):
+    """Key of an albedo autotune result: the device (name and multiprocessor count) and the batch's size class
+    (query count rounded up to a power of two, and the per-query bound)."""
+    bucket = 1 << max(0, int(n_queries) - 1).bit_length()
+    return f"{device_name}|sm{int(sm_count)}|nq{bucket}|max{int(max_samples_per_query)}"
+
+
+def tune_cache_lookup(path, key):
+    """The cached ((warps, groups, ctas), ms) for key, or None (missing or unreadable file, unknown key)."""
+    import json
+    try:
+        with open(path) as fh:
+            entry = json.load(fh).get(key)
+    except (OSError, ValueError, AttributeError):
+        return None
+    if not entry:
+        return None
+    return tuple(int(c) for c in entry["config"]), float(entry["ms"])
+
+
+def tune_cache_store(path, key, config, ms):
+    """Add or replace key in the JSON cache file, written to a temporary file and renamed into place."""
+    import json
+    try:
+        with open(path) as fh:
+            data = json.load(fh)
+        if not isinstance(data, dict):
+            data = {}
+    except (OSError, ValueError):
+        data = {}
+    data[key] = {"config": [int(c) for c in config], "ms": float(ms)}
+    d = os.path.dirname(os.path.abspath(path))
+    os.makedirs(d, exist_ok=True)
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "w") as fh:
+        json.dump(data, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
 def vndf_albedo_autotune(wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples, max_samples_per_query=65536, f0=0.04,
-                         seed=3, counter_base=0, stream_id=0, E=None, workspace=None, stream=None):
-    """Pick and remember the fastest albedo launch configuration; returns ((warps, groups, ctas), ms)."""
+                         seed=3, counter_base=0, stream_id=0, E=None, workspace=None, stream=None, cache=None):
+    """Pick and remember the fastest albedo launch configuration; returns ((warps, groups, ctas), ms).
+
+    With ``cache`` (a JSON file path), a configuration stored there for this device and batch size class is
+    set without timing (vndf_albedo_set_config); otherwise the configurations are timed and the result is
+    stored for the next process.  E is not computed on a cache hit."""
+    key = None
+    if cache is not None:
+        props = torch.cuda.get_device_properties(wi_x.device)
+        key = tune_cache_key(props.name, props.multi_processor_count, wi_x.numel(), max_samples_per_query)
+        hit = tune_cache_lookup(cache, key)
+        if hit is not None:
+            with torch.cuda.device(wi_x.device):
+                vndf_albedo_set_config(hit[0])
+            return hit
     E, workspace, args = _albedo_common(wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples, max_samples_per_query, E,
                                         workspace)
     best = (ctypes.c_int32 * 3)()
@@ -370,6 +439,8 @@ def vndf_albedo_autotune(wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples, max_samp
                                      _ptr(workspace, "workspace", torch.uint8), int(workspace.numel()), best,
                                      ctypes.byref(ms), _stream(stream, wi_x.device))
     _check("vndf_albedo_autotune", st)
+    if key is not None:
+        tune_cache_store(cache, key, tuple(best), ms.value)
     return tuple(best), ms.value
 
 

@@ -284,12 +284,14 @@ std::mutex g_tune_mutex;
 AlbedoConfig g_tuned[64];
 bool g_has_tuned[64] = {false};
 
+constexpr AlbedoConfig kDefaultConfig{8, 1, 8};
+
 AlbedoConfig current_config() {
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   if (dev >= 0 && dev < 64 && g_has_tuned[dev]) return g_tuned[dev];
-  return AlbedoConfig{8, 1, 8};
+  return kDefaultConfig;
 }
 
 int launch_albedo(AlbedoArgs a, const AlbedoConfig& c, cudaStream_t s) {
@@ -484,6 +486,37 @@ extern "C" int vndf_albedo_autotune(int32_t n_queries, const float* wi_x, const 
   }
   if (best_ms) *best_ms = best_t;
   return VNDF_OK;
+}
+
+extern "C" int vndf_albedo_set_config(const int32_t* config) {
+  if (config && !config_ok(AlbedoConfig{config[0], config[1], config[2]})) return VNDF_ERR_ARG;
+  if (const int f = injected_fault("vndf_albedo_set_config", false)) return f;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return VNDF_ERR_CUDA;
+  if (dev >= 64) return config ? VNDF_ERR_SIZE : VNDF_OK;  // configurations are kept for devices 0..63
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_has_tuned[dev] = config != nullptr;
+  if (config) g_tuned[dev] = AlbedoConfig{config[0], config[1], config[2]};
+  return VNDF_OK;
+}
+
+extern "C" int vndf_albedo_get_config(int32_t* config) {
+  if (!config) return VNDF_ERR_NULL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return VNDF_ERR_CUDA;
+  bool set = false;
+  AlbedoConfig c = kDefaultConfig;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    if (dev < 64 && g_has_tuned[dev]) {
+      c = g_tuned[dev];
+      set = true;
+    }
+  }
+  config[0] = c.block_warps;
+  config[1] = c.groups_per_item;
+  config[2] = c.ctas_per_sm;
+  return set ? 1 : 0;
 }
 
 // ---------------------------------------------------------------- no-allocation variant

@@ -178,6 +178,7 @@ def _entry_calls(lib):
         "vndf_microbench": (lambda: lib.vndf_microbench(64, 8, 0, 0, 1, p[0], None), False),
         "vndf_rescue_count": (lambda: lib.vndf_rescue_count(64, p[0], p[1], p[2], p[3], p[4], None, None, 0, 0, 0, 0,
                                                             p[5], None), False),
+        "vndf_albedo_set_config": (lambda: lib.vndf_albedo_set_config(cfg), False),
     }
 
 

@@ -103,6 +103,30 @@ def test_albedo_autotune_keeps_results(v, grid):
     assert torch.equal(v.vndf_albedo_batched(*args), ref)
 
 
+def test_albedo_autotune_cache_sets_the_stored_configuration(v, grid, tmp_path):
+    """A configuration tuned once is stored on disk and, in a later run, set without timing; E does not depend
+    on it."""
+    args = (grid["wi_x"], grid["wi_y"], grid["wi_z"], grid["alpha_x"], None, grid["n_samples"])
+    cache = str(tmp_path / "albedo_tune.json")
+    ref = v.vndf_albedo_batched(*args, config=(8, 1, 8))
+    try:
+        tuned, ms = v.vndf_albedo_autotune(*args, cache=cache)
+        assert v.vndf_albedo_get_config() == (tuned, True)
+        v.vndf_albedo_set_config(None)  # as in a fresh process
+        assert v.vndf_albedo_get_config() == ((8, 1, 8), False)
+        hit = v.vndf_albedo_autotune(*args, cache=cache)
+        assert hit == (tuned, ms)
+        assert v.vndf_albedo_get_config() == (tuned, True)
+        assert torch.equal(v.vndf_albedo_batched(*args), ref)
+        v.vndf_albedo_set_config((4, 4, 16))
+        assert v.vndf_albedo_get_config() == ((4, 4, 16), True)
+        assert torch.equal(v.vndf_albedo_batched(*args), ref)
+        with pytest.raises(v.VndfError):
+            v.vndf_albedo_set_config((0, 1, 1))
+    finally:
+        v.vndf_albedo_set_config(None)
+
+
 def test_albedo_edge_counts(v):
     """Counts 0, 1, 255, 257, above the bound and negative; anisotropic alphas; odd counter base."""
     counts = [0, 1, 255, 257, 3000, 70000, -4, 65536]

@@ -58,6 +58,7 @@ def _bindings(v):
         "vndf_fit_step": (lambda: v.vndf_fit_step(st, *fit_in, loss=torch.empty(1, device=DEV)), True),
         "vndf_microbench": (lambda: v.vndf_microbench(1024, 8, device=DEV), False),
         "vndf_rescue_count": (lambda: v.vndf_rescue_count(*wi, *al, seed=1), False),
+        "vndf_albedo_set_config": (lambda: v.vndf_albedo_set_config(None), False),
     }
 
 
