@@ -68,7 +68,19 @@ def parse_args():
                    help="sizes of the fused forward+adjoint leg (2^k samples; the first is the workload's)")
     p.add_argument("--detail-out", default=None,
                    help="also write the full record (every leg with every field) to this file")
-    return p.parse_args()
+    p.add_argument("--config", type=int, choices=(1, 2, 3, 4, 5), default=None,
+                   help="time the headline and only the legs of one workload: 1 isotropic 2^20, 2 anisotropic "
+                        "stream (prior sampler, reflection, density, end to end), 3 albedo grid, 4 forward+adjoint, "
+                        "5 roughness-map fitting")
+    args = p.parse_args()
+    if args.config is not None:
+        keep = {1: {"isotropic"}, 2: {"prior", "reflection", "pdf", "e2e"}, 3: {"albedo"}, 4: {"fwd_bwd"},
+                5: {"fit"}}[args.config]
+        for leg in ("prior", "reflection", "pdf", "e2e", "isotropic", "albedo", "fwd_bwd", "fit", "extended",
+                    "microbench", "cpu_protocol", "cpu_baseline"):
+            if leg not in keep:
+                setattr(args, "no_" + leg, True)
+    return args
 
 
 # ----------------------------------------------------------------------------- helpers

@@ -111,3 +111,13 @@ def test_printed_line_is_short_and_complete():
     assert line["rescued"] > 0 and line["extended"]["sphere"]["rescued"] > 0
     assert line["e2e"]["how"] == "zero_copy" and line["e2e"]["h2d_bytes_per_step"] == 20 << 28
     assert line["cpu_baseline"]["sample"].startswith("1424x2^20")
+
+
+def test_config_option_keeps_only_that_workloads_legs(monkeypatch):
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--config", "4"])
+    a = bench.parse_args()
+    assert not a.no_fwd_bwd
+    assert a.no_albedo and a.no_fit and a.no_prior and a.no_e2e and a.no_cpu_baseline and a.no_extended
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = bench.parse_args()
+    assert not (a.no_fwd_bwd or a.no_albedo or a.no_fit or a.no_prior or a.no_e2e or a.no_cpu_baseline)
