@@ -180,3 +180,57 @@ def test_cpu_precise_on_wide_inputs(v, kind):
     if ext:
         st.update(parity.compare_cap_mp(np.stack(out[:3]), out[3], u1, u2, wi, d["alpha_x"], d["alpha_y"], limit=150))
     print("cpu wide", kind, st)
+
+
+_FORK_INPUTS = {}
+
+
+def _child_samples(q):
+    # only the library runs in the child (torch's own thread pools are not fork-safe)
+    import paper_2306_05044_gb300 as lib
+    d, u = _FORK_INPUTS["d"], _FORK_INPUTS["u"]
+    out = lib.vndf_cpu_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], u, u, threads=4)
+    q.put(float(np.sum(out[3], dtype=np.float64)))
+
+
+def test_cpu_worker_pool_after_fork(v):
+    """The host worker threads live in the process that made them; a forked child starts its own on first use
+    (it must not wait on workers that fork did not copy) and gets the parent's results."""
+    import multiprocessing as mp
+    d = _inputs(1 << 16, seed=21)
+    u = np.full(1 << 16, 0.25, np.float32)
+    ref = v.vndf_cpu_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], u, u, threads=4)
+    _FORK_INPUTS.update(d=d, u=u)
+    ctx = mp.get_context("fork")
+    q = ctx.Queue()
+    p = ctx.Process(target=_child_samples, args=(q,))
+    p.start()
+    p.join(60)
+    if p.is_alive():
+        p.kill()
+        pytest.fail("the forked child did not finish")
+    assert p.exitcode == 0
+    assert q.get(timeout=10) == float(np.sum(ref[3], dtype=np.float64))
+
+
+def test_cpu_concurrent_callers(v):
+    """Calls from several host threads at once are served one after the other, each with its own results."""
+    import threading
+    inputs = [_inputs(50000, seed=30 + k) for k in range(4)]
+    u = np.linspace(0, 1 - 2.0 ** -24, 50000).astype(np.float32)
+    want = [v.vndf_cpu_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], u, u[::-1].copy(),
+                              threads=3) for d in inputs]
+    got = [None] * 4
+
+    def call(k):
+        d = inputs[k]
+        got[k] = v.vndf_cpu_sample(d["wi_x"], d["wi_y"], d["wi_z"], d["alpha_x"], d["alpha_y"], u, u[::-1].copy(),
+                                   threads=3)
+    ts = [threading.Thread(target=call, args=(k,)) for k in range(4)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    for a, b in zip(got, want):
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)
