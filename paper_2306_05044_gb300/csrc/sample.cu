@@ -22,11 +22,15 @@
 #endif
 // Grid of the staged streaming kernel: at most this many waves of 8 CTAs per SM (3 are resident).
 // Measured at 2^28 samples on GB300: 4 waves 1444 us (cap) / 1624 us (extended domain), 8 waves
-// 1428 / 1589, 16 waves 1411 / 1524, 20 waves 1409 / 1499, 24 waves 1420 / 1504, 32 waves 1452 / 1533.
+// 1428 / 1589, 16 waves 1411 / 1524, 20 waves 1409 / 1499, 24 waves 1420 / 1504, 32 waves 1452 / 1533
+// (launches alone); in the bench loop the cap sampler timed 1410-1414 us at 16 waves and 1421 at 20.
 // Smaller CTA shares balance the tail and let each CTA's final recomputation of its ill-conditioned
-// samples overlap other CTAs' streaming.
+// samples overlap other CTAs' streaming; the extended domain, with six times more of them, gains most.
 #ifndef VNDF_SAMPLE_WAVES
-#define VNDF_SAMPLE_WAVES 20
+#define VNDF_SAMPLE_WAVES 16
+#endif
+#ifndef VNDF_SAMPLE_WAVES_EXT
+#define VNDF_SAMPLE_WAVES_EXT 20
 #endif
 #ifndef VNDF_SAMPLE_PREFETCH
 #define VNDF_SAMPLE_PREFETCH 1
@@ -285,7 +289,8 @@ int launch_sample(const SampleArgs& a, int64_t n, bool vec, cudaStream_t s) {
       // small calls: about VNDF_SAMPLE_MIN_ITERS groups per thread (so the staging overlaps), in whole
       // multiples of the SM count so that every SM runs the same number of CTAs (at 2^20 samples 304
       // CTAs take 6.8 us where 256 took 7.8)
-      unsigned grid = grid_for(n4, kSampleBlock, 2048 / kSampleBlock, VNDF_SAMPLE_WAVES);
+      unsigned grid = grid_for(n4, kSampleBlock, 2048 / kSampleBlock,
+                               METHOD == kMethodCapExt ? VNDF_SAMPLE_WAVES_EXT : VNDF_SAMPLE_WAVES);
       if (VNDF_SAMPLE_MIN_ITERS > 1) {
         const int64_t per_iters = (n4 + int64_t(kSampleBlock) * VNDF_SAMPLE_MIN_ITERS - 1) /
                                   (int64_t(kSampleBlock) * VNDF_SAMPLE_MIN_ITERS);
