@@ -434,6 +434,8 @@ def compact_line(r):
     rf = r["roofline"]
     line["roofline"] = {k: rf[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
     line["roofline"]["kernel"] = "sample_pipe_kernel (cap, Philox, anisotropic, pdf)"
+    if r.get("device"):
+        line["device"] = r["device"]
     if r.get("rescued_frac") is not None:
         line["rescued"] = r["rescued_frac"]
     if "fwd_bwd" in r:
@@ -590,6 +592,8 @@ def run_ours(args, rank, world):
                      "traffic": (tps * n) if tps is not None else None,
                      "algorithmic_bytes": BYTES_PER_SAMPLE * n, "kernel": "sample_pipe_kernel<cap, philox, aniso, pdf>"},
         "gpu_launches": steps,
+        "device": f"{torch.cuda.get_device_name(dev)}, "
+                  f"{torch.cuda.get_device_properties(dev).multi_processor_count} SMs",
         "rescued_frac": rescued_frac,
         "clocks": clock,
         "per_step_ms": {"min": min(per), "median": statistics.median(per), "max": max(per)},

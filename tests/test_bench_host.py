@@ -77,6 +77,7 @@ def _full_record():
     r["prior_sampler"] = dict(leg(), cap_over_prior=1.06 + x)
     r["extended"] = {"sphere": dict(leg(), rescued_frac=4.5e-3 + x / 1e4), "hemisphere": leg()}
     r["rescued_frac"] = 7e-4 + x / 1e5
+    r["device"] = "NVIDIA GB300, 152 SMs"
     for k in ("reflection", "pdf", "isotropic", "fit"):
         r[k] = leg()
     r["paper_protocol"] = {"cap": leg(), "cap_strict": leg(), "polar": leg(), "cap_over_prior": 1.33 + x}
