@@ -18,7 +18,11 @@
  *   scalar path.  Results never depend on the path, the launch shape or how a
  *   batch is split into calls.
  * - `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
- *   are asynchronous and allocate no memory.
+ *   are asynchronous and allocate no memory.  Outside stream capture the
+ *   streaming and adjoint kernels are programmatic dependent launches: they
+ *   may become resident while the work ahead of them on the stream drains,
+ *   but wait for it to complete before they read or write any memory, so
+ *   stream order holds exactly as for ordinary launches.
  * - n = 0 is a no-op that returns VNDF_OK without examining any pointer.
  * - Output arrays must not overlap input arrays or one another: a kernel may
  *   store an output before it has read every input it still needs (the
