@@ -286,14 +286,16 @@ int launch_sample(const SampleArgs& a, int64_t n, bool vec, cudaStream_t s) {
   if (vec) {
     const int64_t n4 = n / 4;
     if (n4 > 0) {
-      // small calls: about VNDF_SAMPLE_MIN_ITERS groups per thread (so the staging overlaps), in whole
-      // multiples of the SM count so that every SM runs the same number of CTAs (at 2^20 samples 304
-      // CTAs take 6.8 us where 256 took 7.8)
+      // small calls: about VNDF_SAMPLE_MIN_ITERS groups per thread (so the staging overlaps; one fewer
+      // up to 2^21 samples, where the grid then fills all three CTA slots of every SM), in whole
+      // multiples of the SM count so that every SM runs the same number of CTAs.  Measured in a CUDA
+      // graph at 2^20 samples: 456 CTAs 6.86 us, 304 CTAs 7.10, 256 CTAs 7.8; at 2^22 (eager) three
+      // groups per thread took 30.45 us against 30.22 with four, at 2^24 103.4 against 100.5.
       unsigned grid = grid_for(n4, kSampleBlock, 2048 / kSampleBlock,
                                METHOD == kMethodCapExt ? VNDF_SAMPLE_WAVES_EXT : VNDF_SAMPLE_WAVES);
-      if (VNDF_SAMPLE_MIN_ITERS > 1) {
-        const int64_t per_iters = (n4 + int64_t(kSampleBlock) * VNDF_SAMPLE_MIN_ITERS - 1) /
-                                  (int64_t(kSampleBlock) * VNDF_SAMPLE_MIN_ITERS);
+      const int64_t iters = VNDF_SAMPLE_MIN_ITERS - (n4 <= (int64_t(1) << 19) ? 1 : 0);
+      if (iters > 1) {
+        const int64_t per_iters = (n4 + int64_t(kSampleBlock) * iters - 1) / (int64_t(kSampleBlock) * iters);
         const int64_t sms = sm_count();
         const int64_t g = (per_iters + sms - 1) / sms * sms;
         if (g < int64_t(grid)) grid = unsigned(g);
