@@ -85,19 +85,19 @@ def parse_args():
 
 # ----------------------------------------------------------------------------- helpers
 KERNEL_FILES = {
-    "stream": ("sample.cu", "rescue.cuh", "staging.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
-    "microbench_cap": ("microbench.cu", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
-    "microbench_cap_strict": ("microbench.cu", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
-    "microbench_polar": ("microbench.cu", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
-    "loss_backward": ("backward.cu", "staging.cuh", "vndf_adjoint.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh",
+    "stream": ("sample.cu", "rescue.cuh", "staging.cuh", "vndf_math.cuh", "pair.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
+    "microbench_cap": ("microbench.cu", "vndf_math.cuh", "pair.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
+    "microbench_cap_strict": ("microbench.cu", "vndf_math.cuh", "pair.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
+    "microbench_polar": ("microbench.cu", "vndf_math.cuh", "pair.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
+    "loss_backward": ("backward.cu", "staging.cuh", "vndf_adjoint.cuh", "vndf_math.cuh", "pair.cuh", "precise.cuh", "philox.cuh",
                       "common.cuh"),
-    "albedo": ("albedo.cu", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
-    "fit": ("fit.cu", "vndf_adjoint.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
-    "reflection": ("reflect.cu", "rescue.cuh", "staging.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh",
+    "albedo": ("albedo.cu", "vndf_math.cuh", "pair.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
+    "fit": ("fit.cu", "vndf_adjoint.cuh", "vndf_math.cuh", "pair.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
+    "reflection": ("reflect.cu", "rescue.cuh", "staging.cuh", "vndf_math.cuh", "pair.cuh", "precise.cuh", "philox.cuh",
                    "common.cuh"),
-    "hemisphere": ("hemisphere.cu", "rescue.cuh", "staging.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh",
+    "hemisphere": ("hemisphere.cu", "rescue.cuh", "staging.cuh", "vndf_math.cuh", "pair.cuh", "precise.cuh", "philox.cuh",
                    "common.cuh"),
-    "extended": ("sample.cu", "rescue.cuh", "staging.cuh", "vndf_math.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
+    "extended": ("sample.cu", "rescue.cuh", "staging.cuh", "vndf_math.cuh", "pair.cuh", "precise.cuh", "philox.cuh", "common.cuh"),
 }
 
 

@@ -387,7 +387,7 @@ size_t vndf_albedo_workspace_bytes(int32_t n_queries, int32_t max_samples_per_qu
  *                      workspaces.
  *   config             NULL (use the configuration vndf_albedo_autotune picked
  *                      on this device, else a default) or three int32 on the
- *                      host: warps per CTA (1-16), 256-sample groups per work
+ *                      host: warps per CTA (1-20), 256-sample groups per work
  *                      item (1-256; each warp takes a contiguous run of whole
  *                      items, the runs of all warps within one item of each
  *                      other), CTAs per SM (1-32; capped at the number an SM
@@ -433,7 +433,7 @@ int vndf_albedo_autotune(int32_t n_queries,
  * tuned earlier (for instance one stored on disk by the Python binding's
  * autotune cache) without timing again.  The configuration only chooses the
  * launch shape: E is the same for every configuration.
- *   config   three int32 on the host (warps per CTA 1-16, groups per item
+ *   config   three int32 on the host (warps per CTA 1-20, groups per item
  *            1-256, CTAs per SM 1-32), or NULL.
  * Returns VNDF_OK, VNDF_ERR_ARG (a value out of range), VNDF_ERR_SIZE (a
  * device ordinal above 63) or VNDF_ERR_CUDA (no current device).

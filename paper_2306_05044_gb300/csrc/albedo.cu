@@ -38,6 +38,7 @@ namespace vndf {
 
 constexpr int kGroupSamples = 256;  // samples per reduction group (one warp)
 constexpr int kLaneSamples = 8;     // consecutive samples per lane
+constexpr int kAlbedoMaxWarps = 20;  // warps per CTA at most (the kernel's launch bound)
 // Up to this many item offsets (nq + 1) are copied into each CTA's shared
 // memory (48 KB, the default dynamic limit), so that finding an item's query
 // costs shared-memory rather than L2 latency; larger batches search in place.
@@ -143,26 +144,45 @@ __device__ __forceinline__ QueryConst query_const(const AlbedoArgs& a, int32_t q
   return c;
 }
 
-// Estimator term of one sample: F G2 / G1(wi), or 0 when wo is below the surface.
-__device__ __forceinline__ float albedo_weight(const QueryConst& c, float f0, float u1, float u2) {
-  float hx, hy, hz, a;
-  cap_half_vector(c.i, u1, u2, hx, hy, hz, a);
-  const float vx = c.ax * hx, vy = c.ay * hy, vz = hz;
-  const float rv = rsqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
-  const float mx = vx * rv, my = vy * rv, mz = vz * rv;
-  const float d = fmaf(mx, c.ux, fmaf(my, c.uy, mz * c.uz));  // wi.wm > 0
-  const float ox = fmaf(2.f * d, mx, -c.ux);
-  const float oy = fmaf(2.f * d, my, -c.uy);
-  const float oz = fmaf(2.f * d, mz, -c.uz);
-  const float sx = c.ax * ox, sy = c.ay * oy;
-  const float po = fmaf(sx, sx, sy * sy);
-  const float lo = sqrt_fast(fmaf(oz, oz, po));
-  const float num = c.A * oz;
-  const float g = num * rcp_fast(fmaf(c.uz * po, rcp_fast(lo + oz), num));
-  const float t = 1.f - d;
-  const float t2 = t * t;
-  const float fr = fmaf(1.f - f0, t2 * t2 * t, f0);
-  return oz > 0.f ? fr * g : 0.f;
+// Estimator terms of two samples (x = 2 u1 and u2 of each in the halves of a
+// float2): F G2 / G1(wi), or 0 when wo is below the surface.  The FP32 fma / mul
+// / add run as packed pairs (pair.cuh), every lane rounded as in the scalar form
+// of the same steps; square roots, reciprocals and the final select per lane.
+__device__ __forceinline__ float2 albedo_weight2(const QueryConst& c, float f0, float2 x, float2 u2) {
+  using V = float2;
+  // the cap sample (cap_half_vector with i = c.i), h = (hx, hy, hz)
+  const float rho2 = fmaf(c.i.x, c.i.x, c.i.y * c.i.y);
+  const float a = __fadd_rn(1.f, c.i.z);
+  const V om = vsub(splat<V>(1.f), u2);
+  const V sin2 = vmul(u2, vfma(splat<V>(2.f * a), om, vmul(u2, splat<V>(rho2))));
+  const V st = vmap(SqrtFast{}, sin2);
+  V sp, cp;
+  sincospi_taylor(x, sp, cp);
+  const V hx = vfma(st, cp, splat<V>(c.i.x));
+  const V hy = vfma(st, sp, splat<V>(c.i.y));
+  const V hz = vmul(om, splat<V>(a));
+  // wm = v / |v| with v = (ax hx, ay hy, hz), and wo = 2 (wi.wm) wm - wi
+  const V vx = vmul(splat<V>(c.ax), hx), vy = vmul(splat<V>(c.ay), hy);
+  const V rv = vmap(RsqrtF{}, vfma(vx, vx, vfma(vy, vy, vmul(hz, hz))));
+  const V mx = vmul(vx, rv), my = vmul(vy, rv), mz = vmul(hz, rv);
+  const V d = vfma(mx, splat<V>(c.ux), vfma(my, splat<V>(c.uy), vmul(mz, splat<V>(c.uz))));  // wi.wm > 0
+  const V d2 = vadd(d, d);
+  const V ox = vfma(d2, mx, splat<V>(-c.ux));
+  const V oy = vfma(d2, my, splat<V>(-c.uy));
+  const V oz = vfma(d2, mz, splat<V>(-c.uz));
+  // G2 / G1(wi) = A oz / (A oz + uz P_o / (L_o + oz))
+  const V sx = vmul(splat<V>(c.ax), ox), sy = vmul(splat<V>(c.ay), oy);
+  const V po = vfma(sx, sx, vmul(sy, sy));
+  const V lo = vmap(SqrtFast{}, vfma(oz, oz, po));
+  const V num = vmul(splat<V>(c.A), oz);
+  const V den = vfma(vmul(splat<V>(c.uz), po), vmap(RcpFast{}, vadd(lo, oz)), num);
+  const V g = vmul(num, vmap(RcpFast{}, den));
+  // Schlick's Fresnel at wi.wm
+  const V t = vsub(splat<V>(1.f), d);
+  const V t2 = vmul(t, t);
+  const V fr = vfma(splat<V>(1.f - f0), vmul(vmul(t2, t2), t), splat<V>(f0));
+  const V w = vmul(fr, g);
+  return make_float2(oz.x > 0.f ? w.x : 0.f, oz.y > 0.f ? w.y : 0.f);
 }
 
 __device__ __forceinline__ float warp_tree(float v) {
@@ -183,10 +203,10 @@ __device__ __forceinline__ int32_t item_query(const int32_t* offsets, int32_t nq
   return lo;
 }
 
-// Two CTAs of up to 512 threads per SM: the register cap (64) leaves room for a lane's eight uniforms and
-// weights to be computed side by side (measured on the 4096-query grid: 204.0 us, against 204.8 us with the
-// sample pairs computed one after the other at 47 registers; a cap for three CTAs spills, 225 us).
-__global__ void __launch_bounds__(512, 2) albedo_kernel(AlbedoArgs a) {
+// One CTA of up to 20 warps per SM (86 registers): a lane computes its eight uniforms and then its four
+// packed weight pairs side by side, which the register file of 2 x 16 warps (64 each) could not hold
+// (4096-query grid, graph replays: 183 us at 20 warps, 187 at 16 with 116 registers, 195 at 32 warps).
+__global__ void __launch_bounds__(32 * kAlbedoMaxWarps, 1) albedo_kernel(AlbedoArgs a) {
   extern __shared__ int32_t s_offsets[];
   const int lane = threadIdx.x & 31;
   const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
@@ -253,12 +273,19 @@ __global__ void __launch_bounds__(512, 2) albedo_kernel(AlbedoArgs a) {
       for (int s = 0; s < kLaneSamples; s += 2) uniforms2(r, uint64_t(j0 + s), U1[s], U2[s], U1[s + 1], U2[s + 1]);
       if ((g + 1) * kGroupSamples <= n) {  // a full group (warp-uniform): no per-sample bound
 #pragma unroll
-        for (int s = 0; s < kLaneSamples; ++s) acc += albedo_weight(c, a.f0, U1[s], U2[s]);
+        for (int s = 0; s < kLaneSamples; s += 2) {
+          const float2 w = albedo_weight2(c, a.f0, make_float2(2.f * U1[s], 2.f * U1[s + 1]),
+                                          make_float2(U2[s], U2[s + 1]));
+          acc += w.x;
+          acc += w.y;
+        }
       } else {
 #pragma unroll
-        for (int s = 0; s < kLaneSamples; ++s) {
-          const float w = albedo_weight(c, a.f0, U1[s], U2[s]);
-          acc += j0 + s < n ? w : 0.f;
+        for (int s = 0; s < kLaneSamples; s += 2) {
+          const float2 w = albedo_weight2(c, a.f0, make_float2(2.f * U1[s], 2.f * U1[s + 1]),
+                                          make_float2(U2[s], U2[s + 1]));
+          acc += j0 + s < n ? w.x : 0.f;
+          acc += j0 + s + 1 < n ? w.y : 0.f;
         }
       }
       acc = warp_tree(acc);
@@ -275,7 +302,7 @@ struct AlbedoConfig {
 };
 
 bool config_ok(const AlbedoConfig& c) {
-  return c.block_warps >= 1 && c.block_warps <= 16 && c.groups_per_item >= 1 && c.groups_per_item <= 256 &&
+  return c.block_warps >= 1 && c.block_warps <= kAlbedoMaxWarps && c.groups_per_item >= 1 && c.groups_per_item <= 256 &&
          c.ctas_per_sm >= 1 && c.ctas_per_sm <= 32;
 }
 
@@ -284,7 +311,7 @@ std::mutex g_tune_mutex;
 AlbedoConfig g_tuned[64];
 bool g_has_tuned[64] = {false};
 
-constexpr AlbedoConfig kDefaultConfig{8, 1, 8};
+constexpr AlbedoConfig kDefaultConfig{20, 2, 1};
 
 AlbedoConfig current_config() {
   int dev = 0;
@@ -294,17 +321,27 @@ AlbedoConfig current_config() {
   return kDefaultConfig;
 }
 
-int launch_albedo(AlbedoArgs a, const AlbedoConfig& c, cudaStream_t s) {
-  a.groups_per_item = c.groups_per_item;
-  albedo_prologue_kernel<<<1, 1024, 0, s>>>(a);
-  const size_t smem = a.nq + 1 <= kCachedOffsets ? size_t(a.nq + 1) * sizeof(int32_t) : 0;
-  // Every CTA must be resident from the start: the item runs are cut for the whole grid, and
-  // a CTA that waited for a free slot would finish its run after the others.
+size_t albedo_smem(const AlbedoArgs& a) {
+  return a.nq + 1 <= kCachedOffsets ? size_t(a.nq + 1) * sizeof(int32_t) : 0;
+}
+
+// CTAs of block_warps warps that one SM holds at once (at least 1).
+int albedo_resident(const AlbedoArgs& a, int32_t block_warps) {
   int resident = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, albedo_kernel, 32 * c.block_warps, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, albedo_kernel, 32 * block_warps, albedo_smem(a)) !=
           cudaSuccess ||
       resident < 1)
     resident = 1;
+  return resident;
+}
+
+int launch_albedo(AlbedoArgs a, const AlbedoConfig& c, cudaStream_t s) {
+  a.groups_per_item = c.groups_per_item;
+  albedo_prologue_kernel<<<1, 1024, 0, s>>>(a);
+  const size_t smem = albedo_smem(a);
+  // Every CTA must be resident from the start: the item runs are cut for the whole grid, and
+  // a CTA that waited for a free slot would finish its run after the others.
+  const int resident = albedo_resident(a, c.block_warps);
   const int ctas = c.ctas_per_sm < resident ? c.ctas_per_sm : resident;
   const unsigned grid = static_cast<unsigned>(sm_count() * ctas);
   albedo_kernel<<<grid, 32 * c.block_warps, smem, s>>>(a);
@@ -429,23 +466,27 @@ extern "C" int vndf_albedo_autotune(int32_t n_queries, const float* wi_x, const 
   const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   AlbedoArgs a = albedo_args(n_queries, wi_x, wi_y, wi_z, alpha_x, alpha_y, n_samples, max_samples_per_query, f0,
                              seed, counter_base, stream_id, E, workspace);
-  static const int32_t warps[] = {4, 8, 16};
+  static const int32_t warps[] = {4, 8, 16, kAlbedoMaxWarps};
   static const int32_t gpis[] = {1, 2, 4};
-  static const int32_t ctas[] = {4, 8, 16};
+  static const int32_t ctas[] = {1, 2, 4, 8, 16};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return VNDF_ERR_CUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) {
     cudaEventDestroy(e0);
     return VNDF_ERR_CUDA;
   }
-  AlbedoConfig best{8, 1, 8};
+  AlbedoConfig best = kDefaultConfig;
   float best_t = INFINITY;
   int rc = VNDF_OK;
-  for (int32_t w : warps)
-    for (int32_t g : gpis)
+  for (int32_t w : warps) {
+    const int resident = albedo_resident(a, w);
+    for (int32_t g : gpis) {
+      int32_t prev = 0;
       for (int32_t c : ctas) {
-        if (w * 32 * c > 2048) continue;  // more threads than an SM holds
-        const AlbedoConfig cfg{w, g, c};
+        const int32_t eff = c < resident ? c : resident;  // the CTAs per SM the launch gets
+        if (eff == prev) continue;                         // the same launch as the last one timed
+        prev = eff;
+        const AlbedoConfig cfg{w, g, eff};
         rc = launch_albedo(a, cfg, s);  // warm-up
         if (rc != VNDF_OK) break;
         float t = INFINITY;
@@ -467,6 +508,10 @@ extern "C" int vndf_albedo_autotune(int32_t n_queries, const float* wi_x, const 
           best = cfg;
         }
       }
+      if (rc != VNDF_OK) break;
+    }
+    if (rc != VNDF_OK) break;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != VNDF_OK) return rc;

@@ -30,6 +30,7 @@
 #pragma once
 #include <cstdint>
 
+#include "pair.cuh"
 #include "precise.cuh"
 
 namespace vndf {
@@ -72,6 +73,17 @@ __device__ __forceinline__ float rcp_fast(float x) {
   return r;
 }
 
+// The same as function objects, for applying them lane by lane (pair.cuh's vmap).
+struct SqrtFast {
+  __device__ __forceinline__ float operator()(float x) const { return sqrt_fast(x); }
+};
+struct RcpFast {
+  __device__ __forceinline__ float operator()(float x) const { return rcp_fast(x); }
+};
+struct RsqrtF {
+  __device__ __forceinline__ float operator()(float x) const { return rsqrtf(x); }
+};
+
 // sin(pi x) and cos(pi x) for finite x (used with x = 2 u1, the azimuth in
 // half turns).  Reduction: j = rint(2x), r = x - j/2 in [-1/4, 1/4]; for
 // x in [0, 2] the subtraction is exact (Sterbenz).  sin(pi r) and cos(pi r)
@@ -80,7 +92,25 @@ __device__ __forceinline__ float rcp_fast(float x) {
 // with fma; the quadrant identities sin(pi (r + k/2)) = {s, c, -s, -c},
 // cos(pi (r + k/2)) = {c, -s, -c, s} are exact.  Absolute error <= 1.5 * 2^-24
 // over all 2^24 uniforms (checked against FP64 sin and cos).
-__device__ __forceinline__ void sincospi_taylor(float x, float& s, float& c) {
+// (Written for float or, with the packed FP32x2 operations of pair.cuh, for a
+// float2 of two independent arguments; both give the same bits per lane.)
+__device__ __forceinline__ void sincospi_quadrant(float j, float ps, float pc, float& s, float& c) {
+  const int k = static_cast<int>(j) & 3;
+  const float a = (k & 1) ? pc : ps;
+  const float b = (k & 1) ? ps : pc;
+  s = (k & 2) ? -a : a;
+  c = ((k + 1) & 2) ? -b : b;
+}
+__device__ __forceinline__ void sincospi_quadrant(float2 j, float2 ps, float2 pc, float2& s, float2& c) {
+  sincospi_quadrant(j.x, ps.x, pc.x, s.x, c.x);
+  sincospi_quadrant(j.y, ps.y, pc.y, s.y, c.y);
+}
+struct RintTwice {
+  __device__ __forceinline__ float operator()(float x) const { return rintf(2.f * x); }
+};
+
+template <typename V>
+__device__ __forceinline__ void sincospi_taylor(V x, V& s, V& c) {
   constexpr float S1 = 3.14159265358979323846f;     //  pi
   constexpr float S3 = -5.16771278004997003f;       // -pi^3 / 3!
   constexpr float S5 = 2.55016403987734549f;        //  pi^5 / 5!
@@ -91,24 +121,20 @@ __device__ __forceinline__ void sincospi_taylor(float x, float& s, float& c) {
   constexpr float C6 = -1.33526276885458949f;       // -pi^6 / 6!
   constexpr float C8 = 0.235330630358893200f;       //  pi^8 / 8!
   constexpr float C10 = -0.0258068913900140009f;    // -pi^10 / 10!
-  const float j = rintf(2.f * x);
-  const float r = fmaf(-0.5f, j, x);
-  const float r2 = r * r;
-  float ps = fmaf(r2, S9, S7);
-  ps = fmaf(r2, ps, S5);
-  ps = fmaf(r2, ps, S3);
-  ps = fmaf(r2, ps, S1);
-  ps *= r;
-  float pc = fmaf(r2, C10, C8);
-  pc = fmaf(r2, pc, C6);
-  pc = fmaf(r2, pc, C4);
-  pc = fmaf(r2, pc, C2);
-  pc = fmaf(r2, pc, 1.f);
-  const int k = static_cast<int>(j) & 3;
-  const float a = (k & 1) ? pc : ps;
-  const float b = (k & 1) ? ps : pc;
-  s = (k & 2) ? -a : a;
-  c = ((k + 1) & 2) ? -b : b;
+  const V j = vmap(RintTwice{}, x);
+  const V r = vfma(splat<V>(-0.5f), j, x);
+  const V r2 = vmul(r, r);
+  V ps = vfma(r2, splat<V>(S9), splat<V>(S7));
+  ps = vfma(r2, ps, splat<V>(S5));
+  ps = vfma(r2, ps, splat<V>(S3));
+  ps = vfma(r2, ps, splat<V>(S1));
+  ps = vmul(ps, r);
+  V pc = vfma(r2, splat<V>(C10), splat<V>(C8));
+  pc = vfma(r2, pc, splat<V>(C6));
+  pc = vfma(r2, pc, splat<V>(C4));
+  pc = vfma(r2, pc, splat<V>(C2));
+  pc = vfma(r2, pc, splat<V>(1.f));
+  sincospi_quadrant(j, ps, pc, s, c);
 }
 
 // Domain of the method: wi.z > 0, alphas > 0, everything finite (NaN fails every test).

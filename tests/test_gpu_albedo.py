@@ -70,7 +70,7 @@ def test_albedo_small_alpha_is_fresnel(v, grid):
 def test_albedo_bit_identical_across_configs_splits_and_graphs(v, grid):
     args = (grid["wi_x"], grid["wi_y"], grid["wi_z"], grid["alpha_x"], None, grid["n_samples"])
     ref = v.vndf_albedo_batched(*args, seed=11, counter_base=5)
-    for cfg in [(1, 1, 1), (4, 1, 2), (8, 4, 4), (16, 8, 4), (2, 256, 32)]:
+    for cfg in [(1, 1, 1), (4, 1, 2), (8, 4, 4), (16, 8, 4), (20, 2, 1), (2, 256, 32)]:
         assert torch.equal(v.vndf_albedo_batched(*args, seed=11, counter_base=5, config=cfg), ref)
     # split the queries into two calls with the stream id advanced by the split point
     k = 1500
@@ -113,7 +113,7 @@ def test_albedo_autotune_cache_sets_the_stored_configuration(v, grid, tmp_path):
         tuned, ms = v.vndf_albedo_autotune(*args, cache=cache)
         assert v.vndf_albedo_get_config() == (tuned, True)
         v.vndf_albedo_set_config(None)  # as in a fresh process
-        assert v.vndf_albedo_get_config() == ((8, 1, 8), False)
+        assert v.vndf_albedo_get_config() == ((20, 2, 1), False)
         hit = v.vndf_albedo_autotune(*args, cache=cache)
         assert hit == (tuned, ms)
         assert v.vndf_albedo_get_config() == (tuned, True)
