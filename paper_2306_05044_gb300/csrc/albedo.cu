@@ -139,7 +139,7 @@ __device__ __forceinline__ QueryConst query_const(const AlbedoArgs& a, int32_t q
   const float sx = c.ax * c.ux, sy = c.ay * c.uy;
   const float l2 = fmaf(sx, sx, fmaf(sy, sy, c.uz * c.uz));
   const float rl = rsqrtf(l2);
-  c.i = Stretched{sx * rl, sy * rl, c.uz * rl};
+  c.i = Stretched{sx * rl, sy * rl, c.uz * rl, fmaf(c.uz, rl, 1.f)};
   c.A = l2 * rl + c.uz;
   return c;
 }
@@ -152,7 +152,7 @@ __device__ __forceinline__ float2 albedo_weight2(const QueryConst& c, float f0, 
   using V = float2;
   // the cap sample (cap_half_vector with i = c.i), h = (hx, hy, hz)
   const float rho2 = fmaf(c.i.x, c.i.x, c.i.y * c.i.y);
-  const float a = __fadd_rn(1.f, c.i.z);
+  const float a = c.i.a;  // 1 + i.z, as in the sampler
   const V om = vsub(splat<V>(1.f), u2);
   const V sin2 = vmul(u2, vfma(splat<V>(2.f * a), om, vmul(u2, splat<V>(rho2))));
   const V st = vmap(SqrtFast{}, sin2);

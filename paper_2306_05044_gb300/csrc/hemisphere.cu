@@ -112,10 +112,17 @@ __global__ void __launch_bounds__(kHemiBlock, 3) hemi_pipe_kernel(HemiArgs a, in
     float MX[4], MY[4], MZ[4], P[4];
     unsigned rescue = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-      rescue |= unsigned(sample_one<kMethodCapExt, PDF, true>(X[k], Y[k], Z[k], 1.f, 1.f, U1[k], U2[k], MX[k],
-                                                              MY[k], MZ[k], P[k]))
-                << k;
+    for (int k = 0; k < 4; k += 2) {  // two packed pairs
+      float2 mx, my, mz, p;
+      const bool2 b = sample_one<kMethodCapExt, PDF, true>(lanes(X, k), lanes(Y, k), lanes(Z, k), splat<float2>(1.f),
+                                                           splat<float2>(1.f), lanes(U1, k), lanes(U2, k), mx, my,
+                                                           mz, p);
+      set_lanes(MX, k, mx);
+      set_lanes(MY, k, my);
+      set_lanes(MZ, k, mz);
+      if constexpr (PDF) set_lanes(P, k, p);
+      rescue |= (unsigned(b.x) << k) | (unsigned(b.y) << (k + 1));
+    }
     if constexpr (!kBatched) {
       if (rescue) {  // rare: redone in place
 #pragma unroll

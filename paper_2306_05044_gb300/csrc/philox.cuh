@@ -26,15 +26,14 @@ __host__ __device__ inline Rng make_rng(uint64_t seed, uint64_t counter_base, ui
 }
 
 // Ten rounds: two 32x32->64 products with the published multipliers, the word
-// permutation, and the Weyl key schedule with the published increments.  Each
-// product is one widening multiply whose halves are the round's lo and hi words.
+// permutation, and the Weyl key schedule with the published increments.
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint64_t p0 = uint64_t(0xD2511F53u) * c.x;
-    const uint64_t p1 = uint64_t(0xCD9E8D57u) * c.z;
-    const uint32_t lo0 = uint32_t(p0), hi0 = uint32_t(p0 >> 32);
-    const uint32_t lo1 = uint32_t(p1), hi1 = uint32_t(p1 >> 32);
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
     c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;

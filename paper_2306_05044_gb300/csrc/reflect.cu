@@ -63,7 +63,7 @@ __device__ __forceinline__ Reflected reflect_one(float wx, float wy, float wz, f
   const float sx = ax * wx, sy = ay * wy;
   const float l2 = fmaf(sx, sx, fmaf(sy, sy, wz * wz));
   const float rl = rsqrtf(l2);
-  const Stretched i{sx * rl, sy * rl, wz * rl};
+  const Stretched i{sx * rl, sy * rl, wz * rl, fmaf(wz, rl, 1.f)};
   float hx, hy, hz, a;
   if constexpr (PRECISE_H) {
     const float4 p = half_vector_precise(wx, wy, wz, ax, ay, u1, u2);

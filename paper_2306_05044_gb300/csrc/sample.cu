@@ -106,12 +106,7 @@ __global__ void __launch_bounds__(kSampleBlock, VNDF_SAMPLE_MIN_BLOCKS) sample_v
       *reinterpret_cast<float4*>(U2) = cur.u2;
     }
     float MX[4], MY[4], MZ[4], P[4];
-    unsigned rescue = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      rescue |= unsigned(sample_one<METHOD, PDF, true>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], MX[k], MY[k],
-                                                       MZ[k], P[k]))
-                << k;
+    unsigned rescue = sample_four<METHOD, PDF>(X, Y, Z, AX, AY, U1, U2, MX, MY, MZ, P);
     if constexpr (is_cap<METHOD>()) {
       if (rescue) {  // rare: ill-conditioned samples redone in double-float
 #pragma unroll
@@ -209,12 +204,7 @@ __global__ void __launch_bounds__(kSampleBlock, VNDF_SAMPLE_MIN_BLOCKS) sample_p
     }
     slot = (slot + 1) % S;
     float MX[4], MY[4], MZ[4], P[4];
-    unsigned rescue = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      rescue |= unsigned(sample_one<METHOD, PDF, true>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], MX[k], MY[k],
-                                                       MZ[k], P[k]))
-                << k;
+    unsigned rescue = sample_four<METHOD, PDF>(X, Y, Z, AX, AY, U1, U2, MX, MY, MZ, P);
     if constexpr (is_cap<METHOD>() && !kBatched) {
       if (rescue) {  // rare: ill-conditioned samples redone in double-float, in place
 #pragma unroll

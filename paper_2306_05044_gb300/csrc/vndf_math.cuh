@@ -149,45 +149,61 @@ __device__ __forceinline__ bool in_domain_ext_inputs(float wx, float wy, float w
   return (ax > 0.f) & (ay > 0.f) & finite_f(wx) & finite_f(wy) & finite_f(wz) & finite_f(ax) & finite_f(ay);
 }
 
-template <int METHOD>
-__device__ __forceinline__ bool in_domain_m(float wx, float wy, float wz, float ax, float ay) {
+__device__ __forceinline__ bool2 in_domain(float2 wx, float2 wy, float2 wz, float2 ax, float2 ay) {
+  return {in_domain(wx.x, wy.x, wz.x, ax.x, ay.x), in_domain(wx.y, wy.y, wz.y, ax.y, ay.y)};
+}
+__device__ __forceinline__ bool2 in_domain_ext_inputs(float2 wx, float2 wy, float2 wz, float2 ax, float2 ay) {
+  return {in_domain_ext_inputs(wx.x, wy.x, wz.x, ax.x, ay.x), in_domain_ext_inputs(wx.y, wy.y, wz.y, ax.y, ay.y)};
+}
+
+template <int METHOD, typename V>
+__device__ __forceinline__ Mask<V> in_domain_m(V wx, V wy, V wz, V ax, V ay) {
   if constexpr (METHOD == kMethodCapExt)
     return in_domain_ext_inputs(wx, wy, wz, ax, ay);
   else
     return in_domain(wx, wy, wz, ax, ay);
 }
 
-struct Stretched {
-  float x, y, z;  // i = M^-1 wi / |M^-1 wi|
+// The samplers below are written for V = float (one sample) or V = float2 (two
+// independent samples, one per half, on the packed FP32x2 operations of
+// pair.cuh).  Every operation is explicit, so both widths round every lane the
+// same way and give the same bits.
+template <typename V>
+struct StretchedV {
+  V x, y, z;  // i = M^-1 wi / |M^-1 wi|
+  V a;        // 1 + i.z rounded once, as fma(wi.z, 1 / |M^-1 wi|, 1)
 };
+using Stretched = StretchedV<float>;
 
-__device__ __forceinline__ Stretched stretch(float wx, float wy, float wz, float ax, float ay) {
-  const float sx = ax * wx, sy = ay * wy;
-  const float l2 = fmaf(sx, sx, fmaf(sy, sy, wz * wz));
-  const float r = rsqrtf(l2);
-  return {sx * r, sy * r, wz * r};
+// a is formed by one fma rather than as 1 + (the rounded i.z): an add whose
+// operand is a packed product used nowhere else may be fused into an fma by the
+// assembler, which would round the two widths differently.
+template <typename V>
+__device__ __forceinline__ StretchedV<V> stretch(V wx, V wy, V wz, V ax, V ay) {
+  const V sx = vmul(ax, wx), sy = vmul(ay, wy);
+  const V r = vmap(RsqrtF{}, vfma(sx, sx, vfma(sy, sy, vmul(wz, wz))));
+  return {vmul(sx, r), vmul(sy, r), vmul(wz, r), vfma(wz, r, splat<V>(1.f))};
 }
 
 // Spherical-cap hemisphere sample: returns h = c + i (unnormalised).  With
 // EXT, i.z may be negative and a = 1 + i.z is formed without cancellation.
-template <bool EXT = false>
-__device__ __forceinline__ void cap_half_vector(const Stretched& i, float u1, float u2,
-                                                float& hx, float& hy, float& hz, float& a) {
-  const float rho2 = fmaf(i.x, i.x, i.y * i.y);                 // 1 - i.z^2
-  // an explicit add, never contracted with the stretch's product into an fma:
-  // both variants then round a the same way and agree bit for bit above the horizon
-  const float a_up = __fadd_rn(1.f, i.z);
-  if constexpr (EXT)
-    a = i.z >= 0.f ? a_up : rho2 * rcp_fast(1.f - i.z);  // 1 - i.z in [1, 2]
+template <bool EXT = false, typename V>
+__device__ __forceinline__ void cap_half_vector(const StretchedV<V>& i, V u1, V u2, V& hx, V& hy, V& hz, V& a) {
+  const V rho2 = vfma(i.x, i.x, vmul(i.y, i.y));  // 1 - i.z^2
+  // both variants take the stretch's a above the horizon, so they agree bit for bit there
+  const V a_up = i.a;
+  if constexpr (EXT)  // 1 - i.z in [1, 2]
+    a = vsel(vge(i.z, splat<V>(0.f)), a_up, vmul(rho2, vmap(RcpFast{}, vsub(splat<V>(1.f), i.z))));
   else
     a = a_up;
-  const float sin2 = u2 * fmaf(2.f * a, 1.f - u2, u2 * rho2);  // (1 - z)(1 + z)
-  const float st = sqrt_fast(sin2);
-  float sp, cp;
-  sincospi_taylor(2.f * u1, sp, cp);
-  hx = fmaf(st, cp, i.x);
-  hy = fmaf(st, sp, i.y);
-  hz = (1.f - u2) * a;                  // z + i.z
+  const V om = vsub(splat<V>(1.f), u2);
+  const V sin2 = vmul(u2, vfma(vmul(splat<V>(2.f), a), om, vmul(u2, rho2)));  // (1 - z)(1 + z)
+  const V st = vmap(SqrtFast{}, sin2);
+  V sp, cp;
+  sincospi_taylor(vmul(splat<V>(2.f), u1), sp, cp);
+  hx = vfma(st, cp, i.x);
+  hy = vfma(st, sp, i.y);
+  hz = vmul(om, a);  // z + i.z
 }
 
 // Heitz 2018 cross-section sampler (Sec. 2 step (2)): returns a unit hemisphere
@@ -200,39 +216,38 @@ __device__ __forceinline__ void cap_half_vector(const Stretched& i, float u1, fl
 //   1 - s        = (i.x^2 + i.y^2) / (2 (1 + i.z)),
 //   1 - t1^2 - t2^2 = (q - t2)(q + t2) = s (q - t2o) (2 (1 - s) q + s (q + t2o)),
 // so all factors are sums of non-negative terms.
-__device__ __forceinline__ void polar_disk_normal(const Stretched& i, float u1, float u2,
-                                                  float& hx, float& hy, float& hz) {
-  const float tmp = fmaf(i.x, i.x, i.y * i.y);
-  float w1x = 1.f, w1y = 0.f;
-  if (tmp > 0.f) {
-    const float r = rsqrtf(tmp);
-    w1x = -i.y * r;
-    w1y = i.x * r;
-  }
+template <typename V>
+__device__ __forceinline__ void polar_disk_normal(const StretchedV<V>& i, V u1, V u2, V& hx, V& hy, V& hz) {
+  const V tmp = vfma(i.x, i.x, vmul(i.y, i.y));
+  // w1 = (-i.y, i.x, 0) / |.|, or (1, 0, 0) at the pole
+  const Mask<V> tilted = vgt(tmp, splat<V>(0.f));
+  const V r0 = vmap(RsqrtF{}, tmp);
+  const V w1x = vsel(tilted, vmul(vneg(i.y), r0), splat<V>(1.f));
+  const V w1y = vsel(tilted, vmul(i.x, r0), splat<V>(0.f));
   // w2 = i x w1 (w1.z = 0)
-  const float w2x = -i.z * w1y;
-  const float w2y = i.z * w1x;
-  const float w2z = fmaf(i.x, w1y, -i.y * w1x);
-  float sp, cp;
-  sincospi_taylor(2.f * u1, sp, cp);
-  const float r = sqrt_fast(u2);
-  const float t1 = r * cp;
-  const float t2o = r * sp;
-  const float om = 1.f - u2;
-  const float q = sqrt_fast(fmaf(u2 * sp, sp, om));  // sqrt(1 - t1^2)
-  const float a = 1.f + i.z;
-  const float s = 0.5f * a;
-  const float oms = 0.5f * tmp * rcp_fast(a);      // 1 - s
-  const bool pos = t2o >= 0.f;
-  const float big = pos ? q + t2o : q - t2o;        // no cancellation either way
-  const float small = om * rcp_fast(big);           // the other one of q -/+ t2o
-  const float qm = pos ? small : big;               // q - t2o
-  const float qp = pos ? big : small;               // q + t2o
-  const float t2 = fmaf(oms, q, s * t2o);
-  const float ti = sqrt_fast(s * qm * fmaf(2.f * oms, q, s * qp));
-  hx = fmaf(t1, w1x, fmaf(t2, w2x, ti * i.x));
-  hy = fmaf(t1, w1y, fmaf(t2, w2y, ti * i.y));
-  hz = fmaf(t2, w2z, ti * i.z);
+  const V w2x = vmul(vneg(i.z), w1y);
+  const V w2y = vmul(i.z, w1x);
+  const V w2z = vfma(i.x, w1y, vmul(vneg(i.y), w1x));
+  V sp, cp;
+  sincospi_taylor(vmul(splat<V>(2.f), u1), sp, cp);
+  const V r = vmap(SqrtFast{}, u2);
+  const V t1 = vmul(r, cp);
+  const V t2o = vmul(r, sp);
+  const V om = vsub(splat<V>(1.f), u2);
+  const V q = vmap(SqrtFast{}, vfma(vmul(u2, sp), sp, om));  // sqrt(1 - t1^2)
+  const V a = vadd(splat<V>(1.f), i.z);
+  const V s = vmul(splat<V>(0.5f), a);
+  const V oms = vmul(vmul(splat<V>(0.5f), tmp), vmap(RcpFast{}, a));  // 1 - s
+  const Mask<V> pos = vge(t2o, splat<V>(0.f));
+  const V big = vsel(pos, vadd(q, t2o), vsub(q, t2o));  // no cancellation either way
+  const V small = vmul(om, vmap(RcpFast{}, big));       // the other one of q -/+ t2o
+  const V qm = vsel(pos, small, big);                   // q - t2o
+  const V qp = vsel(pos, big, small);                   // q + t2o
+  const V t2 = vfma(oms, q, vmul(s, t2o));
+  const V ti = vmap(SqrtFast{}, vmul(vmul(s, qm), vfma(vmul(splat<V>(2.f), oms), q, vmul(s, qp))));
+  hx = vfma(t1, w1x, vfma(t2, w2x, vmul(ti, i.x)));
+  hy = vfma(t1, w1y, vfma(t2, w2y, vmul(ti, i.y)));
+  hz = vfma(t2, w2z, vmul(ti, i.z));
 }
 
 // Threshold on the condition number above which a cap sample is recomputed in
@@ -243,71 +258,101 @@ __device__ __forceinline__ void polar_disk_normal(const Stretched& i, float u1, 
 constexpr float kRescueKappa = 24.f;
 
 // The FP32 tail of a sample: unstretch h, normalise, and (if PDF) the fused density.
-template <int METHOD, bool PDF>
-__device__ __forceinline__ void finish_sample(const Stretched& i, float ax, float ay, float hx, float hy, float hz,
-                                              float a, float& mx, float& my, float& mz, float& pdf) {
-  const float vx = ax * hx, vy = ay * hy, vz = hz;
-  const float vv = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
-  const float rv = rsqrtf(vv);
-  mx = vx * rv;
-  my = vy * rv;
-  mz = vz * rv;
+template <int METHOD, bool PDF, typename V>
+__device__ __forceinline__ void finish_sample(const StretchedV<V>& i, V ax, V ay, V hx, V hy, V hz, V a, V& mx,
+                                              V& my, V& mz, V& pdf) {
+  const V vx = vmul(ax, hx), vy = vmul(ay, hy), vz = hz;
+  const V vv = vfma(vx, vx, vfma(vy, vy, vmul(vz, vz)));
+  const V rv = vmap(RsqrtF{}, vv);
+  mx = vmul(vx, rv);
+  my = vmul(vy, rv);
+  mz = vmul(vz, rv);
   if constexpr (PDF) {
-    const float nv = vv * rv;  // |v|
+    const V nv = vmul(vv, rv);  // |v|
+    const V rden = vmap(RcpFast{}, vmul(vmul(vmul(splat<V>(kPi), ax), ay), a));
     if constexpr (is_cap<METHOD>()) {
       // |v|^3 / (pi ax ay a |h|^2) as (|v|^2 / |h|^2) |v| / (pi ax ay a): |v|^2 / |h|^2 lies
       // between min(ax, ay, 1)^2 and max(ax, ay, 1)^2, so no factor leaves the FP32 range,
       // whereas |v|^3 underflows once |v| < 2e-13 (tiny roughness together with the
       // extended domain's smallest cap heights a)
-      const float hh = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
-      pdf = (vv * rcp_fast(hh)) * nv * rcp_fast(kPi * ax * ay * a);
+      const V hh = vfma(hx, hx, vfma(hy, hy, vmul(hz, hz)));
+      pdf = vmul(vmul(vmul(vv, vmap(RcpFast{}, hh)), nv), rden);
     } else {
-      const float hi = fmaxf(fmaf(hx, i.x, fmaf(hy, i.y, hz * i.z)), 0.f);
-      pdf = 2.f * hi * vv * nv * rcp_fast(kPi * ax * ay * a);
+      const V hi = vmax(vfma(hx, i.x, vfma(hy, i.y, vmul(hz, i.z))), splat<V>(0.f));
+      pdf = vmul(vmul(vmul(vmul(splat<V>(2.f), hi), vv), nv), rden);
     }
   }
 }
 
-// One sample of Sec. 2 steps (1)-(3) with the chosen hemisphere sampler and,
-// if PDF, the fused density.  Out-of-domain inputs give wm = (0,0,1), pdf = 0.
-// With PRECISE (cap sampler only) the return value flags an ill-conditioned
-// sample whose result must be replaced by sample_one_precise; the check costs a
-// few FP32 operations and keeps the rare slow path out of the unrolled loop.
-template <int METHOD, bool PDF, bool PRECISE = false>
-__device__ __forceinline__ bool sample_one(float wx, float wy, float wz, float ax, float ay,
-                                           float u1, float u2,
-                                           float& mx, float& my, float& mz, float& pdf) {
-  bool ok = in_domain_m<METHOD>(wx, wy, wz, ax, ay);
-  const Stretched i = stretch(wx, wy, wz, ax, ay);
-  float hx, hy, hz, a;
+// One sample (V = float) or two (V = float2) of Sec. 2 steps (1)-(3) with the
+// chosen hemisphere sampler and, if PDF, the fused density.  Out-of-domain
+// inputs give wm = (0,0,1), pdf = 0.  With PRECISE (cap sampler only) the
+// returned mask flags ill-conditioned samples whose results must be replaced
+// by sample_one_precise; the check costs a few FP32 operations and keeps the
+// rare slow path out of the unrolled loop.
+template <int METHOD, bool PDF, bool PRECISE = false, typename V>
+__device__ __forceinline__ Mask<V> sample_one(V wx, V wy, V wz, V ax, V ay, V u1, V u2, V& mx, V& my, V& mz,
+                                              V& pdf) {
+  Mask<V> ok = in_domain_m<METHOD>(wx, wy, wz, ax, ay);
+  const StretchedV<V> i = stretch(wx, wy, wz, ax, ay);
+  V hx, hy, hz, a;
   if constexpr (is_cap<METHOD>()) {
     cap_half_vector<METHOD == kMethodCapExt>(i, u1, u2, hx, hy, hz, a);
-    if constexpr (METHOD == kMethodCapExt) ok &= a >= kMinCapA;
+    if constexpr (METHOD == kMethodCapExt) ok &= vge(a, splat<V>(kMinCapA));
   } else {
     polar_disk_normal(i, u1, u2, hx, hy, hz);
-    a = 1.f + i.z;
+    a = vadd(splat<V>(1.f), i.z);
   }
   finish_sample<METHOD, PDF>(i, ax, ay, hx, hy, hz, a, mx, my, mz, pdf);
-  bool bad = false;
+  Mask<V> bad{};
   if constexpr (PRECISE && is_cap<METHOD>()) {
     // |c.x| + |i.x| etc. bound the rounding of h; compare it with |v| and |h|
-    const float sx = fabsf(hx - i.x) + fabsf(i.x), sy = fabsf(hy - i.y) + fabsf(i.y);
-    const float vx = ax * hx, vy = ay * hy;
-    const float vv = fmaf(vx, vx, fmaf(vy, vy, hz * hz));
-    const float k2 = fmaf(ax * sx, ax * sx, fmaf(ay * sy, ay * sy, hz * hz));
+    const V sx = vadd(vabs(vsub(hx, i.x)), vabs(i.x)), sy = vadd(vabs(vsub(hy, i.y)), vabs(i.y));
+    const V vx = vmul(ax, hx), vy = vmul(ay, hy);
+    const V hz2 = vmul(hz, hz);
+    const V vv = vfma(vx, vx, vfma(vy, vy, hz2));
+    const V ksx = vmul(ax, sx), ksy = vmul(ay, sy);
+    const V k2 = vfma(ksx, ksx, vfma(ksy, ksy, hz2));
     // both tests whether or not the pdf is wanted, so the normals do not depend on it
-    const float kh2 = fmaf(sx, sx, fmaf(sy, sy, hz * hz));
-    bad = (k2 > kRescueKappa * kRescueKappa * vv) |
-          (kh2 > kRescueKappa * kRescueKappa * fmaf(hx, hx, fmaf(hy, hy, hz * hz)));
+    const V kh2 = vfma(sx, sx, vfma(sy, sy, hz2));
+    const V K2 = splat<V>(kRescueKappa * kRescueKappa);
+    bad = vgt(k2, vmul(K2, vv)) | vgt(kh2, vmul(K2, vfma(hx, hx, vfma(hy, hy, hz2))));
     bad &= ok;
   }
-  if (!ok) {
-    mx = 0.f;
-    my = 0.f;
-    mz = 1.f;
-    if constexpr (PDF) pdf = 0.f;
-  }
+  mx = vsel(ok, mx, splat<V>(0.f));
+  my = vsel(ok, my, splat<V>(0.f));
+  mz = vsel(ok, mz, splat<V>(1.f));
+  if constexpr (PDF) pdf = vsel(ok, pdf, splat<V>(0.f));
   return bad;
+}
+
+// Lanes k, k + 1 of a thread's four samples as one pair, and back.
+__device__ __forceinline__ float2 lanes(const float (&v)[4], int k) { return make_float2(v[k], v[k + 1]); }
+__device__ __forceinline__ void set_lanes(float (&v)[4], int k, float2 x) {
+  v[k] = x.x;
+  v[k + 1] = x.y;
+}
+
+// A thread's four consecutive samples, computed as two packed pairs; returns the
+// rescue flags of sample_one (PRECISE) as bits 0..3.
+template <int METHOD, bool PDF>
+__device__ __forceinline__ unsigned sample_four(const float (&X)[4], const float (&Y)[4], const float (&Z)[4],
+                                                const float (&AX)[4], const float (&AY)[4], const float (&U1)[4],
+                                                const float (&U2)[4], float (&MX)[4], float (&MY)[4],
+                                                float (&MZ)[4], float (&P)[4]) {
+  unsigned rescue = 0;
+#pragma unroll
+  for (int k = 0; k < 4; k += 2) {
+    float2 mx, my, mz, p;
+    const bool2 b = sample_one<METHOD, PDF, true>(lanes(X, k), lanes(Y, k), lanes(Z, k), lanes(AX, k), lanes(AY, k),
+                                                  lanes(U1, k), lanes(U2, k), mx, my, mz, p);
+    set_lanes(MX, k, mx);
+    set_lanes(MY, k, my);
+    set_lanes(MZ, k, mz);
+    if constexpr (PDF) set_lanes(P, k, p);
+    rescue |= (unsigned(b.x) << k) | (unsigned(b.y) << (k + 1));
+  }
+  return rescue;
 }
 
 // The cap sample recomputed with its half vector in double-float (in-domain
