@@ -49,23 +49,28 @@ __device__ __noinline__ float4 half_vector_precise(float wx, float wy, float wz,
   return r;
 }
 
-struct Reflected {
-  float ox, oy, oz, pdf, weight;
+template <typename V>
+struct ReflectedV {
+  V ox, oy, oz, pdf, weight;
 };
+using Reflected = ReflectedV<float>;
 
-// One reflected sample.  With PRECISE_H the half vector comes from the
-// double-float path; otherwise from FP32, and *bad reports whether it was
-// ill-conditioned (the caller then redoes the sample with PRECISE_H).
-template <bool PRECISE_H>
-__device__ __forceinline__ Reflected reflect_one(float wx, float wy, float wz, float ax, float ay, float u1,
-                                                 float u2, float f0, bool* bad) {
-  const bool ok = in_domain(wx, wy, wz, ax, ay);
-  const float sx = ax * wx, sy = ay * wy;
-  const float l2 = fmaf(sx, sx, fmaf(sy, sy, wz * wz));
-  const float rl = rsqrtf(l2);
-  const Stretched i{sx * rl, sy * rl, wz * rl, fmaf(wz, rl, 1.f)};
-  float hx, hy, hz, a;
+// One reflected sample (V = float) or two (V = float2, on the packed FP32x2
+// operations; both widths give the same bits).  With PRECISE_H (one sample
+// only) the half vector comes from the double-float path; otherwise from FP32,
+// and *bad reports whether it was ill-conditioned (the caller then redoes the
+// sample with PRECISE_H).
+template <bool PRECISE_H, typename V>
+__device__ __forceinline__ ReflectedV<V> reflect_one(V wx, V wy, V wz, V ax, V ay, V u1, V u2, float f0,
+                                                     Mask<V>* bad) {
+  const Mask<V> ok = in_domain(wx, wy, wz, ax, ay);
+  const V sx = vmul(ax, wx), sy = vmul(ay, wy);
+  const V l2 = vfma(sx, sx, vfma(sy, sy, vmul(wz, wz)));
+  const V rl = vmap(RsqrtF{}, l2);
+  const StretchedV<V> i{vmul(sx, rl), vmul(sy, rl), vmul(wz, rl), vfma(wz, rl, splat<V>(1.f))};
+  V hx, hy, hz, a;
   if constexpr (PRECISE_H) {
+    static_assert(sizeof(V) == sizeof(float), "the double-float path takes one sample");
     const float4 p = half_vector_precise(wx, wy, wz, ax, ay, u1, u2);
     hx = p.x;
     hy = p.y;
@@ -74,42 +79,52 @@ __device__ __forceinline__ Reflected reflect_one(float wx, float wy, float wz, f
   } else {
     cap_half_vector(i, u1, u2, hx, hy, hz, a);
     // the condition check of sample_one<cap, PDF, PRECISE>
-    const float cx = fabsf(hx - i.x) + fabsf(i.x), cy = fabsf(hy - i.y) + fabsf(i.y);
-    const float vx = ax * hx, vy = ay * hy;
-    const float vv = fmaf(vx, vx, fmaf(vy, vy, hz * hz));
-    const float k2 = fmaf(ax * cx, ax * cx, fmaf(ay * cy, ay * cy, hz * hz));
-    const float kh2 = fmaf(cx, cx, fmaf(cy, cy, hz * hz));
-    const float hh = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
-    *bad = ok & ((k2 > kRescueKappa * kRescueKappa * vv) | (kh2 > kRescueKappa * kRescueKappa * hh));
+    const V cx = vadd(vabs(vsub(hx, i.x)), vabs(i.x)), cy = vadd(vabs(vsub(hy, i.y)), vabs(i.y));
+    const V vx = vmul(ax, hx), vy = vmul(ay, hy);
+    const V hz2 = vmul(hz, hz);
+    const V vv = vfma(vx, vx, vfma(vy, vy, hz2));
+    const V kx = vmul(ax, cx), ky = vmul(ay, cy);
+    const V k2 = vfma(kx, kx, vfma(ky, ky, hz2));
+    const V kh2 = vfma(cx, cx, vfma(cy, cy, hz2));
+    const V hh = vfma(hx, hx, vfma(hy, hy, hz2));
+    const V K2 = splat<V>(kRescueKappa * kRescueKappa);
+    *bad = ok & (vgt(k2, vmul(K2, vv)) | vgt(kh2, vmul(K2, hh)));
   }
-  const float vx = ax * hx, vy = ay * hy, vz = hz;
-  const float vv = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
-  const float rv = rsqrtf(vv);
-  const float mx = vx * rv, my = vy * rv, mz = vz * rv;
-  const float hh = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
-  const float wn2 = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
-  const float rw = rsqrtf(wn2);                      // 1 / |wi|
-  const float L = l2 * rl;
-  const float ux = wx * rw, uy = wy * rw, uz = wz * rw;  // unit wi
-  const float d = 0.5f * L * hh * rv * rw;           // wi.wm without cancellation
-  Reflected r;
-  r.ox = fmaf(2.f * d, mx, -ux);
-  r.oy = fmaf(2.f * d, my, -uy);
-  r.oz = fmaf(2.f * d, mz, -uz);
+  const V vx = vmul(ax, hx), vy = vmul(ay, hy), vz = hz;
+  const V vv = vfma(vx, vx, vfma(vy, vy, vmul(vz, vz)));
+  const V rv = vmap(RsqrtF{}, vv);
+  const V mx = vmul(vx, rv), my = vmul(vy, rv), mz = vmul(vz, rv);
+  const V hh = vfma(hx, hx, vfma(hy, hy, vmul(hz, hz)));
+  const V rw = vmap(RsqrtF{}, vfma(wx, wx, vfma(wy, wy, vmul(wz, wz))));  // 1 / |wi|
+  const V L = vmul(l2, rl);
+  const V ux = vmul(wx, rw), uy = vmul(wy, rw), uz = vmul(wz, rw);  // unit wi
+  const V d = vmul(vmul(vmul(vmul(splat<V>(0.5f), L), hh), rv), rw);  // wi.wm without cancellation
+  const V d2 = vmul(splat<V>(2.f), d);
+  ReflectedV<V> r;
+  r.ox = vfma(d2, mx, vneg(ux));
+  r.oy = vfma(d2, my, vneg(uy));
+  r.oz = vfma(d2, mz, vneg(uz));
   // PDF = |wi| |v|^4 / (2 pi ax ay L a |h|^4)
-  r.pdf = vv * vv * rcp_fast(2.f * kPi * ax * ay * L * a * hh * hh * rw);
+  V den = vmul(vmul(vmul(splat<V>(2.f * kPi), ax), ay), L);
+  den = vmul(vmul(vmul(vmul(den, a), hh), hh), rw);
+  r.pdf = vmul(vmul(vv, vv), vmap(RcpFast{}, den));
   // weight = F G2 / G1(wi) with G2 / G1 = (L_u + z_u) z_o / ((L_u + z_u) z_o + z_u P_o / (L_o + z_o))
-  const float A = fmaf(L, rw, uz);                   // |M^-1 wi_unit| + wi_unit.z
-  const float px = ax * r.ox, py = ay * r.oy;
-  const float po = fmaf(px, px, py * py);
-  const float lo = sqrt_fast(fmaf(r.oz, r.oz, po));
-  const float num = A * r.oz;
-  const float g = num * rcp_fast(fmaf(uz * po, rcp_fast(lo + r.oz), num));
-  const float t = 1.f - d;
-  const float t2 = t * t;
-  const float fr = fmaf(1.f - f0, t2 * t2 * t, f0);
-  r.weight = r.oz > 0.f ? fr * g : 0.f;
-  if (!ok) r = Reflected{0.f, 0.f, 1.f, 0.f, 0.f};
+  const V A = vfma(L, rw, uz);  // |M^-1 wi_unit| + wi_unit.z
+  const V px = vmul(ax, r.ox), py = vmul(ay, r.oy);
+  const V po = vfma(px, px, vmul(py, py));
+  const V lo = vmap(SqrtFast{}, vfma(r.oz, r.oz, po));
+  const V num = vmul(A, r.oz);
+  const V g = vmul(num, vmap(RcpFast{}, vfma(vmul(uz, po), vmap(RcpFast{}, vadd(lo, r.oz)), num)));
+  const V t = vsub(splat<V>(1.f), d);
+  const V t2 = vmul(t, t);
+  const V fr = vfma(splat<V>(1.f - f0), vmul(vmul(t2, t2), t), splat<V>(f0));
+  r.weight = vsel(vgt(r.oz, splat<V>(0.f)), vmul(fr, g), splat<V>(0.f));
+  // out-of-domain inputs: wo = (0, 0, 1), pdf = weight = 0
+  r.ox = vsel(ok, r.ox, splat<V>(0.f));
+  r.oy = vsel(ok, r.oy, splat<V>(0.f));
+  r.oz = vsel(ok, r.oz, splat<V>(1.f));
+  r.pdf = vsel(ok, r.pdf, splat<V>(0.f));
+  r.weight = vsel(ok, r.weight, splat<V>(0.f));
   return r;
 }
 
@@ -185,16 +200,29 @@ __global__ void __launch_bounds__(kReflBlock, 3) reflect_pipe_kernel(ReflArgs a,
     float OX[4], OY[4], OZ[4], P[4], Wt[4];
     unsigned rescue = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      bool bad;
-      Reflected r = reflect_one<false>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], a.f0, &bad);
-      if (!kBatched && bad) r = reflect_one<true>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], a.f0, nullptr);
-      rescue |= unsigned(bad) << k;
-      OX[k] = r.ox;
-      OY[k] = r.oy;
-      OZ[k] = r.oz;
-      P[k] = r.pdf;
-      Wt[k] = r.weight;
+    for (int k = 0; k < 4; k += 2) {  // two packed pairs
+      bool2 bad;
+      const ReflectedV<float2> r = reflect_one<false>(lanes(X, k), lanes(Y, k), lanes(Z, k), lanes(AX, k),
+                                                      lanes(AY, k), lanes(U1, k), lanes(U2, k), a.f0, &bad);
+      set_lanes(OX, k, r.ox);
+      set_lanes(OY, k, r.oy);
+      set_lanes(OZ, k, r.oz);
+      set_lanes(P, k, r.pdf);
+      set_lanes(Wt, k, r.weight);
+      rescue |= (unsigned(bad.x) << k) | (unsigned(bad.y) << (k + 1));
+    }
+    if constexpr (!kBatched) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (rescue & (1u << k)) {  // rare: redone in place
+          const Reflected r =
+              reflect_one<true>(X[k], Y[k], Z[k], AX[k], AY[k], U1[k], U2[k], a.f0, static_cast<bool*>(nullptr));
+          OX[k] = r.ox;
+          OY[k] = r.oy;
+          OZ[k] = r.oz;
+          P[k] = r.pdf;
+          Wt[k] = r.weight;
+        }
     }
     if (active) {
       st_stream(a.ox + e, *reinterpret_cast<float4*>(OX));
