@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kBwdBlock) backward_scalar_kernel(BwdArgs a, i
       a.gwy[e] = g.wy;
       a.gwz[e] = g.wz;
     }
-    if (a.gax) a.gax[e] = ISO ? g.ax + g.ay : g.ax;
+    if (a.gax) a.gax[e] = ISO ? vadd(g.ax, g.ay) : g.ax;
     if (!ISO && a.gay) a.gay[e] = g.ay;
   }
 }

@@ -93,13 +93,19 @@ __global__ void __launch_bounds__(kFitBlock, 4) fit_kernel(FitArgs a) {
         ku2[k] = u2[k];
       }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        float mx, my, mz, p;
-        sample_one<kMethodCap, false>(wx, wy, wz, ax, ay, u1[k], u2[k], mx, my, mz, p);
+      for (int k = 0; k < 4; k += 2) {  // two packed pairs, added in sample order
+        float2 mx, my, mz, p;
+        sample_one<kMethodCap, false>(splat<float2>(wx), splat<float2>(wy), splat<float2>(wz), splat<float2>(ax),
+                                      splat<float2>(ay), lanes(u1, k), lanes(u2, k), mx, my, mz, p);
         if (j0 + k < a.ns) {
-          sum.x += mx;
-          sum.y += my;
-          sum.z += mz;
+          sum.x += mx.x;
+          sum.y += my.x;
+          sum.z += mz.x;
+        }
+        if (j0 + k + 1 < a.ns) {
+          sum.x += mx.y;
+          sum.y += my.y;
+          sum.z += mz.y;
         }
       }
     }
@@ -121,13 +127,19 @@ __global__ void __launch_bounds__(kFitBlock, 4) fit_kernel(FitArgs a) {
         uniforms2(rt, uint64_t(j0 + 2), u1[2], u2[2], u1[3], u2[3]);
       }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        float mx, my, mz, p;
-        const Grad5 g = cap_backward_one<false>(wx, wy, wz, ax, ay, u1[k], u2[k], gx, gy, gz, 0.f, 0.f, mx, my,
-                                                mz, p);
+      for (int k = 0; k < 4; k += 2) {  // two packed pairs, added in sample order
+        float2 mx, my, mz, p;
+        const Grad5V<float2> g = cap_backward_one<false>(
+            splat<float2>(wx), splat<float2>(wy), splat<float2>(wz), splat<float2>(ax), splat<float2>(ay),
+            lanes(u1, k), lanes(u2, k), splat<float2>(gx), splat<float2>(gy), splat<float2>(gz), splat<float2>(0.f),
+            splat<float2>(0.f), mx, my, mz, p);
         if (j0 + k < a.ns) {
-          ga.x += g.ax;
-          ga.y += g.ay;
+          ga.x += g.ax.x;
+          ga.y += g.ay.x;
+        }
+        if (j0 + k + 1 < a.ns) {
+          ga.x += g.ax.y;
+          ga.y += g.ay.y;
         }
       }
     }

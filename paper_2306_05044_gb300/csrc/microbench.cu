@@ -40,9 +40,13 @@ __global__ void __launch_bounds__(kMicroBlock) microbench_kernel(int64_t lanes, 
     for (int32_t j = 0; j < spl; j += 2) {
       float a1, a2, b1, b2;
       uniforms2(r, j0 + uint64_t(j), a1, a2, b1, b2);
-      float mx, my, mz, p, nx, ny, nz, q;
-      const bool ra = sample_one<METHOD, true, PRECISE>(wx, wy, wz, ax, ay, a1, a2, mx, my, mz, p);
-      const bool rb = sample_one<METHOD, true, PRECISE>(wx, wy, wz, ax, ay, b1, b2, nx, ny, nz, q);
+      // the two samples as one packed pair (same bits as two single-sample calls)
+      float2 m2x, m2y, m2z, p2;
+      const bool2 rr = sample_one<METHOD, true, PRECISE>(splat<float2>(wx), splat<float2>(wy), splat<float2>(wz),
+                                                         splat<float2>(ax), splat<float2>(ay), make_float2(a1, b1),
+                                                         make_float2(a2, b2), m2x, m2y, m2z, p2);
+      float mx = m2x.x, my = m2y.x, mz = m2z.x, p = p2.x, nx = m2x.y, ny = m2y.y, nz = m2z.y, q = p2.y;
+      const bool ra = rr.x, rb = rr.y;
       if constexpr (METHOD == kMethodCap && PRECISE) {
         if (ra) {
           const float4 r = sample_one_precise<true>(wx, wy, wz, ax, ay, a1, a2);
