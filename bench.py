@@ -383,7 +383,7 @@ def cpu_baseline(budget_s=15.0):
             "sample": f"{chunks} chunks of {m} samples of the anisotropic workload recipe (one seed per chunk), "
                       f"FP64 numpy oracle (Philox + cap sampler + pdf), one process per core, {wall:.1f} s of "
                       f"oracle time on the busiest core",
-            "sample_short": f"{chunks}x2^20 samples of the workload recipe, FP64 numpy oracle, {pool.cores} "
+            "sample_short": f"{chunks}x2^20 workload samples, FP64 numpy oracle, {pool.cores} "
                             f"processes, {wall:.0f} s"}
 
 
@@ -433,7 +433,7 @@ def compact_line(r):
                               "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "gpu_launches")}
     rf = r["roofline"]
     line["roofline"] = {k: rf[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
-    line["roofline"]["kernel"] = "sample_pipe_kernel (cap, Philox, anisotropic, pdf)"
+    line["roofline"]["kernel"] = "sample_pipe_kernel<cap,philox,aniso,pdf>"
     if r.get("device"):
         line["device"] = r["device"]
     if r.get("rescued_frac") is not None:
@@ -472,11 +472,15 @@ def compact_line(r):
         line["e2e"]["how"] = "zero_copy" if e.get("alternatives", {}).get("zero_copy") is not None and \
             e["value"] == e["alternatives"]["zero_copy"]["value"] else "copy_pipeline"
         line["e2e"]["alternatives"] = {k: (v or {}).get("value") for k, v in e.get("alternatives", {}).items()}
+        if e.get("host_link"):
+            hl = e["host_link"]
+            line["e2e"]["host_link"] = {"achieved_gbs": hl["achieved_gbs"], "both_gbs": hl["both_gbs"],
+                                        "frac": hl["frac"]}
     if "cpu_baseline" in r:
         cb = r["cpu_baseline"]
         line["cpu_baseline"] = dict(cb, sample=cb.get("sample_short", cb["sample"]))
         line["cpu_baseline"].pop("sample_short", None)
-    line["detail"] = "full record of every leg on stderr"
+    line["detail"] = "stderr"
     return _sig(line)
 
 
@@ -585,7 +589,7 @@ def run_ours(args, rank, world):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "samples_per_gpu": n, "method": "spherical_cap", "rng": "philox4x32-10 in-kernel",
                    "alpha": "log-uniform [1e-3, 1] x, y independent", "cos_theta_i": "uniform [1e-4, 1]",
-                   "l2": "inputs larger than L2 (9.66 GB touched per step); no flush",
+                   "l2": "inputs > L2 (9.66 GB per step), no flush",
                    "parallelism": f"index-range shards x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": f"{peak_kind} copy bandwidth",
@@ -671,6 +675,9 @@ def run_ours(args, rank, world):
         direct = e2e_zero_copy(vndf, d, n, base, dev, stream, steps, warm, barrier, world)
         best = max((x for x in (piped, direct) if x is not None), key=lambda x: x["value"])
         result["e2e"] = dict(best, alternatives={"copy_pipeline": piped, "zero_copy": direct})
+        link = host_link(dev)
+        moved = (best["h2d_bytes_per_step"] + best["d2h_bytes_per_step"]) / (best["ms_per_step"] * 1e-3) / 1e9
+        result["e2e"]["host_link"] = dict(link, achieved_gbs=moved, frac=moved / link["both_gbs"])
 
     if rank == 0 and not args.no_cpu_protocol:
         result["cpu_protocol"] = cpu_protocol(vndf)
@@ -977,6 +984,46 @@ def e2e(vndf, d, n, base, dev, stream, steps, warm, barrier, world):
     return {"value": world * n * steps / (total * 1e-3) / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": 20 * n, "d2h_bytes_per_step": 16 * n,
             "ms_per_step": total / steps, "pipeline": f"{nstreams} streams, {chunk}-sample chunks, pinned host memory"}
+
+
+def host_link(dev, nbytes=1 << 28, reps=5):
+    """Ceiling of the end-to-end step: the copy engines' host<->device bandwidth over the host link (pinned
+    host memory), host-to-device alone, device-to-host alone and both directions at once (GB/s)."""
+    import torch
+    hb = [torch.empty(nbytes, dtype=torch.uint8).pin_memory() for _ in range(2)]
+    db = [torch.empty(nbytes, dtype=torch.uint8, device=dev) for _ in range(2)]
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def rate(fn, moved):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return moved * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+    def h2d():
+        db[0].copy_(hb[0], non_blocking=True)
+
+    def d2h():
+        hb[1].copy_(db[1], non_blocking=True)
+
+    def both():
+        cur = torch.cuda.current_stream(dev)
+        s1.wait_stream(cur)
+        s2.wait_stream(cur)
+        with torch.cuda.stream(s1):
+            h2d()
+        with torch.cuda.stream(s2):
+            d2h()
+        cur.wait_stream(s1)
+        cur.wait_stream(s2)
+
+    return {"h2d_gbs": rate(h2d, nbytes), "d2h_gbs": rate(d2h, nbytes), "both_gbs": rate(both, 2 * nbytes),
+            "how": f"copy engines, {nbytes >> 20} MiB pinned buffers, {reps} copies each"}
 
 
 def e2e_zero_copy(vndf, d, n, base, dev, stream, steps, warm, barrier, world):

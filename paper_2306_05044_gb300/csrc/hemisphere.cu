@@ -20,8 +20,8 @@
 #define VNDF_RESCUE_BATCHED 1
 #endif
 // Grid of the streaming kernel: at most this many waves of 8 CTAs per SM.
-#ifndef VNDF_SAMPLE_WAVES
-#define VNDF_SAMPLE_WAVES 4
+#ifndef VNDF_HEMI_WAVES
+#define VNDF_HEMI_WAVES 4
 #endif
 
 namespace vndf {
@@ -183,7 +183,7 @@ int launch_hemi(const HemiArgs& a, int64_t n, bool vec, cudaStream_t s) {
     constexpr size_t smem =
         size_t(2) * hemi_streams_in<PHILOX>() * kHemiBlock * 16 + (kHemiBlock / 32) * sizeof(RescueQueue);
     if (!ensure_dynamic_smem<hemi_pipe_kernel<PHILOX, PDF>>(smem)) return VNDF_ERR_CUDA;
-    if (!launch_pdl(hemi_pipe_kernel<PHILOX, PDF>, grid_for(n4, kHemiBlock, 8, VNDF_SAMPLE_WAVES), kHemiBlock, smem, s,
+    if (!launch_pdl(hemi_pipe_kernel<PHILOX, PDF>, grid_for(n4, kHemiBlock, 8, VNDF_HEMI_WAVES), kHemiBlock, smem, s,
                     a, n4))
       return VNDF_ERR_CUDA;
     done = 4 * n4;

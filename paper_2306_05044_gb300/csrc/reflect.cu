@@ -26,8 +26,8 @@
 #define VNDF_RESCUE_BATCHED 1
 #endif
 // Grid of the streaming kernel: at most this many waves of 8 CTAs per SM.
-#ifndef VNDF_SAMPLE_WAVES
-#define VNDF_SAMPLE_WAVES 4
+#ifndef VNDF_REFL_WAVES
+#define VNDF_REFL_WAVES 4
 #endif
 
 namespace vndf {
@@ -277,7 +277,7 @@ int launch_reflect(const ReflArgs& a, int64_t n, bool vec, cudaStream_t s) {
     constexpr size_t smem =
         size_t(2) * streams_in<PHILOX, ISO>() * kReflBlock * 16 + (kReflBlock / 32) * sizeof(RescueQueue);
     if (!ensure_dynamic_smem<reflect_pipe_kernel<PHILOX, ISO>>(smem)) return VNDF_ERR_CUDA;
-    if (!launch_pdl(reflect_pipe_kernel<PHILOX, ISO>, grid_for(n4, kReflBlock, 8, VNDF_SAMPLE_WAVES), kReflBlock, smem,
+    if (!launch_pdl(reflect_pipe_kernel<PHILOX, ISO>, grid_for(n4, kReflBlock, 8, VNDF_REFL_WAVES), kReflBlock, smem,
                     s, a, n4))
       return VNDF_ERR_CUDA;
     done = 4 * n4;

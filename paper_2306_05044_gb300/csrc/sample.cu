@@ -20,17 +20,21 @@
 #ifndef VNDF_SAMPLE_MIN_BLOCKS
 #define VNDF_SAMPLE_MIN_BLOCKS 3
 #endif
-// Grid of the staged streaming kernel: at most this many waves of 8 CTAs per SM (3 are resident).
-// Measured at 2^28 samples on GB300: 4 waves 1444 us (cap) / 1624 us (extended domain), 8 waves
-// 1428 / 1589, 16 waves 1411 / 1524, 20 waves 1409 / 1499, 24 waves 1420 / 1504, 32 waves 1452 / 1533
-// (launches alone); in the bench loop the cap sampler timed 1410-1414 us at 16 waves and 1421 at 20.
-// Smaller CTA shares balance the tail and let each CTA's final recomputation of its ill-conditioned
-// samples overlap other CTAs' streaming; the extended domain, with six times more of them, gains most.
+// Grid of the staged streaming kernel: at most this many waves of 8 CTAs per SM (3 are resident), per
+// method.  Measured at 2^28 samples on GB300 (launches alone, packed-pair kernels): cap 16 / 20 / 24 / 28 /
+// 32 waves 1405 / 1394 / 1389 / 1382 / 1390 us; prior 6 / 8 / 10 / 12 / 16 waves 1425 / 1428 / 1430 / 1432 /
+// 1436 us; extended domain 20 / 28 / 32 / 36 / 40 waves 1488 / 1451 / 1465 / 1494 / 1495 us.  Smaller CTA
+// shares balance the tail and let each CTA's final recomputation of its ill-conditioned samples overlap
+// other CTAs' streaming; the prior sampler recomputes nothing and prefers longer runs.  Calls below about
+// 2^27 samples take the small-call grid instead (about four groups per thread).
 #ifndef VNDF_SAMPLE_WAVES
-#define VNDF_SAMPLE_WAVES 16
+#define VNDF_SAMPLE_WAVES 28
 #endif
 #ifndef VNDF_SAMPLE_WAVES_EXT
-#define VNDF_SAMPLE_WAVES_EXT 20
+#define VNDF_SAMPLE_WAVES_EXT 28
+#endif
+#ifndef VNDF_SAMPLE_WAVES_POLAR
+#define VNDF_SAMPLE_WAVES_POLAR 6
 #endif
 #ifndef VNDF_SAMPLE_PREFETCH
 #define VNDF_SAMPLE_PREFETCH 1
@@ -282,7 +286,9 @@ int launch_sample(const SampleArgs& a, int64_t n, bool vec, cudaStream_t s) {
       // graph at 2^20 samples: 456 CTAs 6.86 us, 304 CTAs 7.10, 256 CTAs 7.8; at 2^22 (eager) three
       // groups per thread took 30.45 us against 30.22 with four, at 2^24 103.4 against 100.5.
       unsigned grid = grid_for(n4, kSampleBlock, 2048 / kSampleBlock,
-                               METHOD == kMethodCapExt ? VNDF_SAMPLE_WAVES_EXT : VNDF_SAMPLE_WAVES);
+                               METHOD == kMethodCapExt  ? VNDF_SAMPLE_WAVES_EXT
+                               : METHOD == kMethodPolar ? VNDF_SAMPLE_WAVES_POLAR
+                                                        : VNDF_SAMPLE_WAVES);
       const int64_t iters = VNDF_SAMPLE_MIN_ITERS - (n4 <= (int64_t(1) << 19) ? 1 : 0);
       if (iters > 1) {
         const int64_t per_iters = (n4 + int64_t(kSampleBlock) * iters - 1) / (int64_t(kSampleBlock) * iters);

@@ -68,7 +68,7 @@ def _full_record():
     r["config"] = {"workload": bench.WORKLOAD, "samples_per_gpu": 1 << 28, "method": "spherical_cap",
                    "rng": "philox4x32-10 in-kernel", "alpha": "log-uniform [1e-3, 1] x, y independent",
                    "cos_theta_i": "uniform [1e-4, 1]",
-                   "l2": "inputs larger than L2 (9.66 GB touched per step); no flush",
+                   "l2": "inputs > L2 (9.66 GB per step), no flush",
                    "parallelism": "index-range shards x1"}
     r["clocks"] = clock
     r["fwd_bwd"] = {"2e24": fb(), "2e26": fb()}
@@ -86,7 +86,9 @@ def _full_record():
     r["cpu_protocol"] = {"threads_1": row, "threads_16": row, "paper_reference": "p"}
     e = {"value": 9.3 + x, "unit": "Gsamples/s", "h2d_bytes_per_step": 20 << 28, "d2h_bytes_per_step": 16 << 28,
          "ms_per_step": 28.9 + x, "pipeline": "zero copy"}
-    r["e2e"] = dict(e, alternatives={"copy_pipeline": dict(e, value=7.4 + x), "zero_copy": e})
+    r["e2e"] = dict(e, alternatives={"copy_pipeline": dict(e, value=7.4 + x), "zero_copy": e},
+                    host_link={"h2d_gbs": 210.9 + x, "d2h_gbs": 193.2 + x, "both_gbs": 339.3 + x,
+                               "how": "copy engines", "achieved_gbs": 332.3 + x, "frac": 0.979 + x / 100})
     r["cpu_baseline"] = {"value": 0.0497 + x / 1000, "unit": "Gsamples/s", "cores": 16, "kind": "oracle",
                          "sample": "x" * 300, "sample_short": "1424x2^20 samples, FP64 numpy oracle, 16 processes"}
     return r
@@ -98,7 +100,7 @@ def test_printed_line_is_short_and_complete():
     import json
     line = bench.compact_line(_full_record())
     text = json.dumps(line, separators=(",", ":"))
-    assert len(text) < 2800, len(text)
+    assert len(text) < 2700, len(text)
     keys = list(line)
     assert keys[:13] == ["metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
                          "scaling", "vs_baseline", "dtype", "data", "gpu_launches"]
@@ -106,6 +108,7 @@ def test_printed_line_is_short_and_complete():
               "cpu_baseline"):
         assert k in line, k
     assert set(line["fwd_bwd"]) == {"2e24", "2e26"}
+    assert set(line["e2e"]["host_link"]) == {"achieved_gbs", "both_gbs", "frac"}
     for leg in (line["fwd_bwd"]["2e24"], line["albedo"], line["extended"]["sphere"]):
         assert leg["issue"] is not None and leg["mhz"] == 2070.0
     assert line["fwd_bwd"]["2e26"]["hbm"] is not None
