@@ -77,8 +77,8 @@ __device__ __forceinline__ float2 vmap(F f, float2 x) { return make_float2(f(x.x
 struct bool2 {
   bool x, y;
 };
-__device__ __forceinline__ bool2 operator&(bool2 a, bool2 b) { return {a.x && b.x, a.y && b.y}; }
-__device__ __forceinline__ bool2 operator|(bool2 a, bool2 b) { return {a.x || b.x, a.y || b.y}; }
+__device__ __forceinline__ bool2 operator&(bool2 a, bool2 b) { return {bool(a.x & b.x), bool(a.y & b.y)}; }
+__device__ __forceinline__ bool2 operator|(bool2 a, bool2 b) { return {bool(a.x | b.x), bool(a.y | b.y)}; }
 __device__ __forceinline__ bool2& operator&=(bool2& a, bool2 b) { return a = a & b; }
 
 template <typename V>
