@@ -547,21 +547,28 @@ def run_ours(args, rank, world):
         if world > 1:
             torch.distributed.barrier()
 
-    def timed(fn, steps, warmup, clocks=True):
+    def timed(fn, steps, warmup, clocks=True, per_step=False):
+        """Device time of `steps` calls of fn after `warmup` untimed ones: CUDA events before the first and
+        after the last call, on the launching stream.  With per_step, an event after every call too (the
+        per-step times); those events sit between the launches and cost a short step a few microseconds (the
+        next launch no longer overlaps the one before), so the timed legs go without them."""
         for _ in range(warmup):
             fn()
         barrier()
         sampler = ClockSampler(dev) if clocks and not args.no_clocks else None
         if sampler:
             sampler.start()
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1 if per_step else 2)]
         evs[0].record(stream)
         for k in range(steps):
             fn()
-            evs[k + 1].record(stream)
+            if per_step:
+                evs[k + 1].record(stream)
+        if not per_step:
+            evs[-1].record(stream)
         barrier()
         clock = sampler.stop() if sampler else None
-        per = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+        per = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)] if per_step else []
         total = sharding.max_over_ranks(evs[0].elapsed_time(evs[-1]), dev)
         return total, per, clock
 
@@ -600,8 +607,11 @@ def run_ours(args, rank, world):
                   f"{torch.cuda.get_device_properties(dev).multi_processor_count} SMs",
         "rescued_frac": rescued_frac,
         "clocks": clock,
-        "per_step_ms": {"min": min(per), "median": statistics.median(per), "max": max(per)},
     }
+    # per-step spread from a separate pass with an event after every step (not part of the timed value)
+    _, per, _ = timed(step, min(steps, 20), 1, clocks=False, per_step=True)
+    result["per_step_ms"] = {"min": min(per), "median": statistics.median(per), "max": max(per),
+                             "note": "separate pass with an event after every step"}
 
     if not args.no_prior:
         ptotal, pper, pclock = timed(lambda: step("polar"), steps, warm)
