@@ -3,9 +3,9 @@
 // seen from a direction wi, normalised (the normalisation Sec. 3.3 says a
 // stand-alone use needs) and with the density of Eq. 2.  With alpha = 1 the
 // GGX NDF is D_std and M is the identity, so this is the extended-domain cap
-// sampler of vndf_math.cuh with both roughnesses fixed to 1: the compiler
-// folds the stretch away and the kernel streams 12 bytes in and 16 out per
-// sample (Philox mode).  Ill-conditioned samples (|h| small against its
+// sampler of vndf_math.cuh with both roughnesses fixed to 1 (UnitAlpha: the
+// products with them vanish at compile time), and the kernel streams 12 bytes
+// in and 16 out per sample (Philox mode).  Ill-conditioned samples (|h| small against its
 // summands) are redone in double-float as in vndf_sample, batched per warp.
 #include <cuda_runtime.h>
 
@@ -52,7 +52,7 @@ __device__ __forceinline__ void hemi_stage(const HemiArgs& a, int64_t e, float4*
 template <bool PDF>
 __device__ __forceinline__ float4 hemi_one(float wx, float wy, float wz, float u1, float u2) {
   float4 r;
-  if (sample_one<kMethodCapExt, PDF, true>(wx, wy, wz, 1.f, 1.f, u1, u2, r.x, r.y, r.z, r.w))
+  if (sample_one<kMethodCapExt, PDF, true>(wx, wy, wz, UnitAlpha{}, UnitAlpha{}, u1, u2, r.x, r.y, r.z, r.w))
     r = sample_one_precise<PDF, true>(wx, wy, wz, 1.f, 1.f, u1, u2);
   return r;
 }
@@ -114,9 +114,8 @@ __global__ void __launch_bounds__(kHemiBlock, 3) hemi_pipe_kernel(HemiArgs a, in
 #pragma unroll
     for (int k = 0; k < 4; k += 2) {  // two packed pairs
       float2 mx, my, mz, p;
-      const bool2 b = sample_one<kMethodCapExt, PDF, true>(lanes(X, k), lanes(Y, k), lanes(Z, k), splat<float2>(1.f),
-                                                           splat<float2>(1.f), lanes(U1, k), lanes(U2, k), mx, my,
-                                                           mz, p);
+      const bool2 b = sample_one<kMethodCapExt, PDF, true>(lanes(X, k), lanes(Y, k), lanes(Z, k), UnitAlpha{},
+                                                           UnitAlpha{}, lanes(U1, k), lanes(U2, k), mx, my, mz, p);
       set_lanes(MX, k, mx);
       set_lanes(MY, k, my);
       set_lanes(MZ, k, mz);

@@ -60,6 +60,14 @@ __device__ __forceinline__ float2 vsub(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
 
+// A roughness known to be 1 at compile time (the hemisphere configuration): products with it are the
+// other factor, with no instruction (an inline-PTX multiply by 1 would not be folded away).
+struct UnitAlpha {};
+__device__ __forceinline__ float vmul(UnitAlpha, float x) { return x; }
+__device__ __forceinline__ float2 vmul(UnitAlpha, float2 x) { return x; }
+__device__ __forceinline__ float vmul(float x, UnitAlpha) { return x; }
+__device__ __forceinline__ float2 vmul(float2 x, UnitAlpha) { return x; }
+
 template <typename V>
 __device__ __forceinline__ V splat(float a);
 template <>

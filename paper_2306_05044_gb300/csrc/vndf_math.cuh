@@ -156,8 +156,23 @@ __device__ __forceinline__ bool2 in_domain_ext_inputs(float2 wx, float2 wy, floa
   return {in_domain_ext_inputs(wx.x, wy.x, wz.x, ax.x, ay.x), in_domain_ext_inputs(wx.y, wy.y, wz.y, ax.y, ay.y)};
 }
 
-template <int METHOD, typename V>
-__device__ __forceinline__ Mask<V> in_domain_m(V wx, V wy, V wz, V ax, V ay) {
+// With both roughnesses 1 (UnitAlpha) only the direction is tested.
+__device__ __forceinline__ bool in_domain(float wx, float wy, float wz, UnitAlpha, UnitAlpha) {
+  return (wz > 0.f) & finite_f(wx) & finite_f(wy) & finite_f(wz);
+}
+__device__ __forceinline__ bool in_domain_ext_inputs(float wx, float wy, float wz, UnitAlpha, UnitAlpha) {
+  return finite_f(wx) & finite_f(wy) & finite_f(wz);
+}
+__device__ __forceinline__ bool2 in_domain(float2 wx, float2 wy, float2 wz, UnitAlpha u, UnitAlpha) {
+  return {in_domain(wx.x, wy.x, wz.x, u, u), in_domain(wx.y, wy.y, wz.y, u, u)};
+}
+__device__ __forceinline__ bool2 in_domain_ext_inputs(float2 wx, float2 wy, float2 wz, UnitAlpha u, UnitAlpha) {
+  return {in_domain_ext_inputs(wx.x, wy.x, wz.x, u, u), in_domain_ext_inputs(wx.y, wy.y, wz.y, u, u)};
+}
+
+// A (the roughness type) is V, or UnitAlpha for the hemisphere configuration.
+template <int METHOD, typename V, typename A>
+__device__ __forceinline__ Mask<V> in_domain_m(V wx, V wy, V wz, A ax, A ay) {
   if constexpr (METHOD == kMethodCapExt)
     return in_domain_ext_inputs(wx, wy, wz, ax, ay);
   else
@@ -178,8 +193,8 @@ using Stretched = StretchedV<float>;
 // a is formed by one fma rather than as 1 + (the rounded i.z): an add whose
 // operand is a packed product used nowhere else may be fused into an fma by the
 // assembler, which would round the two widths differently.
-template <typename V>
-__device__ __forceinline__ StretchedV<V> stretch(V wx, V wy, V wz, V ax, V ay) {
+template <typename V, typename A>
+__device__ __forceinline__ StretchedV<V> stretch(V wx, V wy, V wz, A ax, A ay) {
   const V sx = vmul(ax, wx), sy = vmul(ay, wy);
   const V r = vmap(RsqrtF{}, vfma(sx, sx, vfma(sy, sy, vmul(wz, wz))));
   return {vmul(sx, r), vmul(sy, r), vmul(wz, r), vfma(wz, r, splat<V>(1.f))};
@@ -258,8 +273,8 @@ __device__ __forceinline__ void polar_disk_normal(const StretchedV<V>& i, V u1, 
 constexpr float kRescueKappa = 24.f;
 
 // The FP32 tail of a sample: unstretch h, normalise, and (if PDF) the fused density.
-template <int METHOD, bool PDF, typename V>
-__device__ __forceinline__ void finish_sample(const StretchedV<V>& i, V ax, V ay, V hx, V hy, V hz, V a, V& mx,
+template <int METHOD, bool PDF, typename V, typename A>
+__device__ __forceinline__ void finish_sample(const StretchedV<V>& i, A ax, A ay, V hx, V hy, V hz, V a, V& mx,
                                               V& my, V& mz, V& pdf) {
   const V vx = vmul(ax, hx), vy = vmul(ay, hy), vz = hz;
   const V vv = vfma(vx, vx, vfma(vy, vy, vmul(vz, vz)));
@@ -290,8 +305,8 @@ __device__ __forceinline__ void finish_sample(const StretchedV<V>& i, V ax, V ay
 // returned mask flags ill-conditioned samples whose results must be replaced
 // by sample_one_precise; the check costs a few FP32 operations and keeps the
 // rare slow path out of the unrolled loop.
-template <int METHOD, bool PDF, bool PRECISE = false, typename V>
-__device__ __forceinline__ Mask<V> sample_one(V wx, V wy, V wz, V ax, V ay, V u1, V u2, V& mx, V& my, V& mz,
+template <int METHOD, bool PDF, bool PRECISE = false, typename V, typename A>
+__device__ __forceinline__ Mask<V> sample_one(V wx, V wy, V wz, A ax, A ay, V u1, V u2, V& mx, V& my, V& mz,
                                               V& pdf) {
   Mask<V> ok = in_domain_m<METHOD>(wx, wy, wz, ax, ay);
   const StretchedV<V> i = stretch(wx, wy, wz, ax, ay);
