@@ -144,23 +144,17 @@ __device__ __forceinline__ QueryConst query_const(const AlbedoArgs& a, int32_t q
   return c;
 }
 
-// Estimator terms of two samples (x = 2 u1 and u2 of each in the halves of a
-// float2): F G2 / G1(wi), or 0 when wo is below the surface.  The FP32 fma / mul
-// / add run as packed pairs (pair.cuh), every lane rounded as in the scalar form
-// of the same steps; square roots, reciprocals and the final select per lane.
-__device__ __forceinline__ float2 albedo_weight2(const QueryConst& c, float f0, float2 x, float2 u2) {
+// Estimator terms of two samples (u1, u2 of each in the halves of a float2):
+// F G2 / G1(wi), or 0 when wo is below the surface.  The cap sample is the
+// sampler's own (cap_half_vector); the FP32 fma / mul / add run as packed pairs
+// (pair.cuh), every lane rounded as in the one-sample form of the same steps;
+// square roots, reciprocals and the final select per lane.
+__device__ __forceinline__ float2 albedo_weight2(const QueryConst& c, float f0, float2 u1, float2 u2) {
   using V = float2;
-  // the cap sample (cap_half_vector with i = c.i), h = (hx, hy, hz)
-  const float rho2 = fmaf(c.i.x, c.i.x, c.i.y * c.i.y);
-  const float a = c.i.a;  // 1 + i.z, as in the sampler
-  const V om = vsub(splat<V>(1.f), u2);
-  const V sin2 = vmul(u2, vfma(splat<V>(2.f * a), om, vmul(u2, splat<V>(rho2))));
-  const V st = vmap(SqrtFast{}, sin2);
-  V sp, cp;
-  sincospi_taylor(x, sp, cp);
-  const V hx = vfma(st, cp, splat<V>(c.i.x));
-  const V hy = vfma(st, sp, splat<V>(c.i.y));
-  const V hz = vmul(om, splat<V>(a));
+  // the cap sample of Sec. 3.3 for both samples, h = (hx, hy, hz)
+  const StretchedV<V> i{splat<V>(c.i.x), splat<V>(c.i.y), splat<V>(c.i.z), splat<V>(c.i.a)};
+  V hx, hy, hz, a;
+  cap_half_vector(i, u1, u2, hx, hy, hz, a);
   // wm = v / |v| with v = (ax hx, ay hy, hz), and wo = 2 (wi.wm) wm - wi
   const V vx = vmul(splat<V>(c.ax), hx), vy = vmul(splat<V>(c.ay), hy);
   const V rv = vmap(RsqrtF{}, vfma(vx, vx, vfma(vy, vy, vmul(hz, hz))));
@@ -274,7 +268,7 @@ __global__ void __launch_bounds__(32 * kAlbedoMaxWarps, 1) albedo_kernel(AlbedoA
       if ((g + 1) * kGroupSamples <= n) {  // a full group (warp-uniform): no per-sample bound
 #pragma unroll
         for (int s = 0; s < kLaneSamples; s += 2) {
-          const float2 w = albedo_weight2(c, a.f0, make_float2(2.f * U1[s], 2.f * U1[s + 1]),
+          const float2 w = albedo_weight2(c, a.f0, make_float2(U1[s], U1[s + 1]),
                                           make_float2(U2[s], U2[s + 1]));
           acc += w.x;
           acc += w.y;
@@ -282,7 +276,7 @@ __global__ void __launch_bounds__(32 * kAlbedoMaxWarps, 1) albedo_kernel(AlbedoA
       } else {
 #pragma unroll
         for (int s = 0; s < kLaneSamples; s += 2) {
-          const float2 w = albedo_weight2(c, a.f0, make_float2(2.f * U1[s], 2.f * U1[s + 1]),
+          const float2 w = albedo_weight2(c, a.f0, make_float2(U1[s], U1[s + 1]),
                                           make_float2(U2[s], U2[s + 1]));
           acc += j0 + s < n ? w.x : 0.f;
           acc += j0 + s + 1 < n ? w.y : 0.f;
