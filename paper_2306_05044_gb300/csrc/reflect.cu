@@ -142,10 +142,13 @@ __device__ __forceinline__ void refl_stage(const ReflArgs& a, int64_t e, float4*
   }
 }
 
-// Four samples per thread per grid-stride step, inputs staged two steps deep;
-// ill-conditioned samples are queued per warp and redone 32 at a time (rescue.cuh).
+// Four samples per thread per grid-stride step (two packed pairs), inputs staged two steps deep;
+// ill-conditioned samples are queued per warp and redone 32 at a time (rescue.cuh).  Two CTAs per SM:
+// the register file then holds both pairs' reflection and weight arithmetic without spilling (124
+// registers); measured at 2^28 with weights, 1633 us against 1653 us at three CTAs (80 registers, 16-28
+// bytes of spills) and 1670 us at four.
 template <bool PHILOX, bool ISO>
-__global__ void __launch_bounds__(kReflBlock, 3) reflect_pipe_kernel(ReflArgs a, int64_t n4) {
+__global__ void __launch_bounds__(kReflBlock, 2) reflect_pipe_kernel(ReflArgs a, int64_t n4) {
   pdl_trigger();
   pdl_wait();
   constexpr int NS = streams_in<PHILOX, ISO>();
