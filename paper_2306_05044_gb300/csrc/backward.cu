@@ -392,9 +392,6 @@ __global__ void __launch_bounds__(kBwdBlock, VNDF_BWD_MIN_BLOCKS) loss_backward_
   constexpr int NS = loss_streams_in<PHILOX, ISO>();
   pdl_wait();
   if (blockIdx.x == 0 && threadIdx.x == 0) *sum_counter = 0u;  // read by sum_partials_kernel
-#if VNDF_LOSS_PDL
-  asm volatile("griddepcontrol.launch_dependents;");  // the sum kernel may be scheduled; it waits for us
-#endif
   extern __shared__ float4 smem_l[];  // [2][NS][kBwdBlock]
   float4* mine = smem_l + threadIdx.x;
   if (int64_t(blockIdx.x) < chunks)
@@ -403,6 +400,11 @@ __global__ void __launch_bounds__(kBwdBlock, VNDF_BWD_MIN_BLOCKS) loss_backward_
   int slot = 0;
   for (int64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
     const int64_t e = ch * kChunk + 4 * int64_t(threadIdx.x);
+#if VNDF_LOSS_PDL
+    // the sum kernel may be scheduled once every CTA is in its last chunk (not earlier: its waiting CTAs
+    // would hold CTA slots this grid still needs)
+    if (ch + gridDim.x >= chunks) asm volatile("griddepcontrol.launch_dependents;");
+#endif
     if (ch + gridDim.x < chunks)
       loss_stage<PHILOX, ISO>(a, e + int64_t(gridDim.x) * kChunk, mine + (slot ^ 1) * NS * kBwdBlock);
     cp_async_commit();
