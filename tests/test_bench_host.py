@@ -125,3 +125,16 @@ def test_config_option_keeps_only_that_workloads_legs(monkeypatch):
     monkeypatch.setattr(sys, "argv", ["bench.py"])
     a = bench.parse_args()
     assert not (a.no_fwd_bwd or a.no_albedo or a.no_fit or a.no_prior or a.no_e2e or a.no_cpu_baseline)
+
+
+def test_committed_profiles_match_the_current_sources():
+    """Every kernel the bench quotes ncu figures for has a summary taken from its current sources: a source
+    change without a new capture would silently drop `roofline.traffic` and the issue fractions."""
+    assert bench.measured_traffic_per_sample() is not None
+    for kernel in bench.KERNEL_FILES:
+        if kernel == "stream":
+            continue
+        vals = {}
+        for path in bench.ISSUE_FILES:
+            vals.update(bench._profile_values(path, kernel))
+        assert f"tinst_per_sample.{kernel}" in vals, kernel
